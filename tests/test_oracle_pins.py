@@ -1,0 +1,288 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix (no GPU needed).
+
+Each test checks the oracle against something other than itself: values printed in the
+paper (tests/golden), closed forms, invariants and refinement identities.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import geometry as G
+from conftest import golden
+
+
+# ---------------------------------------------------------------- 1-D rules
+def test_gauss_legendre_exact_for_degree_2g_minus_1():
+    for g in (1, 2, 5, 9, 16):
+        x, w = O.gauss01(g)
+        for k in range(2 * g):
+            assert abs(np.sum(w * x ** k) - 1.0 / (k + 1)) < 1e-14
+
+
+def test_chebyshev_nodes_are_zeros_of_T_q_plus_1():
+    for q in (2, 4, 8, 10):
+        x = O.cheb01(q)
+        assert np.all(np.diff(x) > 0)
+        assert np.max(np.abs(np.cos((q + 1) * np.arccos(2 * x - 1)))) < 1e-13
+
+
+# ---------------------------------------------------------------- geometry (Sec. 3.1)
+@pytest.mark.parametrize("name,patches,area", [
+    ("sphere", G.sphere(), 4 * math.pi),
+    ("torus", G.torus(2.0, 0.5), 4 * math.pi ** 2 * 2.0 * 0.5),
+    ("cube", G.cube(2.0), 24.0),
+])
+def test_surface_area_closed_form(name, patches, area):
+    pr = O.Problem(patches, p=1, m=1, kappa=1.0, q=2, eta=1.6, g_reg=10)
+    assert abs(pr.area() - area) / area < 1e-10
+
+
+def test_sphere_points_on_sphere_and_derivative_fd():
+    pr = O.Problem(G.sphere(), p=1, m=0, kappa=1.0, q=2, eta=1.6)
+    rng = np.random.default_rng(5)
+    s = rng.uniform(0.05, 0.95, (20, 2))
+    for j in range(6):
+        x, d1, d2 = pr.eval_patch(j, s)
+        assert np.max(np.abs(np.linalg.norm(x, axis=1) - 1.0)) < 1e-14
+        hh = 1e-6
+        xp, _, _ = pr.eval_patch(j, s + [hh, 0])
+        xm, _, _ = pr.eval_patch(j, s - [hh, 0])
+        assert np.max(np.abs((xp - xm) / (2 * hh) - d1)) < 1e-8
+        xp, _, _ = pr.eval_patch(j, s + [0, hh])
+        xm, _, _ = pr.eval_patch(j, s - [0, hh])
+        assert np.max(np.abs((xp - xm) / (2 * hh) - d2)) < 1e-8
+        # outward orientation: (d1 x d2) . x > 0 on the sphere
+        assert np.all(np.sum(np.cross(d1, d2) * x, axis=1) > 0)
+
+
+# ---------------------------------------------------------------- discrete space (Sec. 3.2, 4.1)
+def test_dof_count_matches_every_entry_of_table1():
+    tab = golden("table1_sphere.txt")
+    for p, n, dofs_real, *_ in tab:
+        m = int(round(math.log2(n)))
+        pr = O.Problem(G.sphere(), p=int(p), m=m, kappa=1.0, q=2, eta=1.6)
+        assert 2 * pr.ndof == int(dofs_real)
+
+
+def test_dof_formula_matches_table2():
+    for p, n, dofs_real in golden("table2_tesla_dofs.txt"):
+        assert 2 * (2 * 226 * (int(n) + int(p) - 1) ** 2) == int(dofs_real)
+
+
+@pytest.mark.parametrize("patches,p,m", [(G.torus(), 2, 1), (G.cube(), 3, 1), (G.sphere(), 1, 2)])
+def test_dof_formula_other_geometries(patches, p, m):
+    pr = O.Problem(patches, p=p, m=m, kappa=1.0, q=2, eta=1.6)
+    assert pr.ndof == 2 * len(patches) * ((1 << m) + p - 1) ** 2
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_T_rows_form_partition_of_unity(p):
+    # B-splines are non-negative combinations of Bernstein polynomials and sum to one, so
+    # every superspace row of |T| sums to one (and entries are +-(non-negative)).
+    pr = O.Problem(G.sphere(), p=p, m=1, kappa=1.0, q=2, eta=1.6)
+    r, c, v = pr.T()
+    sums = np.zeros(pr.nsup)
+    np.add.at(sums, r, np.abs(v))
+    assert np.max(np.abs(sums - 1.0)) < 1e-13
+    # every global DOF is used
+    assert len(np.unique(c)) == pr.ndof
+
+
+@pytest.mark.parametrize("patches", [G.sphere(), G.torus(), G.cube()])
+def test_divergence_theorem_on_closed_surface(patches):
+    # int_Gamma div_Gamma w = 0 for every w in the div-conforming space on a closed surface:
+    # fails if an interface sign or orientation of T were wrong.
+    pr = O.Problem(patches, p=2, m=1, kappa=1.0, q=2, eta=1.6)
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(pr.ndof) + 1j * rng.standard_normal(pr.ndof)
+    assert abs(pr.div_integral(x)) < 1e-12 * np.abs(x).sum()
+    # a single patch-local function alone does have flux: the test is not vacuous
+    e = np.zeros(pr.ndof, complex)
+    r, c, v = pr.T()
+    assert abs(pr.div_integral(e)) == 0.0
+
+
+# ---------------------------------------------------------------- quadrature (Sec. 4.1, [SS97])
+def test_identical_flat_square_closed_form():
+    # int_Q int_Q 1/|x-y| for a square of side a is a^3 (4 ln(1+sqrt2) + 4/3 (1-sqrt2)).
+    pr = O.Problem(G.cube(2.0), p=1, m=0, kappa=1.0, q=2, eta=1.6)
+    assert pr.pair_kind(0, 0) == 3
+    val = pr.pair_scalar(0, 0, 8, 8, 1e-9)
+    exact = 8.0 * (4 * math.log(1 + math.sqrt(2)) + 4.0 / 3.0 * (1 - math.sqrt(2))) / (4 * math.pi)
+    assert abs(val.real - exact) / exact < 1e-9
+
+
+@pytest.mark.parametrize("patches,kappa,g", [(G.cube(2.0), 1.0, 10), (G.sphere(), 3.0, 16)])
+def test_singular_rules_refinement_identity(patches, kappa, g):
+    # The integral over a pair of coarse elements equals the sum over all pairs of their
+    # four children; this ties the identical, common-edge (also across patches), common-
+    # vertex and regular rules to each other.
+    coarse = O.Problem(patches, p=1, m=0, kappa=kappa, q=2, eta=1.6)
+    fine = O.Problem(patches, p=1, m=1, kappa=kappa, q=2, eta=1.6)
+    kinds = set()
+    pairs = [(0, 0), (0, 2), (0, 4), (2, 4), (0, 1)] if g <= 10 else [(0, 0), (0, 2)]
+    for (a, b) in pairs:
+        kinds.add(coarse.pair_kind(a, b))
+        ref = coarse.pair_scalar(a, b, g, g, kappa)
+        tot = 0j
+        for ca in range(4 * a, 4 * a + 4):
+            for cb in range(4 * b, 4 * b + 4):
+                kinds.add(fine.pair_kind(ca, cb))
+                tot += fine.pair_scalar(ca, cb, g, g, kappa)
+        assert abs(tot - ref) / abs(ref) < 1e-9, (a, b, tot, ref)
+    assert kinds >= {0, 1, 2, 3}
+
+
+def test_near_block_quadrature_converges_in_order():
+    pr = O.Problem(G.sphere(), p=1, m=1, kappa=2.0, q=2, eta=1.6)
+    for (a, b) in [(0, 0), (0, 1), (0, 3), (0, 9)]:
+        lo = pr.pair_block(a, b, 8, 8)
+        hi = pr.pair_block(a, b, 14, 14)
+        assert np.abs(lo - hi).max() / np.abs(hi).max() < 1e-7
+
+
+# ---------------------------------------------------------------- operator (eq. Vkh, eq. FMMlr)
+@pytest.fixture(scope="module")
+def small_dense():
+    pr = O.Problem(G.sphere(), p=1, m=1, kappa=1.5, q=4, eta=1.6, g_reg=8, g_sing=5)
+    return pr, pr.dense_superspace()
+
+
+def test_galerkin_matrix_complex_symmetric_not_hermitian(small_dense):
+    pr, V = small_dense
+    scale = np.abs(V).max()
+    assert np.abs(V - V.T).max() / scale < 1e-13
+    assert np.abs(V - V.conj().T).max() / scale > 1e-3
+
+
+def test_fmm_error_decays_exponentially_in_q():
+    # Thm. "Error of the Bilinear Form": the interpolation error decays exponentially
+    # in q; FMM and dense share the near field, so their difference is the far field.
+    errs = []
+    base = None
+    rng = np.random.default_rng(11)
+    for q in (2, 4, 6, 8):
+        pr = O.Problem(G.sphere(), p=1, m=1, kappa=2.0, q=q, eta=1.6, g_reg=10, g_sing=3)
+        if base is None:
+            x = rng.standard_normal(pr.ndof) + 1j * rng.standard_normal(pr.ndof)
+            base = pr.dense_matvec(x)[0]
+        y = pr.fmm_matvec(x)[0]
+        errs.append(np.linalg.norm(y - base) / np.linalg.norm(base))
+    errs = np.array(errs)
+    assert len(pr.far_pairs()) > 0
+    assert np.all(np.diff(np.log10(errs)) < -0.8), errs   # > ~6x per step of 2 in q
+    assert errs[-1] < 1e-7, errs
+
+
+def test_fmm_far_pairs_are_admissible_and_cover_everything():
+    pr = O.Problem(G.sphere(), p=1, m=2, kappa=1.0, q=2, eta=1.6)
+    far, near, balls = pr.far_pairs(), pr.near_pairs(), pr.balls()
+    for l, t, s in far:
+        d = np.linalg.norm(balls[t, :3] - balls[s, :3]) - balls[t, 3] - balls[s, 3]
+        assert d > 0 and 2 * max(balls[t, 3], balls[s, 3]) <= 1.6 * d
+    # every ordered element pair is covered exactly once by a far block or a near pair
+    n2 = 16
+    cover = np.zeros((pr.nE, pr.nE), int)
+    offs = [6 * (4 ** l - 1) // 3 for l in range(4)]
+    for l, t, s in far:
+        lt, ls = t - offs[l], s - offs[l]
+        span = 4 ** (2 - l)
+        jt, kt = divmod(lt, 4 ** l)
+        js, ks = divmod(ls, 4 ** l)
+        et = jt * n2 + kt * span
+        es = js * n2 + ks * span
+        cover[et:et + span, es:es + span] += 1
+    for e, e2 in near:
+        cover[e, e2] += 1
+    assert np.all(cover == 1)
+
+
+def test_gmres_matches_direct_solve(small_dense):
+    pr, V = small_dense
+    b = pr.rhs(np.array([0, 0, 1.0]), np.array([1.0, 0, 0]))
+    x, its, res, rc = pr.gmres(b, use_fmm=False, tol=1e-10)
+    assert rc == 0 and res <= 1e-10
+    r, c, v = pr.T()
+    T = np.zeros((pr.nsup, pr.ndof))
+    np.add.at(T, (r, c), v)
+    A = T.T @ V @ T
+    xd = np.linalg.solve(A, b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-8
+
+
+# ---------------------------------------------------------------- Mie series
+def test_mie_incident_expansion_and_pec_condition():
+    k, a = 1.7, 1.0
+    rng = np.random.default_rng(0)
+    pts = rng.standard_normal((8, 3)) * 0.7
+    ex = np.zeros((8, 3), complex)
+    ex[:, 0] = np.exp(1j * k * pts[:, 2])
+    assert np.abs(O.mie_field(k, a, 0, pts) - ex).max() < 1e-13
+    sp = pts / np.linalg.norm(pts, axis=1, keepdims=True)
+    Et = O.mie_field(k, a, 0, sp) + O.mie_field(k, a, 1, sp)
+    tan = Et - np.sum(Et * sp, axis=1, keepdims=True) * sp
+    assert np.abs(tan).max() < 1e-13
+
+
+def test_mie_far_field_amplitude_is_the_large_r_limit():
+    k, a, R = 1.3, 1.0, 400.0
+    d = np.array([[0, 0, 1.0], [0.6, 0, 0.8], [0, -1.0, 0], [0.48, 0.6, -0.64]])
+    F = O.mie_field(k, a, 4, d)
+    Es = O.mie_field(k, a, 1, d * R) * R * np.exp(-1j * k * R)
+    assert np.abs(F - Es).max() / np.abs(F).max() < 5.0 / (k * R)
+
+
+def test_mie_optical_theorem():
+    # lossless scatterer: scattered power = extinction, sigma_ext = 4 pi / k Im(pol . F(d_inc))
+    k, a = 1.0, 1.0
+    x, w = O.gauss01(24)
+    th, wt = np.pi * x, np.pi * w
+    ph, wp = 2 * np.pi * (np.arange(48) + 0.5) / 48, np.full(48, 2 * np.pi / 48)
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    d = np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)], -1).reshape(-1, 3)
+    F = O.mie_field(k, a, 4, d)
+    wgt = (wt[:, None] * np.sin(th)[:, None] * wp[None, :]).reshape(-1)
+    sca = np.sum(wgt * np.sum(np.abs(F) ** 2, axis=1))
+    ext = 4 * np.pi / k * O.mie_field(k, a, 4, np.array([[0, 0, 1.0]]))[0, 0].imag
+    assert abs(sca - ext) / ext < 1e-10
+
+
+def test_mie_curl_against_finite_differences():
+    k, a = 1.2, 1.0
+    rng = np.random.default_rng(1)
+    P0 = rng.standard_normal((4, 3))
+    P0 *= 1.6 / np.linalg.norm(P0, axis=1, keepdims=True)
+    E = lambda x: O.mie_field(k, a, 0, x) + O.mie_field(k, a, 1, x)
+    hh = 1e-5
+    J = np.zeros((4, 3, 3), complex)
+    for d in range(3):
+        e = np.zeros(3)
+        e[d] = hh
+        J[:, :, d] = (E(P0 + e) - E(P0 - e)) / (2 * hh)
+    curl = np.stack([J[:, 2, 1] - J[:, 1, 2], J[:, 0, 2] - J[:, 2, 0], J[:, 1, 0] - J[:, 0, 1]], axis=1)
+    assert np.abs(curl - O.mie_field(k, a, 2, P0)).max() < 1e-8
+
+
+# ---------------------------------------------------------------- solution vs paper (Sec. 5.1, Tab. 1)
+@pytest.mark.slow
+def test_mie_l2_error_matches_table1_p1():
+    tab = golden("table1_sphere.txt")
+    errs = []
+    for n, m in ((2, 1), (4, 2)):
+        pr = O.Problem(G.sphere(), p=1, m=m, kappa=1.0, q=6, eta=1.6)
+        b = pr.rhs(np.array([0, 0, 1.0]), np.array([1.0, 0, 0]))
+        w, its, res, rc = pr.gmres(b, use_fmm=True, tol=1e-8)
+        assert rc == 0
+        e, nrm = pr.mie_l2(w)
+        paper = tab[(tab[:, 0] == 1) & (tab[:, 1] == n)][0, 5]
+        assert abs(e - paper) / paper < 0.1, (n, e, paper)
+        errs.append(e)
+        # far field against the Mie scattered field far away (e_s ~ E_inf e^{ikr}/r)
+        if m == 2:
+            dirs = np.array([[0, 0, 1.0], [1.0, 0, 0], [0, 0.6, -0.8]])
+            Ef = pr.far_field(w, dirs)
+            Es = O.mie_field(1.0, 1.0, 4, dirs)
+            assert np.abs(Ef - Es).max() / np.abs(Es).max() < 0.05
+    assert 1.6 < errs[0] / errs[1] < 2.6   # O(h^p), p = 1
