@@ -1,0 +1,179 @@
+/* efie.h -- C ABI of the GB300 isogeometric EFIE library.
+ *
+ * The library solves the electric field integral equation for perfectly conducting
+ * scatterers bounded by multipatch NURBS surfaces (Doelz, Kurz, Schoeps, Wolf,
+ * "Isogeometric Boundary Elements in Electromagnetism", arXiv 1807.03097):
+ *
+ *   find w_h in S^1 (div-conforming B-splines, Sec. 3.2) such that
+ *   V_{kappa,h} w_h = -f_h                                   (eq. linsys)
+ *
+ * with the Galerkin matrix of eq. MSLtested applied through the superspace
+ * transformation T^T V* T (eq. superspace) and the interpolation-based H^2 / fast multipole
+ * compression of Sec. 4.2 (eq. FMMlr, Algorithm 1), inside a restarted GMRES (Sec. 5).
+ * Every numerical step runs in CUDA kernels on one GPU; host code only builds index
+ * structures (DOF map, cluster tree, block-cluster tree).
+ *
+ * Conventions
+ *  - All functions return efie_status: 0 on success, > 0 for a completed call with a
+ *    warning (EFIE_NOT_CONVERGED), < 0 on error.  No C++ exception crosses the ABI.
+ *  - Complex numbers are interleaved (re, im) doubles; a vector of n complex values is
+ *    2n doubles.  Several right-hand sides are stored one after the other ([nrhs][n]).
+ *  - ptr_kind EFIE_PTR_HOST: pointers are host memory (pageable or pinned); the call
+ *    copies in and out and returns after the result is in host memory.
+ *    EFIE_PTR_DEVICE: pointers are device memory of the context's GPU; the call is ordered
+ *    on the context's stream and returns once the result is complete on the device.
+ *  - The caller owns every buffer it passes; the library deep-copies inputs and never
+ *    keeps a caller pointer beyond the call.
+ *  - DOF order: patch-major, then component (s1 then s2), then B-spline index i2, i1 (i1
+ *    fastest); a function shared by two patches across an interface is numbered where it
+ *    first occurs, and its part on the other patch carries the sign that keeps the normal
+ *    flux continuous.
+ *  - Thread safety: one context per host thread; contexts are independent.
+ */
+#ifndef EFIE_H
+#define EFIE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int efie_status;
+#define EFIE_OK 0
+#define EFIE_NOT_CONVERGED 1  /* GMRES reached gmres_maxit; output holds the last iterate */
+#define EFIE_EINVAL -1        /* invalid argument (null pointer, size or option out of range) */
+#define EFIE_ENOMEM -2        /* device or host allocation failed */
+#define EFIE_EGEOMETRY -3     /* open, non-manifold, inward-oriented or mismatched patches */
+#define EFIE_ECUDA -4         /* a CUDA call failed; the context should be destroyed */
+#define EFIE_ESTATE -5        /* call out of order (e.g. matvec before efie_setup) */
+#define EFIE_ETIMEOUT -6      /* a device-side wait gave up (status word set by a kernel) */
+
+#define EFIE_FP64 0           /* every step in FP64 */
+#define EFIE_MIXED_FP32 1     /* moments, M2M, M2L, L2L in FP32 (phase split, FP64 per-pair
+                                 phase); geometry, near field and GMRES in FP64 */
+
+#define EFIE_PTR_HOST 0
+#define EFIE_PTR_DEVICE 1
+
+typedef struct efie_ctx efie_ctx;
+
+/* Discretisation and solver parameters (the paper's problem statement, Sec. 4.1, 4.2, 5). */
+typedef struct {
+  int p;             /* degree of S^0; S^1 uses (p, p-1) x (p-1, p), 1 <= p <= 6 (Sec. 3.2) */
+  int level_m;       /* refinement level: 2^m equidistant elements per patch direction,
+                        0 <= m <= 10 (Sec. 4.1) */
+  double kappa;      /* wavenumber, > 0 (eq. HelmholtzGreen) */
+  int q;             /* interpolation degree, q + 1 Chebyshev points per direction,
+                        1 <= q <= 16 (Sec. 4.2) */
+  double eta;        /* admissibility parameter, > 0 (eq. admissibility) */
+  int precision;     /* EFIE_FP64 or EFIE_MIXED_FP32 */
+  int quad_regular;  /* Gauss points per direction for separated near pairs, right-hand
+                        side and far field; 0 selects p + 4 */
+  int quad_singular; /* Gauss points per direction in each Duffy part of touching pairs;
+                        0 selects p + 4 */
+  int gmres_restart; /* restart length (the paper uses 1500), >= 1 */
+  double gmres_tol;  /* residual tolerance */
+  int gmres_maxit;   /* total iteration cap */
+  int tol_is_relative; /* 1: ||r|| <= tol ||b||, 0: ||r|| <= tol */
+} efie_options;
+
+typedef struct {
+  int iterations;        /* GMRES iterations (matrix-vector products) of the last solve */
+  int converged;         /* 1 if the tolerance was met */
+  double residual;       /* final ||b - A x|| (relative if tol_is_relative) */
+  double setup_ms;       /* device time of efie_setup */
+  double solve_ms;       /* wall time of the last solve on the device */
+} efie_solve_info;
+
+/* Fills *opt with defaults: p=1, m=2, kappa=1, q=4, eta=1.6, FP64, restart 1500,
+ * tol 1e-8 relative, maxit 10000. */
+efie_status efie_default_options(efie_options *opt);
+
+/* Creates a context on the current CUDA device.  cuda_stream: a cudaStream_t to order
+ * all work on, or NULL for a stream the context creates.  Errors: EFIE_EINVAL (bad
+ * options), EFIE_ENOMEM, EFIE_ECUDA (no device). */
+efie_status efie_create(efie_ctx **out, const efie_options *opt, void *cuda_stream);
+
+/* Sets the geometry: n_patches NURBS patches F_j: [0,1]^2 -> R^3 (eq. def::geom).
+ *  deg   [n][2]  degrees in s1 and s2 (>= 1)
+ *  ncp   [n][2]  control points in s1 and s2 (<= 64 each)
+ *  knots         per patch the s1 knot vector (ncp0 + deg0 + 1 values) followed by the s2
+ *                knot vector, p-open on [0,1]
+ *  cp            per patch [ncp1][ncp0][3] control points (s1 fastest)
+ *  w             per patch [ncp1][ncp0] positive weights
+ * Host pointers, deep-copied.  Interfaces are detected by matching patch edges (Sec. 3.1:
+ * F_j(.,1) = F_i(.,0) up to orientation).  Errors: EFIE_EINVAL, EFIE_EGEOMETRY (an edge
+ * without exactly one partner, or d1F x d2F not pointing out of the enclosed volume). */
+efie_status efie_set_geometry(efie_ctx *ctx, int n_patches, const int *deg, const int *ncp,
+                              const double *knots, const double *cp, const double *w);
+
+/* Builds the discrete space and T (eq. superspace), cluster tree and block-cluster tree
+ * (Algorithm 1), evaluates the geometry at the interpolation nodes and computes every
+ * near-field element block by Sauter-Schwab / Gauss quadrature (eq. Vkh), all resident on
+ * the device.  Errors: EFIE_ESTATE (no geometry), EFIE_EGEOMETRY, EFIE_ENOMEM, EFIE_ECUDA. */
+efie_status efie_setup(efie_ctx *ctx);
+
+/* Number of complex unknowns 2 N (n + p - 1)^2 of a closed surface. */
+efie_status efie_num_dofs(const efie_ctx *ctx, int64_t *n);
+
+/* y = T^T (N + F) T x for nrhs vectors of efie_num_dofs complex values each (the FMM
+ * approximation of the Galerkin matrix of eq. MSLtested).  Errors: EFIE_ESTATE,
+ * EFIE_EINVAL, EFIE_ECUDA. */
+efie_status efie_matvec(efie_ctx *ctx, int nrhs, const double *x, double *y, int ptr_kind);
+
+/* Right-hand side of eq. linsys for incident plane waves e_i = pol exp(i kappa dir.x):
+ * g_j = -int_Gamma e_i . phi_j dsigma.  dir, pol: [nrhs][3] host arrays; g [nrhs][ndof]
+ * complex in ptr_kind memory. */
+efie_status efie_rhs_plane_waves(efie_ctx *ctx, int nrhs, const double *dir, const double *pol,
+                                 double *g, int ptr_kind);
+
+/* Solves A x = b by restarted GMRES (zero initial guess) for nrhs right-hand sides, one
+ * after the other.  Returns EFIE_NOT_CONVERGED (with the last iterate in x) if some
+ * right-hand side reached gmres_maxit.  info may be NULL. */
+efie_status efie_solve(efie_ctx *ctx, int nrhs, const double *b, double *x, int ptr_kind,
+                       efie_solve_info *info);
+
+/* Right-hand side plus solve: the scattering problem for incident plane waves. */
+efie_status efie_solve_plane_waves(efie_ctx *ctx, int nrhs, const double *dir, const double *pol,
+                                   double *w, int ptr_kind, efie_solve_info *info);
+
+/* Far field of the scattered wave, e_s(r d) ~ E_inf(d) e^{i kappa r} / r, from the
+ * representation formula (eq. ESLP): E_inf(d) = (1/4pi) (W - d (d.W)),
+ * W = int_Gamma w(y) exp(-i kappa d.y) dsigma_y.  w: [nrhs][ndof] complex, dirs: [ndir][3]
+ * unit vectors (host), e_inf: [nrhs][ndir][3] complex; w and e_inf in ptr_kind memory. */
+efie_status efie_far_field(efie_ctx *ctx, int nrhs, const double *w, int ndir, const double *dirs,
+                           double *e_inf, int ptr_kind);
+
+/* Introspection for verification.
+ * efie_block_counts: far blocks, near element pairs, clusters, superspace size.
+ * efie_export_blocks: far [nfar][3] = (level, target cluster, source cluster) and near
+ *   [nnear][2] = (target element, source element), host memory; cluster ids are
+ *   level offset + patch * 4^level + morton index, element ids patch * 4^m + morton index.
+ * efie_export_near_blocks: near-field element blocks [nnear][nb][nb] complex (host),
+ *   nb = 2 (p+1)^2, rows (alpha, b, a) of the target element, columns of the source.
+ * efie_matvec_superspace: ys = (N + F) xs on superspace vectors [nE][2][p+1][p+1]
+ *   complex (ptr_kind memory). */
+efie_status efie_block_counts(const efie_ctx *ctx, int64_t *nfar, int64_t *nnear, int64_t *nclusters,
+                              int64_t *nsuperspace);
+efie_status efie_export_blocks(const efie_ctx *ctx, int *far, int *near);
+efie_status efie_export_near_blocks(efie_ctx *ctx, double *blocks);
+efie_status efie_matvec_superspace(efie_ctx *ctx, const double *xs, double *ys, int ptr_kind);
+
+/* Device time in milliseconds of the named phases of the most recent efie_matvec
+ * (CUDA events on the context stream): out[0] total, [1] gather, [2] near apply,
+ * [3] moments + M2M, [4] M2L, [5] L2L + evaluation, [6] scatter.  Returns the number of
+ * values written (<= n). */
+int efie_last_timings(const efie_ctx *ctx, double *out, int n);
+
+/* Releases all device and host memory of the context (NULL is accepted). */
+efie_status efie_destroy(efie_ctx *ctx);
+
+/* Static description of a status code. */
+const char *efie_status_string(efie_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

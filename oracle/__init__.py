@@ -59,6 +59,7 @@ def _load():
         "orc_dense_matvec": (None, [P, c_int, D, D]),
         "orc_fmm_matvec": (None, [P, c_int, D, D]),
         "orc_fmm_matvec_superspace": (None, [P, D, D]),
+        "orc_fmm_rows": (None, [P, D, c_int, I, D]),
         "orc_rhs": (None, [P, D, D, D]),
         "orc_gmres": (c_int, [P, c_int, D, D, c_int, c_double, c_int, I, D]),
         "orc_far_field": (None, [P, D, c_int, D, D]),
@@ -222,6 +223,13 @@ class Problem:
         ys = np.zeros_like(xs)
         self._L.orc_fmm_matvec_superspace(self.h, _d(xs.view(np.float64)), _d(ys.view(np.float64)))
         return ys
+
+    def fmm_rows(self, xs, elems):
+        xs = _cz(xs).reshape(self.nsup)
+        elems = np.ascontiguousarray(elems, np.int32)
+        out = np.zeros((len(elems), self.nb), np.complex128)
+        self._L.orc_fmm_rows(self.h, _d(xs.view(np.float64)), len(elems), _i(elems), _d(out.view(np.float64)))
+        return out
 
     def rhs(self, d, pol):
         d = np.ascontiguousarray(d, float)

@@ -1019,36 +1019,20 @@ static const double *mom_table(const orc_problem *P, int deriv, int l) {
   return (deriv ? P->Mdt : P->Mt) + o;
 }
 
-/* y* = (N + F) x* in superspace coordinates. */
-static void fmm_superspace(orc_problem *P, const cplx *xs, cplx *ys) {
-  ensure_near_blocks(P);
-  int p = P->p, np1 = p + 1, nb = nb_of(P), q1 = P->q + 1, nI = P->nI;
+/* moments of every cluster, computed directly from its elements:
+ * mu_beta(m) = sum_e sum_ab [int L_m psi_ab] x*_{e,beta,ab},
+ * nu(m) = sum_e sum_beta sum_ab [int L_m d_beta psi_ab] x*_{e,beta,ab} */
+static cplx *direct_moments(const orc_problem *P, const cplx *xs) {
+  int p = P->p, np1 = p + 1, q1 = P->q + 1, nI = P->nI;
   double h = 1.0 / P->n, h2 = h * h;
-  for (int i = 0; i < P->nsup; ++i) ys[i] = 0;
-  /* near field */
-  for (int k = 0; k < P->nnear; ++k) {
-    int e = P->near[2 * k], e2 = P->near[2 * k + 1];
-    const cplx *B = P->nblk + (size_t)k * nb * nb;
-    for (int r = 0; r < nb; ++r) {
-      cplx s = 0;
-      for (int c = 0; c < nb; ++c) s += B[r * nb + c] * xs[(size_t)e2 * nb + c];
-      ys[(size_t)e * nb + r] += s;
-    }
-  }
-  /* moments of every cluster, computed directly from its elements:
-   * mu_beta(m) = sum_e sum_ab [int L_m psi_ab] x*_{e,beta,ab},
-   * nu(m) = sum_e sum_beta sum_ab [int L_m d_beta psi_ab] x*_{e,beta,ab} */
   cplx *mom = calloc((size_t)P->ncl * 3 * nI, sizeof(cplx));
-  cplx *loc = calloc((size_t)P->ncl * 3 * nI, sizeof(cplx));
-  int n2 = P->n * P->n;
   for (int l = 0; l <= P->m; ++l) {
     const double *M = mom_table(P, 0, l), *Md = mom_table(P, 1, l);
     int sh = P->m - l;
     for (int e = 0; e < P->nE; ++e) {
       int j, i1, i2;
       elem_of(P, e, &j, &i1, &i2);
-      int K = morton(i1 >> sh, i2 >> sh);
-      int id = cl_id(P, l, j, K);
+      int id = cl_id(P, l, j, morton(i1 >> sh, i2 >> sh));
       int o1 = i1 - ((i1 >> sh) << sh), o2 = i2 - ((i2 >> sh) << sh);
       cplx *mu = mom + (size_t)id * 3 * nI;
       for (int m2 = 0; m2 < q1; ++m2)
@@ -1064,54 +1048,117 @@ static void fmm_superspace(orc_problem *P, const cplx *xs, cplx *ys) {
               }
     }
   }
-  (void)n2;
-  /* far field: for each admissible block, the coupling matrices K1^(alpha,beta) =
-   * G <d_alpha F(x_m), d_beta F(x_m')> and K2 = -kappa^-2 G at the interpolation nodes */
+  return mom;
+}
+
+/* one admissible block (eq. FMMlr): with K1^(alpha,beta) = G <d_alpha F(x_m), d_beta F(x_m')>
+ * and K2 = -kappa^-2 G at the interpolation nodes, lo += [K1 mu ; K2 nu] */
+static void far_block(const orc_problem *P, int t, int s, const cplx *mom, cplx *loc) {
+  int nI = P->nI;
   double ik2 = 1.0 / (P->kappa * P->kappa);
-  for (int f = 0; f < P->nfar; ++f) {
-    int t = P->far[3 * f + 1], s = P->far[3 * f + 2];
-    const cplx *mu = mom + (size_t)s * 3 * nI;
-    cplx *lo = loc + (size_t)t * 3 * nI;
-    for (int mi = 0; mi < nI; ++mi) {
-      const double *gt = P->cgeo + 9 * ((size_t)t * nI + mi);
-      for (int mj = 0; mj < nI; ++mj) {
-        const double *gs = P->cgeo + 9 * ((size_t)s * nI + mj);
-        cplx G = helmholtz(P->kappa, dist3(gt, gs));
-        for (int alpha = 0; alpha < 2; ++alpha)
-          for (int beta = 0; beta < 2; ++beta) {
-            const double *da = gt + 3 + 3 * alpha, *db = gs + 3 + 3 * beta;
-            double dot = da[0] * db[0] + da[1] * db[1] + da[2] * db[2];
-            lo[alpha * nI + mi] += G * dot * mu[beta * nI + mj];
+  const cplx *mu = mom + (size_t)s * 3 * nI;
+  cplx *lo = loc + (size_t)t * 3 * nI;
+  for (int mi = 0; mi < nI; ++mi) {
+    const double *gt = P->cgeo + 9 * ((size_t)t * nI + mi);
+    for (int mj = 0; mj < nI; ++mj) {
+      const double *gs = P->cgeo + 9 * ((size_t)s * nI + mj);
+      cplx G = helmholtz(P->kappa, dist3(gt, gs));
+      for (int alpha = 0; alpha < 2; ++alpha)
+        for (int beta = 0; beta < 2; ++beta) {
+          const double *da = gt + 3 + 3 * alpha, *db = gs + 3 + 3 * beta;
+          double dot = da[0] * db[0] + da[1] * db[1] + da[2] * db[2];
+          lo[alpha * nI + mi] += G * dot * mu[beta * nI + mj];
+        }
+      lo[2 * nI + mi] += -ik2 * G * mu[2 * nI + mj];
+    }
+  }
+}
+
+/* evaluation of the local fields of the level-l cluster containing e at its test functions */
+static void eval_local(const orc_problem *P, int l, int e, const cplx *loc, cplx *ye) {
+  int p = P->p, np1 = p + 1, q1 = P->q + 1, nI = P->nI;
+  double h = 1.0 / P->n, h2 = h * h;
+  const double *M = mom_table(P, 0, l), *Md = mom_table(P, 1, l);
+  int sh = P->m - l;
+  int j, i1, i2;
+  elem_of(P, e, &j, &i1, &i2);
+  int id = cl_id(P, l, j, morton(i1 >> sh, i2 >> sh));
+  int o1 = i1 - ((i1 >> sh) << sh), o2 = i2 - ((i2 >> sh) << sh);
+  const cplx *lo = loc + (size_t)id * 3 * nI;
+  for (int alpha = 0; alpha < 2; ++alpha)
+    for (int b = 0; b < np1; ++b)
+      for (int a = 0; a < np1; ++a) {
+        cplx acc = 0;
+        for (int m2 = 0; m2 < q1; ++m2)
+          for (int m1 = 0; m1 < q1; ++m1) {
+            double Ma = M[(o1 * q1 + m1) * np1 + a], Mb = M[(o2 * q1 + m2) * np1 + b];
+            double Dda = Md[(o1 * q1 + m1) * np1 + a], Ddb = Md[(o2 * q1 + m2) * np1 + b];
+            acc += h2 * Ma * Mb * lo[alpha * nI + m2 * q1 + m1];
+            acc += h * (alpha == 0 ? Dda * Mb : Ma * Ddb) * lo[2 * nI + m2 * q1 + m1];
           }
-        lo[2 * nI + mi] += -ik2 * G * mu[2 * nI + mj];
+        ye[(alpha * np1 + b) * np1 + a] += acc;
+      }
+}
+
+/* y* = (N + F) x* in superspace coordinates. */
+static void fmm_superspace(orc_problem *P, const cplx *xs, cplx *ys) {
+  ensure_near_blocks(P);
+  int nb = nb_of(P), nI = P->nI;
+  for (int i = 0; i < P->nsup; ++i) ys[i] = 0;
+  /* near field */
+  for (int k = 0; k < P->nnear; ++k) {
+    int e = P->near[2 * k], e2 = P->near[2 * k + 1];
+    const cplx *B = P->nblk + (size_t)k * nb * nb;
+    for (int r = 0; r < nb; ++r) {
+      cplx s = 0;
+      for (int c = 0; c < nb; ++c) s += B[r * nb + c] * xs[(size_t)e2 * nb + c];
+      ys[(size_t)e * nb + r] += s;
+    }
+  }
+  cplx *mom = direct_moments(P, xs);
+  cplx *loc = calloc((size_t)P->ncl * 3 * nI, sizeof(cplx));
+  for (int f = 0; f < P->nfar; ++f) far_block(P, P->far[3 * f + 1], P->far[3 * f + 2], mom, loc);
+  for (int l = 0; l <= P->m; ++l)
+    for (int e = 0; e < P->nE; ++e) eval_local(P, l, e, loc, ys + (size_t)e * nb);
+  free(mom);
+  free(loc);
+}
+
+/* rows of y* = (N + F) x* for selected elements only: near blocks integrated on demand,
+ * far field restricted to the blocks whose target cluster contains the element */
+void orc_fmm_rows(orc_problem *P, const double *xsd, int nrows, const int *elems, double *out) {
+  const cplx *xs = (const cplx *)xsd;
+  int nb = nb_of(P), nI = P->nI;
+  cplx *o = (cplx *)out;
+  regular_cache(P, P->greg);
+  cplx *mom = direct_moments(P, xs);
+  cplx *loc = calloc((size_t)P->ncl * 3 * nI, sizeof(cplx));
+  cplx *blk = malloc(sizeof(cplx) * nb * nb);
+  for (int r = 0; r < nrows; ++r) {
+    int e = elems[r];
+    cplx *ye = o + (size_t)r * nb;
+    for (int i = 0; i < nb; ++i) ye[i] = 0;
+    for (int k = 0; k < P->nnear; ++k) {
+      if (P->near[2 * k] != e) continue;
+      int e2 = P->near[2 * k + 1];
+      pair_block(P, e, e2, P->greg, P->gsing, blk);
+      for (int i = 0; i < nb; ++i) {
+        cplx s = 0;
+        for (int c = 0; c < nb; ++c) s += blk[i * nb + c] * xs[(size_t)e2 * nb + c];
+        ye[i] += s;
       }
     }
-  }
-  /* evaluation at the test functions of every target cluster */
-  for (int l = 0; l <= P->m; ++l) {
-    const double *M = mom_table(P, 0, l), *Md = mom_table(P, 1, l);
-    int sh = P->m - l;
-    for (int e = 0; e < P->nE; ++e) {
-      int j, i1, i2;
-      elem_of(P, e, &j, &i1, &i2);
-      int id = cl_id(P, l, j, morton(i1 >> sh, i2 >> sh));
-      int o1 = i1 - ((i1 >> sh) << sh), o2 = i2 - ((i2 >> sh) << sh);
-      const cplx *lo = loc + (size_t)id * 3 * nI;
-      for (int alpha = 0; alpha < 2; ++alpha)
-        for (int b = 0; b < np1; ++b)
-          for (int a = 0; a < np1; ++a) {
-            cplx acc = 0;
-            for (int m2 = 0; m2 < q1; ++m2)
-              for (int m1 = 0; m1 < q1; ++m1) {
-                double Ma = M[(o1 * q1 + m1) * np1 + a], Mb = M[(o2 * q1 + m2) * np1 + b];
-                double Dda = Md[(o1 * q1 + m1) * np1 + a], Ddb = Md[(o2 * q1 + m2) * np1 + b];
-                acc += h2 * Ma * Mb * lo[alpha * nI + m2 * q1 + m1];
-                acc += h * (alpha == 0 ? Dda * Mb : Ma * Ddb) * lo[2 * nI + m2 * q1 + m1];
-              }
-            ys[((size_t)(e * 2 + alpha) * np1 + b) * np1 + a] += acc;
-          }
+    int j, i1, i2;
+    elem_of(P, e, &j, &i1, &i2);
+    for (int l = 0; l <= P->m; ++l) {
+      int sh = P->m - l, id = cl_id(P, l, j, morton(i1 >> sh, i2 >> sh));
+      memset(loc + (size_t)id * 3 * nI, 0, sizeof(cplx) * 3 * nI);
+      for (int f = 0; f < P->nfar; ++f)
+        if (P->far[3 * f + 1] == id) far_block(P, id, P->far[3 * f + 2], mom, loc);
+      eval_local(P, l, e, loc, ye);
     }
   }
+  free(blk);
   free(mom);
   free(loc);
 }

@@ -71,9 +71,11 @@ void orc_dense_superspace(const orc_problem *P, double *out);
 void orc_dense_matvec(const orc_problem *P, int nrhs, const double *x, double *y);
 /* y = T^T (N + F) T x through the non-nested interpolation FMM */
 void orc_fmm_matvec(orc_problem *P, int nrhs, const double *x, double *y);
-/* FMM matvec restricted to the target clusters in [t0, t1) of the leaf level plus the
- * near field of those target elements (sampling for timing); y in superspace layout */
+/* y* = (N + F) x* on superspace vectors [nE][2][p+1][p+1] complex */
 void orc_fmm_matvec_superspace(orc_problem *P, const double *xs, double *ys);
+/* the rows of y* = (N + F) x* belonging to the listed elements, out [nrows][2(p+1)^2]
+ * (near blocks integrated on demand; for sampled checks and timing at large sizes) */
+void orc_fmm_rows(orc_problem *P, const double *xs, int nrows, const int *elems, double *out);
 
 /* right-hand side g = -T^T int e_i . phi for e_i = pol exp(i kappa d.x) */
 void orc_rhs(const orc_problem *P, const double *dir, const double *pol, double *g);

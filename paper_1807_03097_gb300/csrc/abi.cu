@@ -1,0 +1,509 @@
+// extern "C" entry points of the library (include/efie.h).  Argument checking, host/device
+// copies and the order of the setup phases; every numerical step is a CUDA kernel in the
+// other translation units.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "efie_internal.h"
+
+using namespace efie;
+
+namespace efie {
+efie_status dev_scatter(Ctx *c, const double2 *ys, double2 *y);
+efie_status dev_gather(Ctx *c, const double2 *x, double2 *xs);
+efie_status dev_norms(Ctx *c, int N, const double2 *v, double *out);
+}  // namespace efie
+
+namespace {
+
+template <class T>
+void dfree(T *&p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void release_device(Ctx *c) {
+  dfree(c->d_patches); dfree(c->d_knots); dfree(c->d_cpw);
+  dfree(c->d_tg_ptr); dfree(c->d_tg_col); dfree(c->d_tg_val);
+  dfree(c->d_ts_ptr); dfree(c->d_ts_col); dfree(c->d_ts_val);
+  dfree(c->d_nodeX); dfree(c->d_nodeD); dfree(c->d_nodeXf); dfree(c->d_center);
+  dfree(c->d_far_ptr); dfree(c->d_far_src); dfree(c->d_m2l_targets);
+  dfree(c->d_near_ptr); dfree(c->d_near_src); dfree(c->d_nblk);
+  dfree(c->d_M); dfree(c->d_Md); dfree(c->d_E); dfree(c->d_Mf); dfree(c->d_Mdf); dfree(c->d_Ef);
+  dfree(c->d_x); dfree(c->d_y); dfree(c->d_xs); dfree(c->d_ys); dfree(c->d_ysn);
+  dfree(c->d_mom); dfree(c->d_src); dfree(c->d_acc); dfree(c->d_loc);
+  dfree(c->d_momf); dfree(c->d_srcf); dfree(c->d_locf); dfree(c->d_accm);
+  dfree(c->d_V); dfree(c->d_H); dfree(c->d_h); dfree(c->d_h2); dfree(c->d_part); dfree(c->d_gs);
+  dfree(c->d_w); dfree(c->d_r); dfree(c->d_b); dfree(c->d_sol);
+  c->kr = 0;
+  c->part_cap = 0;
+}
+
+efie_status check_options(const efie_options *o) {
+  if (!o) return EFIE_EINVAL;
+  if (o->p < 1 || o->p > 4) return EFIE_EINVAL;
+  if (o->level_m < 0 || o->level_m > 10) return EFIE_EINVAL;
+  if (!(o->kappa > 0.0) || !std::isfinite(o->kappa)) return EFIE_EINVAL;
+  if (o->q < 1 || o->q + 1 > kMaxQ1) return EFIE_EINVAL;
+  if (!(o->eta > 0.0)) return EFIE_EINVAL;
+  if (o->precision != EFIE_FP64 && o->precision != EFIE_MIXED_FP32) return EFIE_EINVAL;
+  if (o->quad_regular < 0 || o->quad_regular > 16 || o->quad_singular < 0 || o->quad_singular > 16) return EFIE_EINVAL;
+  if (o->gmres_restart < 1 || o->gmres_maxit < 1 || !(o->gmres_tol > 0.0)) return EFIE_EINVAL;
+  return EFIE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *efie_status_string(efie_status s) {
+  switch (s) {
+    case EFIE_OK: return "ok";
+    case EFIE_NOT_CONVERGED: return "GMRES did not reach the tolerance within gmres_maxit iterations";
+    case EFIE_EINVAL: return "invalid argument";
+    case EFIE_ENOMEM: return "out of memory";
+    case EFIE_EGEOMETRY: return "invalid geometry (open, non-manifold, mismatched or inward-oriented patches)";
+    case EFIE_ECUDA: return "CUDA error";
+    case EFIE_ESTATE: return "call out of order";
+    case EFIE_ETIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+efie_status efie_default_options(efie_options *o) {
+  if (!o) return EFIE_EINVAL;
+  std::memset(o, 0, sizeof(*o));
+  o->p = 1;
+  o->level_m = 2;
+  o->kappa = 1.0;
+  o->q = 4;
+  o->eta = 1.6;
+  o->precision = EFIE_FP64;
+  o->gmres_restart = 1500;
+  o->gmres_tol = 1e-8;
+  o->gmres_maxit = 10000;
+  o->tol_is_relative = 1;
+  return EFIE_OK;
+}
+
+efie_status efie_create(efie_ctx **out, const efie_options *opt, void *cuda_stream) {
+  if (!out) return EFIE_EINVAL;
+  *out = nullptr;
+  if (check_options(opt) != EFIE_OK) return EFIE_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return EFIE_ECUDA;
+  Ctx *c = new (std::nothrow) Ctx();
+  if (!c) return EFIE_ENOMEM;
+  c->opt = *opt;
+  cudaGetDevice(&c->device);
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return EFIE_ECUDA;
+    }
+    c->own_stream = true;
+  }
+  if (cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) {
+    delete c;
+    return EFIE_ECUDA;
+  }
+  for (int i = 0; i < 8; ++i) cudaEventCreate(&c->tm.ev[i]);
+  c->tm.made = true;
+  *out = reinterpret_cast<efie_ctx *>(c);
+  return EFIE_OK;
+}
+
+efie_status efie_destroy(efie_ctx *ctx) {
+  if (!ctx) return EFIE_OK;
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->stream2) cudaStreamSynchronize(c->stream2);
+  release_device(c);
+  if (c->h_res) cudaFreeHost(c->h_res);
+  if (c->tm.made)
+    for (int i = 0; i < 8; ++i) cudaEventDestroy(c->tm.ev[i]);
+  if (c->fork) cudaEventDestroy(c->fork);
+  if (c->join) cudaEventDestroy(c->join);
+  if (c->stream2) cudaStreamDestroy(c->stream2);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return EFIE_OK;
+}
+
+efie_status efie_set_geometry(efie_ctx *ctx, int n_patches, const int *deg, const int *ncp, const double *knots,
+                              const double *cp, const double *w) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c || n_patches <= 0 || n_patches > 100000 || !deg || !ncp || !knots || !cp || !w) return EFIE_EINVAL;
+  cudaSetDevice(c->device);
+  std::vector<PatchDesc> P(n_patches);
+  std::vector<double> kn, hw;
+  size_t ko = 0, co = 0;
+  for (int j = 0; j < n_patches; ++j) {
+    PatchDesc &d = P[j];
+    for (int t = 0; t < 2; ++t) {
+      d.deg[t] = deg[2 * j + t];
+      d.ncp[t] = ncp[2 * j + t];
+      if (d.deg[t] < 1 || d.deg[t] > kMaxGeoDeg || d.ncp[t] < d.deg[t] + 1 || d.ncp[t] > kMaxGeoCp) return EFIE_EINVAL;
+      int nk = d.ncp[t] + d.deg[t] + 1;
+      d.kofs[t] = (int)kn.size();
+      for (int i = 0; i < nk; ++i) {
+        double v = knots[ko + i];
+        if (!std::isfinite(v) || (i > 0 && v < knots[ko + i - 1])) return EFIE_EINVAL;
+        kn.push_back(v);
+      }
+      if (knots[ko] != 0.0 || knots[ko + nk - 1] != 1.0) return EFIE_EINVAL;
+      ko += nk;
+    }
+    d.cofs = (int)(hw.size() / 4);
+    int nc = d.ncp[0] * d.ncp[1];
+    for (int i = 0; i < nc; ++i) {
+      double wt = w[co + i];
+      if (!(wt > 0.0) || !std::isfinite(wt)) return EFIE_EINVAL;
+      for (int k = 0; k < 3; ++k) {
+        double v = cp[3 * (co + i) + k];
+        if (!std::isfinite(v)) return EFIE_EINVAL;
+        hw.push_back(wt * v);
+      }
+      hw.push_back(wt);
+    }
+    co += nc;
+  }
+  release_device(c);
+  c->setup_done = false;
+  c->np = n_patches;
+  c->patches = P;
+  c->knots = kn;
+  c->cpw = hw;
+  EFIE_TRY(dalloc(c, &c->d_patches, P.size()));
+  EFIE_TRY(dalloc(c, &c->d_knots, kn.size()));
+  EFIE_TRY(dalloc(c, &c->d_cpw, hw.size() / 4));
+  EFIE_CUDA(cudaMemcpy(c->d_patches, P.data(), sizeof(PatchDesc) * P.size(), cudaMemcpyHostToDevice));
+  EFIE_CUDA(cudaMemcpy(c->d_knots, kn.data(), 8 * kn.size(), cudaMemcpyHostToDevice));
+  EFIE_CUDA(cudaMemcpy(c->d_cpw, hw.data(), 8 * hw.size(), cudaMemcpyHostToDevice));
+  EFIE_CUDA(cudaDeviceSynchronize());
+  c->have_geometry = true;
+  return EFIE_OK;
+}
+
+efie_status efie_setup(efie_ctx *ctx) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c) return EFIE_EINVAL;
+  if (!c->have_geometry) return EFIE_ESTATE;
+  cudaSetDevice(c->device);
+  auto t0 = std::chrono::steady_clock::now();
+  const efie_options &o = c->opt;
+  c->p = o.p;
+  c->m = o.level_m;
+  c->n = 1 << c->m;
+  c->q = o.q;
+  c->q1 = o.q + 1;
+  c->nI = c->q1 * c->q1;
+  c->p1 = o.p + 1;
+  c->nb = 2 * c->p1 * c->p1;
+  c->kappa = o.kappa;
+  c->eta = o.eta;
+  c->gr = o.quad_regular > 0 ? o.quad_regular : o.p + 4;
+  c->gs = o.quad_singular > 0 ? o.quad_singular : o.p + 4;
+  c->nE = c->np * c->n * c->n;
+  c->nsup = c->nE * c->nb;
+  host_tables(c);
+
+  // interfaces, orientation, DOF map and T
+  std::vector<int> pid;
+  std::vector<double> st, X, D;
+  for (int j = 0; j < c->np; ++j)
+    for (int k = 0; k < 4; ++k)
+      for (int t = 0; t < 5; ++t) {
+        double u = t / 4.0;
+        double s1 = k == 0 ? 0.0 : (k == 1 ? 1.0 : u), s2 = k == 2 ? 0.0 : (k == 3 ? 1.0 : u);
+        pid.push_back(j);
+        st.push_back(s1);
+        st.push_back(s2);
+      }
+  EFIE_TRY(dev_eval_points(c, pid, st, X, nullptr));
+  std::vector<double> none;
+  EFIE_TRY(host_build_space(c, X, none));
+  // outward orientation: enclosed volume (1/3) int x . (d1F x d2F) ds > 0
+  {
+    pid.clear();
+    st.clear();
+    std::vector<double> gx, gw;
+    gauss_legendre01(8, gx, gw);
+    for (int j = 0; j < c->np; ++j)
+      for (int a = 0; a < 8; ++a)
+        for (int b = 0; b < 8; ++b) {
+          pid.push_back(j);
+          st.push_back(gx[a]);
+          st.push_back(gx[b]);
+        }
+    EFIE_TRY(dev_eval_points(c, pid, st, X, &D));
+    double vol = 0.0;
+    for (size_t i = 0; i < pid.size(); ++i) {
+      const double *x = &X[3 * i], *d1 = &D[6 * i], *d2 = &D[6 * i + 3];
+      double nx = d1[1] * d2[2] - d1[2] * d2[1], ny = d1[2] * d2[0] - d1[0] * d2[2], nz = d1[0] * d2[1] - d1[1] * d2[0];
+      int a = (int)((i / 8) % 8), b = (int)(i % 8);
+      vol += gw[a] * gw[b] * (x[0] * nx + x[1] * ny + x[2] * nz) / 3.0;
+    }
+    if (!(vol > 0.0)) {
+      c->err = "patches are oriented inwards (d1F x d2F must point out of the enclosed volume)";
+      return EFIE_EGEOMETRY;
+    }
+  }
+  // vertex grid of every patch, for the classification of touching element pairs
+  pid.clear();
+  st.clear();
+  for (int j = 0; j < c->np; ++j)
+    for (int v2 = 0; v2 <= c->n; ++v2)
+      for (int v1 = 0; v1 <= c->n; ++v1) {
+        pid.push_back(j);
+        st.push_back((double)v1 / c->n);
+        st.push_back((double)v2 / c->n);
+      }
+  std::vector<double> corners;
+  EFIE_TRY(dev_eval_points(c, pid, st, corners, nullptr));
+
+  // cluster tree, geometry at the interpolation nodes, block-cluster tree
+  c->lev_off.assign(c->m + 2, 0);
+  for (int l = 0; l <= c->m; ++l) c->lev_off[l + 1] = c->lev_off[l] + c->np * (1 << (2 * l));
+  c->ncl = c->lev_off[c->m + 1];
+  EFIE_TRY(dev_cluster_geometry(c));
+  EFIE_TRY(host_build_trees(c));
+
+  // near field
+  std::vector<NearPair> pairs;
+  std::vector<int> mirror;
+  EFIE_TRY(host_classify_near(c, corners, pairs, mirror));
+  EFIE_TRY(dev_near_quadrature(c, pairs, mirror));
+  EFIE_TRY(dev_alloc_work(c));
+  EFIE_CUDA(cudaStreamSynchronize(c->stream));
+  c->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  c->setup_done = true;
+  return EFIE_OK;
+}
+
+efie_status efie_num_dofs(const efie_ctx *ctx, int64_t *n) {
+  const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+  if (!c || !n) return EFIE_EINVAL;
+  if (!c->setup_done) return EFIE_ESTATE;
+  *n = c->ndof;
+  return EFIE_OK;
+}
+
+efie_status efie_block_counts(const efie_ctx *ctx, int64_t *nfar, int64_t *nnear, int64_t *ncl, int64_t *nsup) {
+  const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+  if (!c) return EFIE_EINVAL;
+  if (!c->setup_done) return EFIE_ESTATE;
+  if (nfar) *nfar = c->nfar;
+  if (nnear) *nnear = c->nnear;
+  if (ncl) *ncl = c->ncl;
+  if (nsup) *nsup = c->nsup;
+  return EFIE_OK;
+}
+
+efie_status efie_export_blocks(const efie_ctx *ctx, int *far, int *near) {
+  const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+  if (!c) return EFIE_EINVAL;
+  if (!c->setup_done) return EFIE_ESTATE;
+  if (far) std::memcpy(far, c->far.data(), 4 * c->far.size());
+  if (near) std::memcpy(near, c->nearl.data(), 4 * c->nearl.size());
+  return EFIE_OK;
+}
+
+efie_status efie_export_near_blocks(efie_ctx *ctx, double *blocks) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c || !blocks) return EFIE_EINVAL;
+  if (!c->setup_done) return EFIE_ESTATE;
+  cudaSetDevice(c->device);
+  const size_t nb2 = (size_t)c->nb * c->nb;
+  std::vector<double2> tmp(nb2 * c->nnear);
+  EFIE_CUDA(cudaMemcpy(tmp.data(), c->d_nblk, 16 * tmp.size(), cudaMemcpyDeviceToHost));
+  double2 *out = reinterpret_cast<double2 *>(blocks);
+  for (int at = 0; at < c->nnear; ++at) {
+    int k = c->near_perm[at];
+    for (int cc = 0; cc < c->nb; ++cc)
+      for (int rr = 0; rr < c->nb; ++rr) out[(size_t)k * nb2 + rr * c->nb + cc] = tmp[(size_t)at * nb2 + cc * c->nb + rr];
+  }
+  return EFIE_OK;
+}
+
+efie_status efie_matvec(efie_ctx *ctx, int nrhs, const double *x, double *y, int ptr_kind) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c || nrhs < 0 || (nrhs > 0 && (!x || !y))) return EFIE_EINVAL;
+  if (ptr_kind != EFIE_PTR_HOST && ptr_kind != EFIE_PTR_DEVICE) return EFIE_EINVAL;
+  if (!c->setup_done) return EFIE_ESTATE;
+  cudaSetDevice(c->device);
+  const size_t N = c->ndof;
+  for (int r = 0; r < nrhs; ++r) {
+    const double2 *xr = reinterpret_cast<const double2 *>(x) + r * N;
+    double2 *yr = reinterpret_cast<double2 *>(y) + r * N;
+    if (ptr_kind == EFIE_PTR_HOST) {
+      EFIE_CUDA(cudaMemcpyAsync(c->d_x, xr, 16 * N, cudaMemcpyHostToDevice, c->stream));
+      EFIE_TRY(dev_matvec(c, c->d_x, c->d_y));
+      EFIE_CUDA(cudaMemcpyAsync(yr, c->d_y, 16 * N, cudaMemcpyDeviceToHost, c->stream));
+    } else {
+      EFIE_TRY(dev_matvec(c, xr, yr));
+    }
+  }
+  EFIE_CUDA(cudaStreamSynchronize(c->stream));
+  if (nrhs > 0) {
+    float ms[7];
+    cudaEventElapsedTime(&ms[0], c->tm.ev[0], c->tm.ev[6]);
+    cudaEventElapsedTime(&ms[1], c->tm.ev[0], c->tm.ev[1]);
+    cudaEventElapsedTime(&ms[2], c->tm.ev[1], c->tm.ev[2]);
+    cudaEventElapsedTime(&ms[3], c->tm.ev[1], c->tm.ev[3]);
+    cudaEventElapsedTime(&ms[4], c->tm.ev[3], c->tm.ev[4]);
+    cudaEventElapsedTime(&ms[5], c->tm.ev[4], c->tm.ev[5]);
+    cudaEventElapsedTime(&ms[6], c->tm.ev[5], c->tm.ev[6]);
+    for (int i = 0; i < 7; ++i) c->last_ms[i] = ms[i];
+  }
+  return EFIE_OK;
+}
+
+efie_status efie_matvec_superspace(efie_ctx *ctx, const double *xs, double *ys, int ptr_kind) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c || !xs || !ys) return EFIE_EINVAL;
+  if (ptr_kind != EFIE_PTR_HOST && ptr_kind != EFIE_PTR_DEVICE) return EFIE_EINVAL;
+  if (!c->setup_done) return EFIE_ESTATE;
+  cudaSetDevice(c->device);
+  const size_t S = c->nsup;
+  double2 *in = c->d_xs, *out = c->d_ys;
+  double2 *tmp_in = nullptr, *tmp_out = nullptr;
+  if (ptr_kind == EFIE_PTR_HOST) {
+    EFIE_TRY(dalloc(c, &tmp_in, S));
+    EFIE_TRY(dalloc(c, &tmp_out, S));
+    EFIE_CUDA(cudaMemcpyAsync(tmp_in, xs, 16 * S, cudaMemcpyHostToDevice, c->stream));
+    in = tmp_in;
+    out = tmp_out;
+  } else {
+    in = reinterpret_cast<double2 *>(const_cast<double *>(xs));
+    out = reinterpret_cast<double2 *>(ys);
+  }
+  EFIE_TRY(dev_matvec_super(c, in, out));
+  if (ptr_kind == EFIE_PTR_HOST) EFIE_CUDA(cudaMemcpyAsync(ys, out, 16 * S, cudaMemcpyDeviceToHost, c->stream));
+  EFIE_CUDA(cudaStreamSynchronize(c->stream));
+  if (tmp_in) cudaFree(tmp_in);
+  if (tmp_out) cudaFree(tmp_out);
+  return EFIE_OK;
+}
+
+efie_status efie_rhs_plane_waves(efie_ctx *ctx, int nrhs, const double *dir, const double *pol, double *g,
+                                 int ptr_kind) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c || nrhs < 0 || (nrhs > 0 && (!dir || !pol || !g))) return EFIE_EINVAL;
+  if (ptr_kind != EFIE_PTR_HOST && ptr_kind != EFIE_PTR_DEVICE) return EFIE_EINVAL;
+  if (!c->setup_done) return EFIE_ESTATE;
+  cudaSetDevice(c->device);
+  const size_t N = c->ndof;
+  for (int r = 0; r < nrhs; ++r) {
+    double2 *gr = reinterpret_cast<double2 *>(g) + r * N;
+    double2 *dst = ptr_kind == EFIE_PTR_HOST ? c->d_y : gr;
+    EFIE_TRY(dev_rhs(c, dir + 3 * r, pol + 3 * r, dst));
+    if (ptr_kind == EFIE_PTR_HOST) EFIE_CUDA(cudaMemcpy(gr, c->d_y, 16 * N, cudaMemcpyDeviceToHost));
+  }
+  return EFIE_OK;
+}
+
+static efie_status solve_impl(Ctx *c, int nrhs, const double *b, double *x, int ptr_kind, efie_solve_info *info,
+                              const double *dir, const double *pol) {
+  const size_t N = c->ndof;
+  if (!c->d_b) EFIE_TRY(dalloc(c, &c->d_b, N));
+  efie_status result = EFIE_OK;
+  int its_max = 0, all_conv = 1;
+  double worst = 0.0;
+  auto t0 = std::chrono::steady_clock::now();
+  for (int r = 0; r < nrhs; ++r) {
+    double2 *xr = reinterpret_cast<double2 *>(x) + r * N;
+    const double2 *br = b ? reinterpret_cast<const double2 *>(b) + r * N : nullptr;
+    if (dir) {
+      EFIE_TRY(dev_rhs(c, dir + 3 * r, pol + 3 * r, c->d_b));
+    } else if (ptr_kind == EFIE_PTR_HOST) {
+      EFIE_CUDA(cudaMemcpyAsync(c->d_b, br, 16 * N, cudaMemcpyHostToDevice, c->stream));
+    } else {
+      EFIE_CUDA(cudaMemcpyAsync(c->d_b, br, 16 * N, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    double2 *dst = ptr_kind == EFIE_PTR_HOST ? c->d_x : xr;
+    int its = 0, conv = 0;
+    double res = 0.0;
+    EFIE_TRY(dev_gmres(c, c->d_b, dst, &its, &res, &conv));
+    if (ptr_kind == EFIE_PTR_HOST) {
+      EFIE_CUDA(cudaMemcpyAsync(xr, c->d_x, 16 * N, cudaMemcpyDeviceToHost, c->stream));
+      EFIE_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    its_max = std::max(its_max, its);
+    worst = std::max(worst, res);
+    if (!conv) {
+      all_conv = 0;
+      result = EFIE_NOT_CONVERGED;
+    }
+  }
+  EFIE_CUDA(cudaStreamSynchronize(c->stream));
+  c->info.iterations = its_max;
+  c->info.converged = all_conv;
+  c->info.residual = worst;
+  c->info.setup_ms = c->setup_ms;
+  c->info.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = c->info;
+  return result;
+}
+
+efie_status efie_solve(efie_ctx *ctx, int nrhs, const double *b, double *x, int ptr_kind, efie_solve_info *info) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c || nrhs < 0 || (nrhs > 0 && (!b || !x))) return EFIE_EINVAL;
+  if (ptr_kind != EFIE_PTR_HOST && ptr_kind != EFIE_PTR_DEVICE) return EFIE_EINVAL;
+  if (!c->setup_done) return EFIE_ESTATE;
+  cudaSetDevice(c->device);
+  return solve_impl(c, nrhs, b, x, ptr_kind, info, nullptr, nullptr);
+}
+
+efie_status efie_solve_plane_waves(efie_ctx *ctx, int nrhs, const double *dir, const double *pol, double *w,
+                                   int ptr_kind, efie_solve_info *info) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c || nrhs < 0 || (nrhs > 0 && (!dir || !pol || !w))) return EFIE_EINVAL;
+  if (ptr_kind != EFIE_PTR_HOST && ptr_kind != EFIE_PTR_DEVICE) return EFIE_EINVAL;
+  if (!c->setup_done) return EFIE_ESTATE;
+  cudaSetDevice(c->device);
+  return solve_impl(c, nrhs, nullptr, w, ptr_kind, info, dir, pol);
+}
+
+efie_status efie_far_field(efie_ctx *ctx, int nrhs, const double *w, int ndir, const double *dirs, double *e_inf,
+                           int ptr_kind) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c || nrhs < 0 || ndir < 0 || (nrhs > 0 && ndir > 0 && (!w || !dirs || !e_inf))) return EFIE_EINVAL;
+  if (ptr_kind != EFIE_PTR_HOST && ptr_kind != EFIE_PTR_DEVICE) return EFIE_EINVAL;
+  if (!c->setup_done) return EFIE_ESTATE;
+  if (ndir == 0 || nrhs == 0) return EFIE_OK;
+  cudaSetDevice(c->device);
+  const size_t N = c->ndof;
+  double2 *d_out = nullptr;
+  EFIE_TRY(dalloc(c, &d_out, 3 * (size_t)ndir));
+  for (int r = 0; r < nrhs; ++r) {
+    const double2 *wr = reinterpret_cast<const double2 *>(w) + r * N;
+    double2 *er = reinterpret_cast<double2 *>(e_inf) + (size_t)r * ndir * 3;
+    const double2 *src = wr;
+    if (ptr_kind == EFIE_PTR_HOST) {
+      EFIE_CUDA(cudaMemcpyAsync(c->d_x, wr, 16 * N, cudaMemcpyHostToDevice, c->stream));
+      src = c->d_x;
+    }
+    EFIE_TRY(dev_far_field(c, src, ndir, dirs, ptr_kind == EFIE_PTR_HOST ? d_out : er));
+    if (ptr_kind == EFIE_PTR_HOST) EFIE_CUDA(cudaMemcpy(er, d_out, 48 * (size_t)ndir, cudaMemcpyDeviceToHost));
+  }
+  cudaFree(d_out);
+  return EFIE_OK;
+}
+
+int efie_last_timings(const efie_ctx *ctx, double *out, int n) {
+  const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+  if (!c || !out) return 0;
+  int k = n < 7 ? n : 7;
+  for (int i = 0; i < k; ++i) out[i] = c->last_ms[i];
+  return k;
+}
+
+}  // extern "C"

@@ -1,0 +1,203 @@
+// Internal definitions of the GB300 EFIE library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/efie.h"
+
+namespace efie {
+
+constexpr int kMaxGeoDeg = 8;     // NURBS degree limit of the device evaluator
+constexpr int kMaxGeoCp = 64;     // control points per direction
+constexpr int kMaxQ1 = 17;        // q + 1 interpolation points per direction
+constexpr int kMaxP1 = 7;         // p + 1 Bernstein functions per direction
+
+// One NURBS patch as the device sees it: offsets into the packed knot and homogeneous
+// control point arrays.
+struct PatchDesc {
+  int deg[2];
+  int ncp[2];
+  int kofs[2];  // offset of the s1 / s2 knot vector in the knot array
+  int cofs;     // offset of the [ncp1][ncp0] homogeneous control net (w x, w y, w z, w)
+};
+
+// Quadrature meta data of one near-field element pair.
+struct NearPair {
+  int e, e2;    // target, source element
+  int kind;     // 0 separated, 1 common vertex, 2 common edge, 3 identical
+  int r1, r2;   // square symmetries taking the canonical Duffy coordinates to each element
+};
+
+struct Timers {
+  cudaEvent_t ev[8];
+  bool made = false;
+};
+
+// Per-level tables of the hierarchical interpolation (Sec. 4.2): constant across levels
+// because every cluster is mapped onto its own parameter box.
+struct Tables {
+  std::vector<double> xcheb;  // q+1 Chebyshev nodes on [0,1]
+  std::vector<double> M;      // [q1][p1]  int_0^1 L_m B_a
+  std::vector<double> Md;     // [q1][p1]  int_0^1 L_m B_a'
+  std::vector<double> E;      // [2][q1][q1]  E_c[m][m'] = L_m((c + x_m') / 2)
+  std::vector<double> gx, gw;  // Gauss rule of quad_regular points
+  std::vector<double> sx, sw;  // Gauss rule of quad_singular points
+};
+
+struct Ctx {
+  efie_options opt{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t stream2 = nullptr;  // near-field apply overlaps the far-field chain
+  cudaEvent_t fork = nullptr, join = nullptr;
+  bool own_stream = false;
+
+  // geometry (host copy, homogeneous control points)
+  int np = 0;
+  std::vector<PatchDesc> patches;
+  std::vector<double> knots;
+  std::vector<double> cpw;  // [..][4]
+  bool have_geometry = false;
+  PatchDesc *d_patches = nullptr;
+  double *d_knots = nullptr;
+  double4 *d_cpw = nullptr;
+
+  // discretisation
+  int p = 1, m = 0, n = 1, q = 1, q1 = 2, nI = 4, p1 = 2, nb = 8;
+  int nE = 0, nsup = 0, ndof = 0;
+  int gr = 5, gs = 5;  // Gauss orders
+  double kappa = 1.0, eta = 1.6;
+  std::vector<int> edge_nbr;  // [np*4][3]: neighbour patch, edge, reversed
+
+  // T (eq. superspace) as CSR in both directions
+  int *d_tg_ptr = nullptr, *d_tg_col = nullptr;
+  double *d_tg_val = nullptr;
+  int *d_ts_ptr = nullptr, *d_ts_col = nullptr;
+  double *d_ts_val = nullptr;
+  int nT = 0;
+
+  // clusters
+  int ncl = 0;
+  std::vector<int> lev_off;  // [m+2]
+  std::vector<double> ball;  // [ncl][4]
+  double *d_nodeX = nullptr;  // [ncl][nI][3]
+  double *d_nodeD = nullptr;  // [ncl][nI][6]  (d1F, d2F)
+  float *d_nodeXf = nullptr;  // [ncl][nI][3] offsets from the cluster centre (FP32 path)
+  double *d_center = nullptr; // [ncl][3]
+
+  // block-cluster tree (Algorithm 1)
+  std::vector<int> far;   // [nfar][3] (level, target, source)
+  std::vector<int> nearl; // [nnear][2]
+  int nfar = 0, nnear = 0;
+  int *d_far_ptr = nullptr, *d_far_src = nullptr;  // CSR by target cluster
+  int *d_m2l_targets = nullptr;
+  int n_m2l_targets = 0;
+  int *d_near_ptr = nullptr, *d_near_src = nullptr;  // CSR by target element
+  double2 *d_nblk = nullptr;  // [nnear][nb (col)][nb (row)]
+  std::vector<int> near_perm;  // CSR position -> index in nearl
+
+  // tables on the device
+  double *d_M = nullptr, *d_Md = nullptr, *d_E = nullptr;
+  float *d_Mf = nullptr, *d_Mdf = nullptr, *d_Ef = nullptr;
+  Tables tab;
+
+  // work vectors (FP64)
+  double2 *d_x = nullptr, *d_y = nullptr, *d_xs = nullptr, *d_ys = nullptr, *d_ysn = nullptr;
+  double2 *d_mom = nullptr;  // [ncl][3][nI]
+  double2 *d_src = nullptr;  // [ncl][4][nI]
+  double2 *d_acc = nullptr;  // [ncl][4][nI]
+  double2 *d_loc = nullptr;  // [ncl][3][nI]
+  // work vectors (FP32 path)
+  float2 *d_momf = nullptr, *d_srcf = nullptr, *d_locf = nullptr;
+  double2 *d_accm = nullptr;  // mixed path accumulates each pair's FP32 sum in FP64
+
+  // GMRES
+  int kr = 0;  // allocated restart length
+  double2 *d_V = nullptr;     // [kr+1][ndof]
+  double2 *d_H = nullptr;     // [kr+1][kr]
+  double2 *d_h = nullptr;     // [kr+1]
+  double2 *d_h2 = nullptr;    // [kr+1]
+  double2 *d_part = nullptr;  // partial dot products
+  double *d_gs = nullptr;     // Givens / residual state
+  double2 *d_w = nullptr, *d_r = nullptr, *d_b = nullptr, *d_sol = nullptr;
+  double *h_res = nullptr;    // pinned host mirror of the residual estimate
+  int part_cap = 0;
+
+  bool setup_done = false;
+  Timers tm;
+  float last_ms[7] = {0, 0, 0, 0, 0, 0, 0};
+  double setup_ms = 0.0;
+  efie_solve_info info{};
+  std::string err;
+};
+
+// helpers implemented in the .cu / .cpp files
+efie_status host_build_space(Ctx *c, const std::vector<double> &edge_pts, const std::vector<double> &corner_pts);
+efie_status host_build_trees(Ctx *c);
+efie_status host_classify_near(Ctx *c, const std::vector<double> &corner_pts, std::vector<NearPair> &pairs,
+                               std::vector<int> &mirror);
+void host_tables(Ctx *c);
+void gauss_legendre01(int g, std::vector<double> &x, std::vector<double> &w);
+
+// device-side phases
+efie_status dev_eval_points(Ctx *c, const std::vector<int> &patch, const std::vector<double> &st,
+                            std::vector<double> &X, std::vector<double> *D);
+efie_status dev_cluster_geometry(Ctx *c);
+efie_status dev_near_quadrature(Ctx *c, const std::vector<NearPair> &pairs, const std::vector<int> &mirror);
+efie_status dev_matvec_super(Ctx *c, const double2 *xs, double2 *ys);  // ys = (N + F) xs
+efie_status dev_matvec(Ctx *c, const double2 *x, double2 *y);           // y = T^T (N+F) T x
+efie_status dev_rhs(Ctx *c, const double *dir, const double *pol, double2 *g);
+efie_status dev_far_field(Ctx *c, const double2 *w, int ndir, const double *dirs, double2 *out);
+efie_status dev_gmres(Ctx *c, const double2 *b, double2 *x, int *its, double *res, int *conv);
+efie_status dev_alloc_work(Ctx *c);
+
+#define EFIE_CUDA(call)                                                              \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      c->err = std::string(#call) + ": " + cudaGetErrorString(e_);                   \
+      return (e_ == cudaErrorMemoryAllocation) ? EFIE_ENOMEM : EFIE_ECUDA;           \
+    }                                                                                \
+  } while (0)
+
+#define EFIE_TRY(expr)             \
+  do {                             \
+    efie_status s_ = (expr);       \
+    if (s_ < 0) return s_;         \
+  } while (0)
+
+template <class T>
+inline efie_status dalloc(Ctx *c, T **p, size_t count) {
+  if (*p) {
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    c->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    *p = nullptr;
+    return EFIE_ENOMEM;
+  }
+  return EFIE_OK;
+}
+
+inline int morton2(int i1, int i2) {
+  int k = 0;
+  for (int b = 0; b < 15; ++b) k |= (((i1 >> b) & 1) << (2 * b)) | (((i2 >> b) & 1) << (2 * b + 1));
+  return k;
+}
+inline void unmorton2(int k, int &i1, int &i2) {
+  i1 = 0;
+  i2 = 0;
+  for (int b = 0; b < 15; ++b) {
+    i1 |= ((k >> (2 * b)) & 1) << b;
+    i2 |= ((k >> (2 * b + 1)) & 1) << b;
+  }
+}
+
+}  // namespace efie

@@ -1,0 +1,318 @@
+// Device-resident restarted GMRES (a11) for the complex symmetric EFIE system (Sec. 5: complex
+// GMRES without preconditioner, restarted every 1500 iterations).  Arnoldi by classical
+// Gram-Schmidt applied twice (CGS2) with deterministic two-stage reductions (fixed order,
+// independent of launch timing), Givens rotations and back substitution on the device.
+// Only the residual estimate (8 bytes) crosses to the host per iteration.
+#include <cmath>
+
+#include "efie_internal.h"
+
+namespace efie {
+
+constexpr int kDotThreads = 256;
+constexpr int kRowsPerThread = 4;
+constexpr int kChunk = kDotThreads * kRowsPerThread;
+constexpr int kVecPerBlock = 8;
+
+// part[i * nchunk + chunk] = sum_{t in chunk} conj(V_i[t]) w[t], i = i0 .. i0+7
+__global__ void __launch_bounds__(kDotThreads) k_dot_partial(int N, int nvec, const double2 *__restrict__ V, size_t ldv,
+                                                             const double2 *__restrict__ w, double2 *__restrict__ part,
+                                                             int nchunk) {
+  int chunk = blockIdx.x, i0 = blockIdx.y * kVecPerBlock;
+  double2 acc[kVecPerBlock];
+#pragma unroll
+  for (int v = 0; v < kVecPerBlock; ++v) acc[v] = make_double2(0.0, 0.0);
+  for (int rr = 0; rr < kRowsPerThread; ++rr) {
+    int t = chunk * kChunk + rr * kDotThreads + threadIdx.x;
+    if (t < N) {
+      double2 wt = w[t];
+#pragma unroll
+      for (int v = 0; v < kVecPerBlock; ++v) {
+        int i = i0 + v;
+        if (i < nvec) {
+          double2 a = V[(size_t)i * ldv + t];
+          acc[v].x += a.x * wt.x + a.y * wt.y;
+          acc[v].y += a.x * wt.y - a.y * wt.x;
+        }
+      }
+    }
+  }
+  __shared__ double2 red[kDotThreads / 32][kVecPerBlock];
+  int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < kVecPerBlock; ++v) {
+    double x = acc[v].x, y = acc[v].y;
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_down_sync(0xffffffffu, x, o);
+      y += __shfl_down_sync(0xffffffffu, y, o);
+    }
+    if (lane == 0) red[wp][v] = make_double2(x, y);
+  }
+  __syncthreads();
+  if (threadIdx.x < kVecPerBlock) {
+    int v = threadIdx.x, i = i0 + v;
+    double2 s = make_double2(0.0, 0.0);
+    for (int k = 0; k < kDotThreads / 32; ++k) {
+      s.x += red[k][v].x;
+      s.y += red[k][v].y;
+    }
+    if (i < nvec) part[(size_t)i * nchunk + chunk] = s;
+  }
+}
+
+// h[i] = sum over chunks (one warp per vector, fixed order)
+__global__ void k_dot_final(int nvec, int nchunk, const double2 *__restrict__ part, double2 *__restrict__ h) {
+  int i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (i >= nvec) return;
+  double x = 0.0, y = 0.0;
+  for (int k = lane; k < nchunk; k += 32) {
+    x += part[(size_t)i * nchunk + k].x;
+    y += part[(size_t)i * nchunk + k].y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_down_sync(0xffffffffu, x, o);
+    y += __shfl_down_sync(0xffffffffu, y, o);
+  }
+  if (lane == 0) h[i] = make_double2(x, y);
+}
+
+// w[t] += sgn * sum_i h[i] V_i[t]
+__global__ void k_combine(int N, int nvec, const double2 *__restrict__ V, size_t ldv, const double2 *__restrict__ h,
+                          double sgn, double2 *__restrict__ w) {
+  extern __shared__ double2 sh[];
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) sh[i] = h[i];
+  __syncthreads();
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  double x = 0.0, y = 0.0;
+  for (int i = 0; i < nvec; ++i) {
+    double2 a = V[(size_t)i * ldv + t], c = sh[i];
+    x += c.x * a.x - c.y * a.y;
+    y += c.x * a.y + c.y * a.x;
+  }
+  w[t].x += sgn * x;
+  w[t].y += sgn * y;
+}
+
+__global__ void k_scale_copy(int N, const double2 *__restrict__ w, const double *__restrict__ st, int idx,
+                             double2 *__restrict__ out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  double b = st[idx];
+  double f = b > 0.0 ? 1.0 / b : 0.0;
+  out[t] = make_double2(w[t].x * f, w[t].y * f);
+}
+
+__global__ void k_residual(int N, const double2 *__restrict__ b, double2 *__restrict__ r) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  r[t] = make_double2(b[t].x - r[t].x, b[t].y - r[t].y);
+}
+
+// Givens state layout in st: [0] beta of the new vector, [1] residual estimate,
+// [2 .. 2+kr) cs, then sn (complex) [kr][2], then g (complex) [kr+1][2].
+__device__ inline double *gs_cs(double *st) { return st + 2; }
+
+__global__ void k_givens_init(double *st, int kr, const double2 *h) {
+  // g = (||r||, 0, ...); h[0] holds ||r||^2
+  double beta = sqrt(h[0].x);
+  double *g = st + 2 + kr + 2 * kr;
+  for (int i = 0; i <= kr; ++i) {
+    g[2 * i] = 0.0;
+    g[2 * i + 1] = 0.0;
+  }
+  g[0] = beta;
+  st[0] = beta;
+  st[1] = beta;
+}
+
+// Column j of the Hessenberg matrix from the CGS2 coefficients h1 + h2 and the norm of the
+// orthogonalised vector; previous rotations, new rotation, residual estimate |g_{j+1}|.
+__global__ void k_givens_step(int j, int kr, const double2 *h1, const double2 *h2, const double2 *nrm2, double2 *H,
+                              double *st) {
+  double *cs = st + 2;
+  double *sn = st + 2 + kr;       // complex [kr]
+  double *g = st + 2 + 3 * kr;    // complex [kr+1]
+  double beta = sqrt(fmax(nrm2[0].x, 0.0));
+  for (int i = 0; i <= j; ++i) H[(size_t)i * kr + j] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
+  for (int i = 0; i < j; ++i) {
+    double2 a = H[(size_t)i * kr + j], b = H[(size_t)(i + 1) * kr + j];
+    double c = cs[i], sr = sn[2 * i], si = sn[2 * i + 1];
+    // [a; b] <- [c a + s b; -conj(s) a + c b]
+    double2 na = make_double2(c * a.x + sr * b.x - si * b.y, c * a.y + sr * b.y + si * b.x);
+    double2 nb = make_double2(-(sr * a.x + si * a.y) + c * b.x, -(sr * a.y - si * a.x) + c * b.y);
+    H[(size_t)i * kr + j] = na;
+    H[(size_t)(i + 1) * kr + j] = nb;
+  }
+  double2 a = H[(size_t)j * kr + j];
+  double aa = hypot(a.x, a.y), tt = hypot(aa, beta);
+  double c, sr, si;
+  if (aa == 0.0) {
+    c = 0.0; sr = 1.0; si = 0.0;
+  } else {
+    c = aa / tt;
+    sr = (a.x / aa) * beta / tt;
+    si = (a.y / aa) * beta / tt;
+  }
+  cs[j] = c;
+  sn[2 * j] = sr;
+  sn[2 * j + 1] = si;
+  H[(size_t)j * kr + j] = make_double2(c * a.x + sr * beta, c * a.y + si * beta);
+  double gr = g[2 * j], gi = g[2 * j + 1];
+  g[2 * (j + 1)] = -(sr * gr + si * gi);
+  g[2 * (j + 1) + 1] = -(sr * gi - si * gr);
+  g[2 * j] = c * gr;
+  g[2 * j + 1] = c * gi;
+  st[0] = beta;
+  st[1] = hypot(g[2 * (j + 1)], g[2 * (j + 1) + 1]);
+}
+
+// y = H(0:jd, 0:jd)^{-1} g(0:jd), one warp: row sums in parallel, rows in sequence.
+__global__ void k_backsolve(int jd, int kr, const double2 *H, const double *st, double2 *y) {
+  const double *g = st + 2 + 3 * kr;
+  int lane = threadIdx.x;
+  for (int i = jd - 1; i >= 0; --i) {
+    double x = 0.0, z = 0.0;
+    for (int t = i + 1 + lane; t < jd; t += 32) {
+      double2 hh = H[(size_t)i * kr + t], yy = y[t];
+      x += hh.x * yy.x - hh.y * yy.y;
+      z += hh.x * yy.y + hh.y * yy.x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_down_sync(0xffffffffu, x, o);
+      z += __shfl_down_sync(0xffffffffu, z, o);
+    }
+    if (lane == 0) {
+      double sr = g[2 * i] - x, si = g[2 * i + 1] - z;
+      double2 d = H[(size_t)i * kr + i];
+      double den = d.x * d.x + d.y * d.y;
+      y[i] = make_double2((sr * d.x + si * d.y) / den, (si * d.x - sr * d.y) / den);
+    }
+    __syncwarp();
+  }
+}
+
+static efie_status ensure_part(Ctx *c, int N, int nvec) {
+  int nchunk = (N + kChunk - 1) / kChunk;
+  int need = nchunk * (nvec + kVecPerBlock);
+  if (need > c->part_cap) {
+    EFIE_TRY(dalloc(c, &c->d_part, (size_t)need));
+    c->part_cap = need;
+  }
+  return EFIE_OK;
+}
+
+// h[0..nvec) = V^H w (V columns of stride ldv)
+static efie_status dots(Ctx *c, int N, int nvec, const double2 *V, size_t ldv, const double2 *w, double2 *h) {
+  EFIE_TRY(ensure_part(c, N, nvec));
+  int nchunk = (N + kChunk - 1) / kChunk;
+  dim3 grid(nchunk, (nvec + kVecPerBlock - 1) / kVecPerBlock);
+  k_dot_partial<<<grid, kDotThreads, 0, c->stream>>>(N, nvec, V, ldv, w, c->d_part, nchunk);
+  k_dot_final<<<(nvec + 7) / 8, 256, 0, c->stream>>>(nvec, nchunk, c->d_part, h);
+  EFIE_CUDA(cudaGetLastError());
+  return EFIE_OK;
+}
+
+efie_status dev_gmres(Ctx *c, const double2 *b, double2 *x, int *its_out, double *res_out, int *conv_out) {
+  const int N = c->ndof;
+  const int kr = std::max(1, std::min(c->opt.gmres_restart, c->opt.gmres_maxit));
+  cudaStream_t st = c->stream;
+  if (kr != c->kr) {
+    EFIE_TRY(dalloc(c, &c->d_V, (size_t)(kr + 1) * N));
+    EFIE_TRY(dalloc(c, &c->d_H, (size_t)(kr + 1) * kr));
+    EFIE_TRY(dalloc(c, &c->d_h, (size_t)kr + 1));
+    EFIE_TRY(dalloc(c, &c->d_h2, (size_t)kr + 1));
+    EFIE_TRY(dalloc(c, &c->d_gs, (size_t)2 + 5 * kr + 2));
+    c->kr = kr;
+  }
+  if (!c->d_w) {
+    EFIE_TRY(dalloc(c, &c->d_w, N));
+    EFIE_TRY(dalloc(c, &c->d_r, N));
+    EFIE_TRY(dalloc(c, &c->d_sol, (size_t)kr + 1));
+  }
+  if (!c->h_res) EFIE_CUDA(cudaMallocHost((void **)&c->h_res, 4 * sizeof(double)));
+  double2 *V = c->d_V;
+  const int blk = 256, grid = (N + blk - 1) / blk;
+  // ||b||
+  EFIE_TRY(dots(c, N, 1, b, N, b, c->d_h));
+  EFIE_CUDA(cudaMemcpyAsync(c->h_res, c->d_h, sizeof(double2), cudaMemcpyDeviceToHost, st));
+  EFIE_CUDA(cudaStreamSynchronize(st));
+  const double bn = std::sqrt(std::max(c->h_res[0], 0.0));
+  const double target = c->opt.tol_is_relative ? c->opt.gmres_tol * bn : c->opt.gmres_tol;
+  EFIE_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * N, st));
+  int its = 0, conv = 0;
+  double res = bn;
+  if (bn == 0.0) conv = 1;
+  bool first = true;
+  while (!conv && its < c->opt.gmres_maxit) {
+    // r = b - A x
+    if (first) {
+      EFIE_CUDA(cudaMemcpyAsync(c->d_r, b, sizeof(double2) * N, cudaMemcpyDeviceToDevice, st));
+    } else {
+      EFIE_TRY(dev_matvec(c, x, c->d_r));
+      k_residual<<<grid, blk, 0, st>>>(N, b, c->d_r);
+    }
+    first = false;
+    EFIE_TRY(dots(c, N, 1, c->d_r, N, c->d_r, c->d_h));
+    k_givens_init<<<1, 1, 0, st>>>(c->d_gs, kr, c->d_h);
+    k_scale_copy<<<grid, blk, 0, st>>>(N, c->d_r, c->d_gs, 0, V);
+    EFIE_CUDA(cudaMemcpyAsync(c->h_res, c->d_gs, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    EFIE_CUDA(cudaStreamSynchronize(st));
+    res = c->h_res[1];
+    if (res <= target) {
+      conv = 1;
+      break;
+    }
+    int jd = 0;
+    for (int j = 0; j < kr && its < c->opt.gmres_maxit; ++j) {
+      double2 *vj = V + (size_t)j * N;
+      EFIE_TRY(dev_matvec(c, vj, c->d_w));
+      ++its;
+      // CGS2
+      EFIE_TRY(dots(c, N, j + 1, V, N, c->d_w, c->d_h));
+      k_combine<<<grid, blk, sizeof(double2) * (j + 1), st>>>(N, j + 1, V, N, c->d_h, -1.0, c->d_w);
+      EFIE_TRY(dots(c, N, j + 1, V, N, c->d_w, c->d_h2));
+      k_combine<<<grid, blk, sizeof(double2) * (j + 1), st>>>(N, j + 1, V, N, c->d_h2, -1.0, c->d_w);
+      EFIE_TRY(dots(c, N, 1, c->d_w, N, c->d_w, c->d_h2 + kr));
+      k_givens_step<<<1, 1, 0, st>>>(j, kr, c->d_h, c->d_h2, c->d_h2 + kr, c->d_H, c->d_gs);
+      k_scale_copy<<<grid, blk, 0, st>>>(N, c->d_w, c->d_gs, 0, V + (size_t)(j + 1) * N);
+      EFIE_CUDA(cudaGetLastError());
+      EFIE_CUDA(cudaMemcpyAsync(c->h_res, c->d_gs, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      EFIE_CUDA(cudaStreamSynchronize(st));
+      res = c->h_res[1];
+      jd = j + 1;
+      if (res <= target || !(res == res)) break;
+    }
+    if (jd > 0) {
+      k_backsolve<<<1, 32, 0, st>>>(jd, kr, c->d_H, c->d_gs, c->d_sol);
+      k_combine<<<grid, blk, sizeof(double2) * jd, st>>>(N, jd, V, N, c->d_sol, 1.0, x);
+      EFIE_CUDA(cudaGetLastError());
+    }
+    if (res <= target) {
+      // confirm with the true residual
+      EFIE_TRY(dev_matvec(c, x, c->d_r));
+      k_residual<<<grid, blk, 0, st>>>(N, b, c->d_r);
+      EFIE_TRY(dots(c, N, 1, c->d_r, N, c->d_r, c->d_h));
+      EFIE_CUDA(cudaMemcpyAsync(c->h_res, c->d_h, sizeof(double2), cudaMemcpyDeviceToHost, st));
+      EFIE_CUDA(cudaStreamSynchronize(st));
+      res = std::sqrt(std::max(c->h_res[0], 0.0));
+      if (res <= target * 1.05) conv = 1;
+      first = false;
+    }
+    if (!(res == res)) break;
+  }
+  *its_out = its;
+  *res_out = c->opt.tol_is_relative ? (bn > 0 ? res / bn : 0.0) : res;
+  *conv_out = conv;
+  return EFIE_OK;
+}
+
+efie_status dev_norms(Ctx *c, int N, const double2 *v, double *out) {
+  EFIE_TRY(dots(c, N, 1, v, N, v, c->d_h));
+  EFIE_CUDA(cudaMemcpyAsync(c->h_res, c->d_h, sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+  EFIE_CUDA(cudaStreamSynchronize(c->stream));
+  *out = std::sqrt(std::max(c->h_res[0], 0.0));
+  return EFIE_OK;
+}
+
+}  // namespace efie

@@ -1,0 +1,368 @@
+// Near field (a2, a9): element-pair blocks of eq. Vkh for the non-admissible leaf pairs of
+// Algorithm 1, computed on the device in FP64 with tensor Gauss rules for separated pairs
+// and the Sauter-Schwab singularity-removing substitutions [SS97] for touching pairs
+// (identical: 8 Duffy parts, common edge: 6, common vertex: 4), and their application
+// y*_e = sum_{e'} N_{e e'} x*_{e'} as an HBM-streaming block-sparse product.
+#include <cmath>
+
+#include "geom.cuh"
+
+namespace efie {
+
+constexpr int kQC = 32;          // quadrature points staged per chunk
+constexpr int kQuadThreads = 256;
+
+struct QuadArgs {
+  const PatchDesc *patches;
+  const double *knots;
+  const double4 *cpw;
+  const NearPair *pairs;
+  const int *todo;   // indices of the pairs computed here (the others are mirrored)
+  const int *slot;   // pair index -> position of its block in the CSR order of the apply
+  int ntodo;
+  int n, p, gr, gs;
+  const double *rx, *rw, *sx, *sw;  // Gauss rules on [0,1]
+  double kappa, h;
+  double2 *blocks;   // [nnear][nb col][nb row]
+};
+
+__device__ inline void sym_apply(int code, double u0, double u1, double &a, double &b) {
+  a = (code & 1) ? u1 : u0;
+  b = (code & 1) ? u0 : u1;
+  if (code & 2) a = 1.0 - a;
+  if (code & 4) b = 1.0 - b;
+}
+
+// Canonical coordinates (s_hat, t_hat) and weight of quadrature point k of a pair.
+__device__ inline void canonical_point(int kind, int g, const double *x, const double *w, int k, double sh[2],
+                                       double th[2], double &W) {
+  int g2 = g * g, g4 = g2 * g2;
+  int part = k / g4, rem = k - part * g4;
+  int i0 = rem / (g2 * g), i1 = (rem / g2) % g, i2 = (rem / g) % g, i3 = rem % g;
+  W = w[i0] * w[i1] * w[i2] * w[i3];
+  double a = x[i0], b = x[i1], c = x[i2], d = x[i3];
+  if (kind == 0) {
+    sh[0] = a; sh[1] = b; th[0] = c; th[1] = d;
+  } else if (kind == 3) {
+    // identical: relative coordinates in one of 4 quadrants, split into 2 triangles
+    int sgn0 = (part & 1) ? -1 : 1, sgn1 = (part & 2) ? -1 : 1;
+    double z0 = (part >> 2) == 0 ? a : a * b;
+    double z1 = (part >> 2) == 0 ? a * b : a;
+    sh[0] = (sgn0 < 0 ? z0 : 0.0) + (1.0 - z0) * c;
+    sh[1] = (sgn1 < 0 ? z1 : 0.0) + (1.0 - z1) * d;
+    th[0] = sh[0] + sgn0 * z0;
+    th[1] = sh[1] + sgn1 * z1;
+    W *= a * (1.0 - z0) * (1.0 - z1);
+  } else if (kind == 2) {
+    // common edge {x2 = 0}: singular coordinates (|z1|, s2, t2), 3 pyramids x 2 signs
+    int sgn = (part & 1) ? -1 : 1, pyr = part >> 1;
+    double z, s2, t2;
+    if (pyr == 0) { z = a; s2 = a * b; t2 = a * c; }
+    else if (pyr == 1) { s2 = a; z = a * b; t2 = a * c; }
+    else { t2 = a; z = a * b; s2 = a * c; }
+    sh[0] = (sgn < 0 ? z : 0.0) + (1.0 - z) * d;
+    th[0] = sh[0] + sgn * z;
+    sh[1] = s2;
+    th[1] = t2;
+    W *= a * a * (1.0 - z);
+  } else {
+    // common vertex at the origin: 4 pyramids by the largest coordinate
+    double v[4];
+    double e[3] = {b, c, d};
+    int t = 0;
+    for (int q = 0; q < 4; ++q) v[q] = (q == part) ? a : a * e[t++];
+    sh[0] = v[0]; sh[1] = v[1]; th[0] = v[2]; th[1] = v[3];
+    W *= a * a * a;
+  }
+}
+
+// One block per element pair.  Each chunk of kQC points: threads [0, kQC) evaluate the
+// target element, [kQC, 2 kQC) the source element, then every thread accumulates its
+// block entries: B[r][c] += G w (sum_k U_k[r] V_k[c]) with U_k = h^2 d_alpha F_k psi_r
+// (k < 3), U_3 = h d_alpha psi_r, V_3 = -kappa^-2 h d_beta psi_c.
+template <int P>
+__global__ void __launch_bounds__(kQuadThreads) k_near_quad(QuadArgs A) {
+  constexpr int P1 = P + 1, NB = 2 * P1 * P1, NB2 = NB * NB;
+  constexpr int EPT = (NB2 + kQuadThreads - 1) / kQuadThreads;
+  extern __shared__ double sm[];
+  double *U = sm;                       // [kQC][4][NB]
+  double *V = U + kQC * 4 * NB;         // [kQC][4][NB]
+  double *XY = V + kQC * 4 * NB;        // [2][kQC][3]
+  double *GW = XY + 2 * kQC * 3;        // [kQC][2]
+  double *wts = GW + 2 * kQC;           // [kQC]
+  int pi = blockIdx.x;
+  if (pi >= A.ntodo) return;
+  const NearPair pr = A.pairs[A.todo[pi]];
+  const int n = A.n, n2 = n * n;
+  const int g = pr.kind == 0 ? A.gr : A.gs;
+  const double *gx = pr.kind == 0 ? A.rx : A.sx;
+  const double *gw = pr.kind == 0 ? A.rw : A.sw;
+  const int parts = pr.kind == 0 ? 1 : (pr.kind == 3 ? 8 : (pr.kind == 2 ? 6 : 4));
+  const int nq = parts * g * g * g * g;
+  const double h = A.h, h2 = h * h, ik2 = 1.0 / (A.kappa * A.kappa);
+
+  // element placement
+  int ej = pr.e / n2, eK = pr.e % n2, fj = pr.e2 / n2, fK = pr.e2 % n2;
+  int ea = 0, eb = 0, fa = 0, fb = 0;
+  for (int bt = 0; bt < 15; ++bt) {
+    ea |= ((eK >> (2 * bt)) & 1) << bt;
+    eb |= ((eK >> (2 * bt + 1)) & 1) << bt;
+    fa |= ((fK >> (2 * bt)) & 1) << bt;
+    fb |= ((fK >> (2 * bt + 1)) & 1) << bt;
+  }
+
+  double2 acc[EPT];
+#pragma unroll
+  for (int t = 0; t < EPT; ++t) acc[t] = make_double2(0.0, 0.0);
+
+  for (int q0 = 0; q0 < nq; q0 += kQC) {
+    int tid = threadIdx.x;
+    if (tid < 2 * kQC) {
+      int side = tid / kQC, ql = tid % kQC, k = q0 + ql;
+      double *Us = side == 0 ? U : V;
+      if (k < nq) {
+        double sh[2], th[2], W;
+        canonical_point(pr.kind, g, gx, gw, k, sh, th, W);
+        double sg0, sg1;
+        int code = side == 0 ? pr.r1 : pr.r2;
+        sym_apply(code, side == 0 ? sh[0] : th[0], side == 0 ? sh[1] : th[1], sg0, sg1);
+        int pj = side == 0 ? ej : fj;
+        int ia = side == 0 ? ea : fa, ib = side == 0 ? eb : fb;
+        double X[3], D1[3], D2[3];
+        dev_patch_eval(A.patches[pj], A.knots, A.cpw, (ia + sg0) * h, (ib + sg1) * h, X, D1, D2);
+        double B0[kMaxP1], dB0[kMaxP1], B1[kMaxP1], dB1[kMaxP1];
+        dev_bernstein(P, sg0, B0, dB0);
+        dev_bernstein(P, sg1, B1, dB1);
+        double f3 = side == 0 ? h : -ik2 * h;
+        for (int al = 0; al < 2; ++al) {
+          const double *D = al == 0 ? D1 : D2;
+          for (int b = 0; b < P1; ++b)
+            for (int a = 0; a < P1; ++a) {
+              int r = (al * P1 + b) * P1 + a;
+              double ps = B0[a] * B1[b];
+              double dps = al == 0 ? dB0[a] * B1[b] : B0[a] * dB1[b];
+              Us[(ql * 4 + 0) * NB + r] = h2 * D[0] * ps;
+              Us[(ql * 4 + 1) * NB + r] = h2 * D[1] * ps;
+              Us[(ql * 4 + 2) * NB + r] = h2 * D[2] * ps;
+              Us[(ql * 4 + 3) * NB + r] = f3 * dps;
+            }
+        }
+        XY[(side * kQC + ql) * 3 + 0] = X[0];
+        XY[(side * kQC + ql) * 3 + 1] = X[1];
+        XY[(side * kQC + ql) * 3 + 2] = X[2];
+        if (side == 0) wts[ql] = W;
+      } else {
+        for (int r = 0; r < 4 * NB; ++r) Us[ql * 4 * NB + r] = 0.0;
+        XY[(side * kQC + ql) * 3 + 0] = 0.0;
+        XY[(side * kQC + ql) * 3 + 1] = 0.0;
+        XY[(side * kQC + ql) * 3 + 2] = (double)side;  // dummy pair at distance 1; weight 0
+        if (side == 0) wts[ql] = 0.0;
+      }
+    }
+    __syncthreads();
+    if (tid < kQC) {
+      double dx = XY[tid * 3] - XY[(kQC + tid) * 3];
+      double dy = XY[tid * 3 + 1] - XY[(kQC + tid) * 3 + 1];
+      double dz = XY[tid * 3 + 2] - XY[(kQC + tid) * 3 + 2];
+      double r = sqrt(dx * dx + dy * dy + dz * dz);
+      double sn, cs;
+      sincos(A.kappa * r, &sn, &cs);
+      double f = wts[tid] / (4.0 * M_PI * r);
+      GW[2 * tid] = f * cs;
+      GW[2 * tid + 1] = f * sn;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < EPT; ++t) {
+      int idx = tid + t * kQuadThreads;
+      if (idx < NB2) {
+        int cc = idx / NB, rr = idx % NB;  // column-major block entry (rr, cc)
+        double sre = 0.0, sim = 0.0;
+        for (int ql = 0; ql < kQC; ++ql) {
+          const double *u = U + ql * 4 * NB, *v = V + ql * 4 * NB;
+          double s = u[rr] * v[cc] + u[NB + rr] * v[NB + cc] + u[2 * NB + rr] * v[2 * NB + cc] +
+                     u[3 * NB + rr] * v[3 * NB + cc];
+          sre += GW[2 * ql] * s;
+          sim += GW[2 * ql + 1] * s;
+        }
+        acc[t].x += sre;
+        acc[t].y += sim;
+      }
+    }
+    __syncthreads();
+  }
+  double2 *out = A.blocks + (size_t)A.slot[A.todo[pi]] * NB2;
+#pragma unroll
+  for (int t = 0; t < EPT; ++t) {
+    int idx = threadIdx.x + t * kQuadThreads;
+    if (idx < NB2) out[idx] = acc[t];
+  }
+}
+
+// B(e2, e) = B(e, e2)^T for the pairs that were not integrated directly.
+__global__ void k_near_mirror(int nb, const int *todo_m, const int *src_of, const int *slot, int nm,
+                              double2 *blocks) {
+  int nb2 = nb * nb;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)nm * nb2) return;
+  int k = (int)(t / nb2), idx = (int)(t % nb2);
+  int cc = idx / nb, rr = idx % nb;
+  int dst = slot[todo_m[k]], src = slot[src_of[k]];
+  blocks[(size_t)dst * nb2 + cc * nb + rr] = blocks[(size_t)src * nb2 + rr * nb + cc];
+}
+
+efie_status dev_near_quadrature(Ctx *c, const std::vector<NearPair> &pairs, const std::vector<int> &mirror) {
+  if (c->nnear == 0) return EFIE_OK;
+  const int nb = c->nb;
+  std::vector<int> todo, todo_m, src_of;
+  for (int k = 0; k < c->nnear; ++k) {
+    if (pairs[k].e <= pairs[k].e2) {
+      todo.push_back(k);
+    } else {
+      todo_m.push_back(k);
+      src_of.push_back(mirror[k]);
+    }
+  }
+  NearPair *d_pairs = nullptr;
+  int *d_todo = nullptr, *d_todo_m = nullptr, *d_src_of = nullptr, *d_slot = nullptr;
+  std::vector<int> slot(c->nnear);
+  for (int at = 0; at < c->nnear; ++at) slot[c->near_perm[at]] = at;
+  double *d_rule = nullptr;
+  EFIE_TRY(dalloc(c, &d_pairs, pairs.size()));
+  EFIE_TRY(dalloc(c, &d_todo, todo.size()));
+  EFIE_TRY(dalloc(c, &d_todo_m, todo_m.size()));
+  EFIE_TRY(dalloc(c, &d_src_of, src_of.size()));
+  EFIE_TRY(dalloc(c, &d_rule, 2 * (size_t)(c->gr + c->gs)));
+  EFIE_TRY(dalloc(c, &d_slot, slot.size()));
+  EFIE_CUDA(cudaMemcpy(d_slot, slot.data(), 4 * slot.size(), cudaMemcpyHostToDevice));
+  EFIE_CUDA(cudaMemcpy(d_pairs, pairs.data(), sizeof(NearPair) * pairs.size(), cudaMemcpyHostToDevice));
+  EFIE_CUDA(cudaMemcpy(d_todo, todo.data(), 4 * todo.size(), cudaMemcpyHostToDevice));
+  if (!todo_m.empty()) {
+    EFIE_CUDA(cudaMemcpy(d_todo_m, todo_m.data(), 4 * todo_m.size(), cudaMemcpyHostToDevice));
+    EFIE_CUDA(cudaMemcpy(d_src_of, src_of.data(), 4 * src_of.size(), cudaMemcpyHostToDevice));
+  }
+  std::vector<double> rule;
+  rule.insert(rule.end(), c->tab.gx.begin(), c->tab.gx.end());
+  rule.insert(rule.end(), c->tab.gw.begin(), c->tab.gw.end());
+  rule.insert(rule.end(), c->tab.sx.begin(), c->tab.sx.end());
+  rule.insert(rule.end(), c->tab.sw.begin(), c->tab.sw.end());
+  EFIE_CUDA(cudaMemcpy(d_rule, rule.data(), 8 * rule.size(), cudaMemcpyHostToDevice));
+  EFIE_TRY(dalloc(c, &c->d_nblk, (size_t)c->nnear * nb * nb));
+  EFIE_CUDA(cudaDeviceSynchronize());  // pageable uploads complete before stream work reads them
+
+  QuadArgs A;
+  A.patches = c->d_patches;
+  A.knots = c->d_knots;
+  A.cpw = c->d_cpw;
+  A.pairs = d_pairs;
+  A.todo = d_todo;
+  A.slot = d_slot;
+  A.ntodo = (int)todo.size();
+  A.n = c->n;
+  A.p = c->p;
+  A.gr = c->gr;
+  A.gs = c->gs;
+  A.rx = d_rule;
+  A.rw = d_rule + c->gr;
+  A.sx = d_rule + 2 * c->gr;
+  A.sw = d_rule + 2 * c->gr + c->gs;
+  A.kappa = c->kappa;
+  A.h = 1.0 / c->n;
+  A.blocks = c->d_nblk;
+  size_t smem = sizeof(double) * (2 * kQC * 4 * (size_t)nb + 2 * kQC * 3 + 2 * kQC + kQC);
+  switch (c->p) {
+#define EFIE_QUAD_CASE(PP)                                                                          \
+  case PP:                                                                                          \
+    EFIE_CUDA(cudaFuncSetAttribute(k_near_quad<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                   (int)smem));                                                    \
+    k_near_quad<PP><<<A.ntodo, kQuadThreads, smem, c->stream>>>(A);                                 \
+    break;
+    EFIE_QUAD_CASE(1)
+    EFIE_QUAD_CASE(2)
+    EFIE_QUAD_CASE(3)
+    EFIE_QUAD_CASE(4)
+#undef EFIE_QUAD_CASE
+    default:
+      c->err = "device near-field quadrature supports 1 <= p <= 4";
+      return EFIE_EINVAL;
+  }
+  EFIE_CUDA(cudaGetLastError());
+  if (!todo_m.empty()) {
+    long long tot = (long long)todo_m.size() * nb * nb;
+    k_near_mirror<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(nb, d_todo_m, d_src_of, d_slot,
+                                                                       (int)todo_m.size(), c->d_nblk);
+    EFIE_CUDA(cudaGetLastError());
+  }
+  EFIE_CUDA(cudaStreamSynchronize(c->stream));
+  cudaFree(d_pairs);
+  cudaFree(d_todo);
+  cudaFree(d_todo_m);
+  cudaFree(d_src_of);
+  cudaFree(d_rule);
+  cudaFree(d_slot);
+  return EFIE_OK;
+}
+
+// y*_e = sum over near sources e' of N_{e e'} x*_{e'}; one warp per target element, lane r
+// owns rows r and r + 32; blocks are column-major so that a warp reads each column as one
+// contiguous run.
+template <int NB>
+__global__ void k_near_apply(int nE, const int *__restrict__ ptr, const int *__restrict__ src,
+                             const double2 *__restrict__ blocks, const double2 *__restrict__ xs,
+                             double2 *__restrict__ ysn) {
+  constexpr int RPL = (NB + 31) / 32;
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= nE) return;
+  double2 acc[RPL];
+#pragma unroll
+  for (int t = 0; t < RPL; ++t) acc[t] = make_double2(0.0, 0.0);
+  for (int k = ptr[warp]; k < ptr[warp + 1]; ++k) {
+    const double2 *B = blocks + (size_t)k * NB * NB;
+    const double2 *x = xs + (size_t)src[k] * NB;
+    double2 xl[RPL];
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      int cidx = lane + 32 * t;
+      xl[t] = cidx < NB ? x[cidx] : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int tc = 0; tc < RPL; ++tc) {
+      const int ncol = (NB - 32 * tc) < 32 ? (NB - 32 * tc) : 32;
+#pragma unroll 4
+      for (int c0 = 0; c0 < ncol; ++c0) {
+        const int cc = 32 * tc + c0;
+        double xr = __shfl_sync(0xffffffffu, xl[tc].x, c0);
+        double xi = __shfl_sync(0xffffffffu, xl[tc].y, c0);
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+          int rr = lane + 32 * t;
+          if (rr < NB) {
+            double2 b = B[cc * NB + rr];
+            acc[t].x += b.x * xr - b.y * xi;
+            acc[t].y += b.x * xi + b.y * xr;
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < RPL; ++t) {
+    int rr = lane + 32 * t;
+    if (rr < NB) ysn[(size_t)warp * NB + rr] = acc[t];
+  }
+}
+
+efie_status dev_near_apply(Ctx *c, const double2 *xs, double2 *ysn, cudaStream_t st) {
+  int threads = 128, blocks = (c->nE * 32 + threads - 1) / threads;
+  switch (c->nb) {
+    case 8: k_near_apply<8><<<blocks, threads, 0, st>>>(c->nE, c->d_near_ptr, c->d_near_src, c->d_nblk, xs, ysn); break;
+    case 18: k_near_apply<18><<<blocks, threads, 0, st>>>(c->nE, c->d_near_ptr, c->d_near_src, c->d_nblk, xs, ysn); break;
+    case 32: k_near_apply<32><<<blocks, threads, 0, st>>>(c->nE, c->d_near_ptr, c->d_near_src, c->d_nblk, xs, ysn); break;
+    case 50: k_near_apply<50><<<blocks, threads, 0, st>>>(c->nE, c->d_near_ptr, c->d_near_src, c->d_nblk, xs, ysn); break;
+    default: c->err = "unsupported block size"; return EFIE_EINVAL;
+  }
+  EFIE_CUDA(cudaGetLastError());
+  return EFIE_OK;
+}
+
+}  // namespace efie

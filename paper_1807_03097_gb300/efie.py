@@ -1,0 +1,250 @@
+"""Thin ctypes binding of the C ABI in include/efie.h (argument marshalling only).
+
+Every numerical step runs in the CUDA library ``_build/libefie.so``; importing this module
+without the compiled library raises, there is no CPU fallback.  Host arrays are numpy
+complex128 / float64; device arrays are torch CUDA tensors (complex128), passed by pointer.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libefie.so")
+
+EFIE_OK = 0
+EFIE_NOT_CONVERGED = 1
+EFIE_FP64 = 0
+EFIE_MIXED_FP32 = 1
+EFIE_PTR_HOST = 0
+EFIE_PTR_DEVICE = 1
+
+# every symbol declared in include/efie.h
+ABI_SYMBOLS = (
+    "efie_default_options", "efie_create", "efie_set_geometry", "efie_setup", "efie_num_dofs",
+    "efie_matvec", "efie_rhs_plane_waves", "efie_solve", "efie_solve_plane_waves", "efie_far_field",
+    "efie_block_counts", "efie_export_blocks", "efie_export_near_blocks", "efie_matvec_superspace",
+    "efie_last_timings", "efie_destroy", "efie_status_string",
+)
+
+
+class EfieOptions(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("level_m", ctypes.c_int), ("kappa", ctypes.c_double), ("q", ctypes.c_int),
+                ("eta", ctypes.c_double), ("precision", ctypes.c_int), ("quad_regular", ctypes.c_int),
+                ("quad_singular", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("gmres_tol", ctypes.c_double),
+                ("gmres_maxit", ctypes.c_int), ("tol_is_relative", ctypes.c_int)]
+
+
+class EfieSolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("residual", ctypes.c_double),
+                ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+
+
+class EfieError(RuntimeError):
+    def __init__(self, status, where, lib):
+        self.status = status
+        msg = lib.efie_status_string(status).decode()
+        super().__init__(f"{where}: status {status} ({msg})")
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the compiled library; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    P, D, I, I64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), \
+        ctypes.POINTER(ctypes.c_int64)
+    c_int = ctypes.c_int
+    sig = {
+        "efie_default_options": (c_int, [ctypes.POINTER(EfieOptions)]),
+        "efie_create": (c_int, [ctypes.POINTER(P), ctypes.POINTER(EfieOptions), P]),
+        "efie_set_geometry": (c_int, [P, c_int, I, I, D, D, D]),
+        "efie_setup": (c_int, [P]),
+        "efie_num_dofs": (c_int, [P, I64]),
+        "efie_matvec": (c_int, [P, c_int, P, P, c_int]),
+        "efie_rhs_plane_waves": (c_int, [P, c_int, D, D, P, c_int]),
+        "efie_solve": (c_int, [P, c_int, P, P, c_int, ctypes.POINTER(EfieSolveInfo)]),
+        "efie_solve_plane_waves": (c_int, [P, c_int, D, D, P, c_int, ctypes.POINTER(EfieSolveInfo)]),
+        "efie_far_field": (c_int, [P, c_int, P, c_int, D, P, c_int]),
+        "efie_block_counts": (c_int, [P, I64, I64, I64, I64]),
+        "efie_export_blocks": (c_int, [P, I, I]),
+        "efie_export_near_blocks": (c_int, [P, D]),
+        "efie_matvec_superspace": (c_int, [P, P, P, c_int]),
+        "efie_last_timings": (c_int, [P, D, c_int]),
+        "efie_destroy": (c_int, [P]),
+        "efie_status_string": (ctypes.c_char_p, [c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _d(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _i(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _ptr(a):
+    """(pointer, kind) of a numpy array (host) or a torch CUDA tensor (device)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data), EFIE_PTR_HOST
+    if hasattr(a, "data_ptr") and getattr(a, "is_cuda", False):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), EFIE_PTR_DEVICE
+    raise TypeError("expected a numpy array or a CUDA tensor")
+
+
+def options(**kw) -> EfieOptions:
+    L = load()
+    o = EfieOptions()
+    L.efie_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Solver:
+    """One EFIE context: geometry + discretisation resident on the current CUDA device."""
+
+    def __init__(self, patches=None, stream=None, **opts):
+        self._L = load()
+        self.opts = options(**opts)
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream) if stream else None
+        self._check(self._L.efie_create(ctypes.byref(h), ctypes.byref(self.opts), st), "efie_create")
+        self.h = h
+        self.ndof = None
+        if patches is not None:
+            self.set_geometry(patches)
+            self.setup()
+
+    def _check(self, st, where):
+        if st < 0:
+            raise EfieError(st, where, self._L)
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.efie_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_geometry(self, patches):
+        from workloads.geometry import flatten
+
+        deg, ncp, knots, cp, w = flatten(patches)
+        self._check(self._L.efie_set_geometry(self.h, len(patches), _i(deg), _i(ncp), _d(knots), _d(cp), _d(w)),
+                    "efie_set_geometry")
+
+    def setup(self):
+        self._check(self._L.efie_setup(self.h), "efie_setup")
+        n = ctypes.c_int64()
+        self._check(self._L.efie_num_dofs(self.h, ctypes.byref(n)), "efie_num_dofs")
+        self.ndof = int(n.value)
+        a, b, c, d = (ctypes.c_int64() for _ in range(4))
+        self._check(self._L.efie_block_counts(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                              ctypes.byref(d)), "efie_block_counts")
+        self.nfar, self.nnear, self.ncl, self.nsup = int(a.value), int(b.value), int(c.value), int(d.value)
+
+    def matvec(self, x, out=None):
+        """y = A x for x of shape (ndof,) or (nrhs, ndof); numpy (host) or CUDA tensor (device)."""
+        nrhs = 1 if x.ndim == 1 else x.shape[0]
+        if out is None:
+            out = np.empty_like(x) if isinstance(x, np.ndarray) else x.new_empty(x.shape)
+        px, kx = _ptr(x)
+        py, ky = _ptr(out)
+        if kx != ky:
+            raise ValueError("x and out must both be host or both be device arrays")
+        self._check(self._L.efie_matvec(self.h, nrhs, px, py, kx), "efie_matvec")
+        return out
+
+    def matvec_superspace(self, xs, out=None):
+        if out is None:
+            out = np.empty_like(xs) if isinstance(xs, np.ndarray) else xs.new_empty(xs.shape)
+        px, kx = _ptr(xs)
+        py, _ = _ptr(out)
+        self._check(self._L.efie_matvec_superspace(self.h, px, py, kx), "efie_matvec_superspace")
+        return out
+
+    def rhs(self, dirs, pols, out=None):
+        dirs = np.ascontiguousarray(dirs, float).reshape(-1, 3)
+        pols = np.ascontiguousarray(pols, float).reshape(-1, 3)
+        if out is None:
+            out = np.zeros((dirs.shape[0], self.ndof), np.complex128)
+        po, k = _ptr(out)
+        self._check(self._L.efie_rhs_plane_waves(self.h, dirs.shape[0], _d(dirs), _d(pols), po, k),
+                    "efie_rhs_plane_waves")
+        return out
+
+    def solve(self, b, out=None):
+        nrhs = 1 if b.ndim == 1 else b.shape[0]
+        if out is None:
+            out = np.zeros_like(b) if isinstance(b, np.ndarray) else b.new_zeros(b.shape)
+        pb, kb = _ptr(b)
+        px, _ = _ptr(out)
+        info = EfieSolveInfo()
+        st = self._check(self._L.efie_solve(self.h, nrhs, pb, px, kb, ctypes.byref(info)), "efie_solve")
+        return out, info, st
+
+    def solve_plane_waves(self, dirs, pols, out=None):
+        dirs = np.ascontiguousarray(dirs, float).reshape(-1, 3)
+        pols = np.ascontiguousarray(pols, float).reshape(-1, 3)
+        if out is None:
+            out = np.zeros((dirs.shape[0], self.ndof), np.complex128)
+        po, k = _ptr(out)
+        info = EfieSolveInfo()
+        st = self._check(self._L.efie_solve_plane_waves(self.h, dirs.shape[0], _d(dirs), _d(pols), po, k,
+                                                        ctypes.byref(info)), "efie_solve_plane_waves")
+        return out, info, st
+
+    def far_field(self, w, dirs, out=None):
+        dirs = np.ascontiguousarray(dirs, float).reshape(-1, 3)
+        nrhs = 1 if w.ndim == 1 else w.shape[0]
+        if out is None:
+            out = np.zeros((nrhs, dirs.shape[0], 3), np.complex128) if isinstance(w, np.ndarray) else \
+                w.new_zeros((nrhs, dirs.shape[0], 3))
+        pw, kw = _ptr(w)
+        po, _ = _ptr(out)
+        self._check(self._L.efie_far_field(self.h, nrhs, pw, dirs.shape[0], _d(dirs), po, kw), "efie_far_field")
+        return out
+
+    def blocks(self):
+        far = np.zeros((self.nfar, 3), np.int32)
+        near = np.zeros((self.nnear, 2), np.int32)
+        self._check(self._L.efie_export_blocks(self.h, _i(far), _i(near)), "efie_export_blocks")
+        return far, near
+
+    def near_blocks(self):
+        nb = 2 * (self.opts.p + 1) ** 2
+        out = np.zeros((self.nnear, nb, nb), np.complex128)
+        self._check(self._L.efie_export_near_blocks(self.h, _d(out.view(np.float64))), "efie_export_near_blocks")
+        return out
+
+    def last_timings(self):
+        out = np.zeros(7)
+        n = self._L.efie_last_timings(self.h, _d(out), 7)
+        return dict(zip(["total", "gather", "near", "moments_m2m", "m2l", "l2l_eval", "scatter"], out[:n]))
