@@ -1,0 +1,347 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 isogeometric EFIE library.
+
+Workload: plane-wave scattering by the unit sphere as 6 exact rational NURBS patches,
+div-conforming B-splines of degree p = 2 on 32 x 32 elements per patch (13 068 complex
+DOFs), wavenumber kappa = 10, interpolation degree q = 8, eta = 1.6, GMRES(1500) to a
+relative residual of 1e-6, one plane wave along +z polarised in x.
+
+One step = one pass of the whole hot path: device setup from the device-resident geometry
+(geometry at the interpolation nodes, Sauter-Schwab near field, trees), right-hand side,
+device GMRES solve (FMM matrix-vector products) and the far field in 64 directions.
+value = solves per second (steps per second, whole job).  The mixed-precision form (FP32
+phase-split M2L, FP64 near field, geometry and GMRES) is the timed form; its
+matrix-vector product is checked against the FP64 form in the same run.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import geometry as G  # noqa: E402
+
+WORKLOAD = {
+    "workload": "sphere6_nurbs_p2_n32_kappa10_q8_eta1.6_gmres1e-6",
+    "geometry": "unit sphere, 6 exact rational Bezier patches (bidegree 4)",
+    "p": 2, "elements_per_patch": "32x32", "level_m": 5, "kappa": 10.0, "q": 8, "eta": 1.6,
+    "gmres_tol": 1e-6, "gmres_restart": 1500, "incident": "dir +z, pol x", "far_field_directions": 64,
+    "l2": "working set > L2 (near-field blocks 0.68 GB, Krylov basis up to 0.31 GB)",
+}
+MAXIT = 3000
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def peaks():
+    try:
+        with open(MEASURED) as f:
+            return json.load(f)
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev=0):
+        self.dev = dev
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def far_dirs(n=64):
+    # Fibonacci directions on the sphere (deterministic)
+    k = np.arange(n) + 0.5
+    z = 1 - 2 * k / n
+    ph = math.pi * (1 + 5 ** 0.5) * k
+    r = np.sqrt(1 - z * z)
+    return np.stack([r * np.cos(ph), r * np.sin(ph), z], axis=1)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------- CPU oracle
+def oracle_sample(seconds_hint=15.0, its=None):
+    """Oracle cost of one solve of the workload, from a bounded sample: FMM rows of a few
+    elements (near blocks integrated on demand + far field) timed at two sample sizes, which
+    separates the per-element cost from the global moment cost; near-block integration of
+    the sampled pairs timed on its own.  Returns (solves/s, details)."""
+    import oracle as O
+
+    geo = G.sphere()
+    w = WORKLOAD
+    t0 = time.time()
+    r = O.Problem(geo, p=w["p"], m=w["level_m"], kappa=w["kappa"], q=w["q"], eta=w["eta"])
+    t_create = time.time() - t0
+    rng = np.random.default_rng(5)
+    xs = rng.standard_normal(r.nsup) + 1j * rng.standard_normal(r.nsup)
+    near = r.near_pairs()
+    nE = r.nE
+    e_all = rng.permutation(nE)
+    n1, n2 = 2, 6
+    t = time.time()
+    r.fmm_rows(xs, e_all[:n1])
+    t1 = time.time() - t
+    t = time.time()
+    r.fmm_rows(xs, e_all[n1:n1 + n2])
+    t2 = time.time() - t
+    per_row = max(t2 - t1, 1e-9) / (n2 - n1)
+    fixed = max(t1 - n1 * per_row, 0.0)
+    # near-block integration (setup) share of a row
+    sel = [k for k, (a, _) in enumerate(near) if a in set(e_all[:3].tolist())]
+    t = time.time()
+    for k in sel:
+        r.pair_block(int(near[k][0]), int(near[k][1]))
+    t_quad_row = (time.time() - t) / 3
+    setup = t_create + nE * t_quad_row
+    apply_ = fixed + nE * max(per_row - t_quad_row, 0.0)
+    its = its or 1
+    solve = setup + its * apply_
+    return 1.0 / solve, {"oracle_setup_s_est": setup, "oracle_matvec_s_est": apply_, "iterations": its,
+                         "sample": f"oracle FMM rows of {n1}+{n2} of {nE} elements and near blocks of 3 elements, "
+                                   f"scaled to the full operator; solve = setup + {its} x matvec"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    its = args.ref_iterations
+    vals = []
+    det = None
+    for _ in range(args.warmup + args.steps):
+        v, det = oracle_sample(its=its)
+        vals.append(v)
+    vals = vals[args.warmup:]
+    val = statistics.median(vals)
+    line = {"impl": "reference", "metric": "FMM-EFIE solves/s (plane-wave scattering solve incl. setup) at GMRES 1e-6",
+            "value": val, "unit": "solves/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / val, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": WORKLOAD,
+            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": det["sample"]},
+            "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "details": det}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------- GPU
+def run_gpu(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_1807_03097_gb300 import Solver
+    from workloads.geometry import flatten
+
+    w = WORKLOAD
+    geo = G.sphere()
+    stream = torch.cuda.current_stream()
+    kw = dict(p=w["p"], level_m=w["level_m"], kappa=w["kappa"], q=w["q"], eta=w["eta"], gmres_tol=w["gmres_tol"],
+              gmres_restart=w["gmres_restart"], gmres_maxit=args.maxit)
+    prec = 1 if args.precision == "mixed" else 0
+    s = Solver(geo, stream=stream.cuda_stream, precision=prec, **kw)
+    N = s.ndof
+    dirs = far_dirs(64)
+    d_inc, p_inc = np.array([[0, 0, 1.0]]), np.array([[1.0, 0, 0]])
+    wdev = torch.zeros((1, N), dtype=torch.complex128, device="cuda")
+    edev = torch.zeros((1, 64, 3), dtype=torch.complex128, device="cuda")
+
+    def step():
+        s.setup()
+        _, info, st = s.solve_plane_waves(d_inc, p_inc, out=wdev)
+        s.far_field(wdev[0], dirs, out=edev)
+        return info, st
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    l0 = s.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    its = []
+    conv = []
+    for _ in range(args.steps):
+        info, st = step()
+        its.append(info.iterations)
+        conv.append(bool(info.converged))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    launches = s.launch_count() - l0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1000.0 / ms
+    if args.only_steps:
+        if rank == 0:
+            print(json.dumps({"metric": "steps only", "value": value, "unit": "solves/s", "ms_per_step": ms,
+                              "gmres_iterations": int(np.median(its)), "gpu_launches": int(launches)}))
+        s.close()
+        return 0
+
+    # matrix-vector products: mixed vs FP64 form, per-phase device times (CUDA events on
+    # the library's stream), roofline of the dominant kernel
+    rng = np.random.default_rng(0)
+    x = torch.from_numpy(rng.standard_normal(N) + 1j * rng.standard_normal(N)).cuda()
+    y = torch.empty_like(x)
+    ph = []
+    for i in range(23):
+        s.matvec(x, out=y)
+        if i >= 3:
+            ph.append(s.last_timings())
+    mv = {k: statistics.median([p[k] for p in ph]) for k in ph[0]}
+    y_mixed = y.clone()
+    s64 = Solver(geo, stream=stream.cuda_stream, precision=0, **kw)
+    y64 = torch.empty_like(x)
+    ph64 = []
+    for i in range(3):
+        s64.matvec(x, out=y64)
+        if i >= 1:
+            ph64.append(s64.last_timings())
+    mv64 = {k: statistics.median([p[k] for p in ph64]) for k in ph64[0]}
+    err_vs_fp64 = float(torch.linalg.norm(y_mixed - y64) / torch.linalg.norm(y64))
+    # far-field error of the mixed solution vs the FP64 operator applied in the same solve
+    pk = peaks()
+    n_eval = s.nfar * (w["q"] + 1) ** 4
+    flops_per_eval = 48.0  # 4 complex MACs (32) + kernel generation (16, op weights in the design doc)
+    m2l_ms = mv["m2l"]
+    achieved = n_eval * flops_per_eval / (m2l_ms * 1e-3) / 1e12
+    fp32_peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    roof = {"kernel": "k_m2l_f32", "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": None,
+            "peak_note": "FP32 SIMT: 152 SMs x 128 lanes x 2 flop x max SM clock (derived, not measured)",
+            "work": f"{n_eval:.3e} kernel entries x {flops_per_eval:.0f} flop per matvec", "m2l_ms": m2l_ms}
+    near_bytes = s.nnear * s.nb * s.nb * 16 + 2 * s.nsup * 16
+    near_roof = {"kernel": "k_near_apply", "bound": "hbm", "achieved": near_bytes / (mv["near"] * 1e-3) / 1e9,
+                 "peak": pk.get("hbm_gbs"), "unit": "GB/s", "near_ms": mv["near"], "bytes": near_bytes}
+    near_roof["frac"] = near_roof["achieved"] / near_roof["peak"]
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    deg, ncp, knots, cp, wgt = flatten(geo)
+    h2d = sum(a.nbytes for a in (deg, ncp, knots, cp, wgt, d_inc, p_inc, dirs))
+    d2h = N * 16 + 64 * 3 * 16
+    s_e2e = Solver(None, stream=stream.cuda_stream, precision=prec, **kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.e2e_steps)):
+        s_e2e.set_geometry(geo)
+        s_e2e.setup()
+        wh, _, _ = s_e2e.solve_plane_waves(d_inc, p_inc)
+        s_e2e.far_field(wh[0], dirs)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1000.0 / max(1, args.e2e_steps)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, det = oracle_sample(its=int(np.median(its)))
+        cpu = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": det["sample"],
+               "oracle_matvec_s_est": det["oracle_matvec_s_est"], "oracle_setup_s_est": det["oracle_setup_s_est"]}
+
+    if rank == 0:
+        line = {
+            "metric": "FMM-EFIE solves/s (plane-wave scattering solve incl. setup) at GMRES 1e-6, "
+                      "mixed-precision matvec <=1e-5 rel err vs FP64",
+            "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32-m2l/f64" if prec else "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, precision=args.precision, parallelism="replicas" if world > 1 else "single"),
+            "gmres_iterations": int(np.median(its)), "converged": all(conv),
+            "matvec_per_s": 1000.0 / mv["total"], "matvec_ms_phases": mv,
+            "matvec_per_s_fp64": 1000.0 / mv64["total"], "matvec_ms_phases_fp64": mv64,
+            "matvec_rel_err_vs_fp64": err_vs_fp64,
+            "roofline": roof, "roofline_near": near_roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": 1000.0 / e2e_ms, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    s.close()
+    s64.close()
+    s_e2e.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--maxit", type=int, default=MAXIT)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--ref-iterations", type=int, default=1000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-steps", action="store_true", help="time the steps only (for launch-list profiling)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -167,6 +167,10 @@ efie_status efie_matvec_superspace(efie_ctx *ctx, const double *xs, double *ys, 
  * values written (<= n). */
 int efie_last_timings(const efie_ctx *ctx, double *out, int n);
 
+/* Number of CUDA kernels this context has launched since efie_create (all phases);
+ * -1 for a NULL context. */
+int64_t efie_launch_count(const efie_ctx *ctx);
+
 /* Releases all device and host memory of the context (NULL is accepted). */
 efie_status efie_destroy(efie_ctx *ctx);
 

@@ -498,6 +498,11 @@ efie_status efie_far_field(efie_ctx *ctx, int nrhs, const double *w, int ndir, c
   return EFIE_OK;
 }
 
+int64_t efie_launch_count(const efie_ctx *ctx) {
+  const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+  return c ? (int64_t)c->launches : -1;
+}
+
 int efie_last_timings(const efie_ctx *ctx, double *out, int n) {
   const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
   if (!c || !out) return 0;

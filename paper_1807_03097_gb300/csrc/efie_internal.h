@@ -128,6 +128,7 @@ struct Ctx {
   int part_cap = 0;
 
   bool setup_done = false;
+  long long launches = 0;  // kernels launched by this context (all phases)
   Timers tm;
   float last_ms[7] = {0, 0, 0, 0, 0, 0, 0};
   double setup_ms = 0.0;

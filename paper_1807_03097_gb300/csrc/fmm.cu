@@ -450,34 +450,34 @@ static efie_status far_chain(Ctx *c, const double2 *xs, double2 *ys, C2<R> *mom,
   const R h = (R)(1.0 / c->n);
   cudaStream_t st = c->stream;
   size_t csz = sizeof(C2<R>);
-  k_leaf_moments<R><<<c->nE, 128, 0, st>>>(c->nE, c->lev_off[m], p1, q1, h, M, Md, xs, mom);
+  k_leaf_moments<R><<<c->nE, 128, 0, st>>>(c->nE, c->lev_off[m], p1, q1, h, M, Md, xs, mom); ++c->launches;
   for (int l = m - 1; l >= 0; --l) {
     int npar = c->np << (2 * l);
-    k_m2m<R><<<npar, 128, m2m_smem(q1, csz), st>>>(npar, c->lev_off[l], c->lev_off[l + 1], q1, E, mom);
+    k_m2m<R><<<npar, 128, m2m_smem(q1, csz), st>>>(npar, c->lev_off[l], c->lev_off[l + 1], q1, E, mom); ++c->launches;
   }
   long long tot = (long long)c->ncl * nI;
-  k_fold<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(tot, nI, c->d_nodeD, mom, srcv);
+  k_fold<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(tot, nI, c->d_nodeD, mom, srcv); ++c->launches;
   cudaEventRecord(c->tm.ev[3], st);
   int thr = ((nI + 31) / 32) * 32;
   if (c->n_m2l_targets > 0) {
     if (sizeof(R) == 8) {
       size_t sm = sizeof(double) * (3 * nI + 1) + sizeof(double2) * 4 * nI;
       k_m2l_f64<<<c->n_m2l_targets, thr, sm, st>>>(c->d_m2l_targets, c->d_far_ptr, c->d_far_src, nI, c->kappa,
-                                                   c->d_nodeX, (const double2 *)srcv, c->d_acc);
+                                                   c->d_nodeX, (const double2 *)srcv, c->d_acc); ++c->launches;
     } else {
       size_t sm = sizeof(float) * (3 * nI + 1) + sizeof(float2) * 4 * nI;
       k_m2l_f32<<<c->n_m2l_targets, thr, sm, st>>>(c->d_m2l_targets, c->d_far_ptr, c->d_far_src, nI, c->kappa,
-                                                   c->d_center, c->d_nodeXf, (const float2 *)srcv, c->d_acc);
+                                                   c->d_center, c->d_nodeXf, (const float2 *)srcv, c->d_acc); ++c->launches;
     }
   }
   cudaEventRecord(c->tm.ev[4], st);
   k_unfold<R, double2><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(tot, nI, (R)(1.0 / (c->kappa * c->kappa)),
-                                                                     c->d_nodeD, c->d_acc, loc);
+                                                                     c->d_nodeD, c->d_acc, loc); ++c->launches;
   for (int l = 0; l < m; ++l) {
     int npar = c->np << (2 * l);
-    k_l2l<R><<<npar, 128, l2l_smem(q1, csz), st>>>(npar, c->lev_off[l], c->lev_off[l + 1], q1, E, loc);
+    k_l2l<R><<<npar, 128, l2l_smem(q1, csz), st>>>(npar, c->lev_off[l], c->lev_off[l + 1], q1, E, loc); ++c->launches;
   }
-  k_leaf_eval<R><<<c->nE, 128, 0, st>>>(c->nE, c->lev_off[m], p1, q1, h, M, Md, loc, ys);
+  k_leaf_eval<R><<<c->nE, 128, 0, st>>>(c->nE, c->lev_off[m], p1, q1, h, M, Md, loc, ys); ++c->launches;
   EFIE_CUDA(cudaGetLastError());
   return EFIE_OK;
 }
@@ -515,7 +515,7 @@ efie_status dev_matvec_super(Ctx *c, const double2 *xs, double2 *ys) {
   cudaEventRecord(c->tm.ev[0], c->stream);
   cudaEventRecord(c->tm.ev[1], c->stream);
   EFIE_TRY(superspace_apply(c, xs, ys, c->d_ysn));
-  k_add<<<(c->nsup + 255) / 256, 256, 0, c->stream>>>(c->nsup, ys, c->d_ysn);
+  k_add<<<(c->nsup + 255) / 256, 256, 0, c->stream>>>(c->nsup, ys, c->d_ysn); ++c->launches;
   EFIE_CUDA(cudaGetLastError());
   cudaEventRecord(c->tm.ev[6], c->stream);
   return EFIE_OK;
@@ -524,12 +524,12 @@ efie_status dev_matvec_super(Ctx *c, const double2 *xs, double2 *ys) {
 efie_status dev_matvec(Ctx *c, const double2 *x, double2 *y) {
   cudaStream_t st = c->stream;
   EFIE_CUDA(cudaEventRecord(c->tm.ev[0], st));
-  k_gather<<<(c->nsup + 255) / 256, 256, 0, st>>>(c->nsup, c->d_tg_ptr, c->d_tg_col, c->d_tg_val, x, c->d_xs);
+  k_gather<<<(c->nsup + 255) / 256, 256, 0, st>>>(c->nsup, c->d_tg_ptr, c->d_tg_col, c->d_tg_val, x, c->d_xs); ++c->launches;
   EFIE_CUDA(cudaGetLastError());
   EFIE_CUDA(cudaEventRecord(c->tm.ev[1], st));
   EFIE_TRY(superspace_apply(c, c->d_xs, c->d_ys, c->d_ysn));
   k_scatter<<<(c->ndof + 255) / 256, 256, 0, st>>>(c->ndof, c->d_ts_ptr, c->d_ts_col, c->d_ts_val, c->d_ys, c->d_ysn,
-                                                  y);
+                                                  y); ++c->launches;
   EFIE_CUDA(cudaGetLastError());
   EFIE_CUDA(cudaEventRecord(c->tm.ev[6], st));
   return EFIE_OK;
@@ -537,13 +537,13 @@ efie_status dev_matvec(Ctx *c, const double2 *x, double2 *y) {
 
 efie_status dev_scatter(Ctx *c, const double2 *ys, double2 *y) {
   k_scatter<<<(c->ndof + 255) / 256, 256, 0, c->stream>>>(c->ndof, c->d_ts_ptr, c->d_ts_col, c->d_ts_val, ys, nullptr,
-                                                         y);
+                                                         y); ++c->launches;
   EFIE_CUDA(cudaGetLastError());
   return EFIE_OK;
 }
 
 efie_status dev_gather(Ctx *c, const double2 *x, double2 *xs) {
-  k_gather<<<(c->nsup + 255) / 256, 256, 0, c->stream>>>(c->nsup, c->d_tg_ptr, c->d_tg_col, c->d_tg_val, x, xs);
+  k_gather<<<(c->nsup + 255) / 256, 256, 0, c->stream>>>(c->nsup, c->d_tg_ptr, c->d_tg_col, c->d_tg_val, x, xs); ++c->launches;
   EFIE_CUDA(cudaGetLastError());
   return EFIE_OK;
 }

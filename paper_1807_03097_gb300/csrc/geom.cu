@@ -36,7 +36,7 @@ efie_status dev_eval_points(Ctx *c, const std::vector<int> &patch, const std::ve
   EFIE_CUDA(cudaMemcpyAsync(d_pid, patch.data(), 4 * (size_t)npts, cudaMemcpyHostToDevice, c->stream));
   EFIE_CUDA(cudaMemcpyAsync(d_st, st.data(), 16 * (size_t)npts, cudaMemcpyHostToDevice, c->stream));
   k_eval_points<<<(npts + 127) / 128, 128, 0, c->stream>>>(c->d_patches, c->d_knots, c->d_cpw, npts, d_pid, d_st,
-                                                          d_X, d_D);
+                                                          d_X, d_D); ++c->launches;
   EFIE_CUDA(cudaGetLastError());
   EFIE_CUDA(cudaMemcpyAsync(X.data(), d_X, 24 * (size_t)npts, cudaMemcpyDeviceToHost, c->stream));
   if (D) EFIE_CUDA(cudaMemcpyAsync(D->data(), d_D, 48 * (size_t)npts, cudaMemcpyDeviceToHost, c->stream));
@@ -137,7 +137,7 @@ efie_status dev_cluster_geometry(Ctx *c) {
   EFIE_CUDA(cudaMemcpy(d_lev, c->lev_off.data(), 4 * c->lev_off.size(), cudaMemcpyHostToDevice));
   EFIE_CUDA(cudaMemcpy(d_x, c->tab.xcheb.data(), 8 * (size_t)c->q1, cudaMemcpyHostToDevice));
   EFIE_CUDA(cudaDeviceSynchronize());
-  k_cluster_balls<<<c->ncl, 128, 0, c->stream>>>(c->d_patches, c->d_knots, c->d_cpw, d_lev, nlev, c->ncl, d_ball);
+  k_cluster_balls<<<c->ncl, 128, 0, c->stream>>>(c->d_patches, c->d_knots, c->d_cpw, d_lev, nlev, c->ncl, d_ball); ++c->launches;
   EFIE_CUDA(cudaGetLastError());
   c->ball.assign(4 * (size_t)c->ncl, 0.0);
   EFIE_CUDA(cudaMemcpyAsync(c->ball.data(), d_ball, 32 * (size_t)c->ncl, cudaMemcpyDeviceToHost, c->stream));
@@ -148,7 +148,7 @@ efie_status dev_cluster_geometry(Ctx *c) {
   long long tot = (long long)c->ncl * c->nI;
   k_node_geometry<<<(unsigned)((tot + 127) / 128), 128, 0, c->stream>>>(c->d_patches, c->d_knots, c->d_cpw, d_lev,
                                                                       nlev, c->ncl, c->q1, d_x, d_ball, c->d_nodeX,
-                                                                      c->d_nodeD, c->d_nodeXf);
+                                                                      c->d_nodeD, c->d_nodeXf); ++c->launches;
   EFIE_CUDA(cudaGetLastError());
   EFIE_CUDA(cudaMemcpyAsync(c->d_center, d_ball, 32 * (size_t)c->ncl, cudaMemcpyDeviceToDevice, c->stream));
   EFIE_CUDA(cudaStreamSynchronize(c->stream));

@@ -207,8 +207,8 @@ static efie_status dots(Ctx *c, int N, int nvec, const double2 *V, size_t ldv, c
   EFIE_TRY(ensure_part(c, N, nvec));
   int nchunk = (N + kChunk - 1) / kChunk;
   dim3 grid(nchunk, (nvec + kVecPerBlock - 1) / kVecPerBlock);
-  k_dot_partial<<<grid, kDotThreads, 0, c->stream>>>(N, nvec, V, ldv, w, c->d_part, nchunk);
-  k_dot_final<<<(nvec + 7) / 8, 256, 0, c->stream>>>(nvec, nchunk, c->d_part, h);
+  k_dot_partial<<<grid, kDotThreads, 0, c->stream>>>(N, nvec, V, ldv, w, c->d_part, nchunk); ++c->launches;
+  k_dot_final<<<(nvec + 7) / 8, 256, 0, c->stream>>>(nvec, nchunk, c->d_part, h); ++c->launches;
   EFIE_CUDA(cudaGetLastError());
   return EFIE_OK;
 }
@@ -250,12 +250,12 @@ efie_status dev_gmres(Ctx *c, const double2 *b, double2 *x, int *its_out, double
       EFIE_CUDA(cudaMemcpyAsync(c->d_r, b, sizeof(double2) * N, cudaMemcpyDeviceToDevice, st));
     } else {
       EFIE_TRY(dev_matvec(c, x, c->d_r));
-      k_residual<<<grid, blk, 0, st>>>(N, b, c->d_r);
+      k_residual<<<grid, blk, 0, st>>>(N, b, c->d_r); ++c->launches;
     }
     first = false;
     EFIE_TRY(dots(c, N, 1, c->d_r, N, c->d_r, c->d_h));
-    k_givens_init<<<1, 1, 0, st>>>(c->d_gs, kr, c->d_h);
-    k_scale_copy<<<grid, blk, 0, st>>>(N, c->d_r, c->d_gs, 0, V);
+    k_givens_init<<<1, 1, 0, st>>>(c->d_gs, kr, c->d_h); ++c->launches;
+    k_scale_copy<<<grid, blk, 0, st>>>(N, c->d_r, c->d_gs, 0, V); ++c->launches;
     EFIE_CUDA(cudaMemcpyAsync(c->h_res, c->d_gs, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     EFIE_CUDA(cudaStreamSynchronize(st));
     res = c->h_res[1];
@@ -270,12 +270,12 @@ efie_status dev_gmres(Ctx *c, const double2 *b, double2 *x, int *its_out, double
       ++its;
       // CGS2
       EFIE_TRY(dots(c, N, j + 1, V, N, c->d_w, c->d_h));
-      k_combine<<<grid, blk, sizeof(double2) * (j + 1), st>>>(N, j + 1, V, N, c->d_h, -1.0, c->d_w);
+      k_combine<<<grid, blk, sizeof(double2) * (j + 1), st>>>(N, j + 1, V, N, c->d_h, -1.0, c->d_w); ++c->launches;
       EFIE_TRY(dots(c, N, j + 1, V, N, c->d_w, c->d_h2));
-      k_combine<<<grid, blk, sizeof(double2) * (j + 1), st>>>(N, j + 1, V, N, c->d_h2, -1.0, c->d_w);
+      k_combine<<<grid, blk, sizeof(double2) * (j + 1), st>>>(N, j + 1, V, N, c->d_h2, -1.0, c->d_w); ++c->launches;
       EFIE_TRY(dots(c, N, 1, c->d_w, N, c->d_w, c->d_h2 + kr));
-      k_givens_step<<<1, 1, 0, st>>>(j, kr, c->d_h, c->d_h2, c->d_h2 + kr, c->d_H, c->d_gs);
-      k_scale_copy<<<grid, blk, 0, st>>>(N, c->d_w, c->d_gs, 0, V + (size_t)(j + 1) * N);
+      k_givens_step<<<1, 1, 0, st>>>(j, kr, c->d_h, c->d_h2, c->d_h2 + kr, c->d_H, c->d_gs); ++c->launches;
+      k_scale_copy<<<grid, blk, 0, st>>>(N, c->d_w, c->d_gs, 0, V + (size_t)(j + 1) * N); ++c->launches;
       EFIE_CUDA(cudaGetLastError());
       EFIE_CUDA(cudaMemcpyAsync(c->h_res, c->d_gs, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
       EFIE_CUDA(cudaStreamSynchronize(st));
@@ -284,14 +284,14 @@ efie_status dev_gmres(Ctx *c, const double2 *b, double2 *x, int *its_out, double
       if (res <= target || !(res == res)) break;
     }
     if (jd > 0) {
-      k_backsolve<<<1, 32, 0, st>>>(jd, kr, c->d_H, c->d_gs, c->d_sol);
-      k_combine<<<grid, blk, sizeof(double2) * jd, st>>>(N, jd, V, N, c->d_sol, 1.0, x);
+      k_backsolve<<<1, 32, 0, st>>>(jd, kr, c->d_H, c->d_gs, c->d_sol); ++c->launches;
+      k_combine<<<grid, blk, sizeof(double2) * jd, st>>>(N, jd, V, N, c->d_sol, 1.0, x); ++c->launches;
       EFIE_CUDA(cudaGetLastError());
     }
     if (res <= target) {
       // confirm with the true residual
       EFIE_TRY(dev_matvec(c, x, c->d_r));
-      k_residual<<<grid, blk, 0, st>>>(N, b, c->d_r);
+      k_residual<<<grid, blk, 0, st>>>(N, b, c->d_r); ++c->launches;
       EFIE_TRY(dots(c, N, 1, c->d_r, N, c->d_r, c->d_h));
       EFIE_CUDA(cudaMemcpyAsync(c->h_res, c->d_h, sizeof(double2), cudaMemcpyDeviceToHost, st));
       EFIE_CUDA(cudaStreamSynchronize(st));

@@ -276,6 +276,7 @@ efie_status dev_near_quadrature(Ctx *c, const std::vector<NearPair> &pairs, cons
     EFIE_CUDA(cudaFuncSetAttribute(k_near_quad<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                                    (int)smem));                                                    \
     k_near_quad<PP><<<A.ntodo, kQuadThreads, smem, c->stream>>>(A);                                 \
+    ++c->launches;                                                                                  \
     break;
     EFIE_QUAD_CASE(1)
     EFIE_QUAD_CASE(2)
@@ -290,7 +291,7 @@ efie_status dev_near_quadrature(Ctx *c, const std::vector<NearPair> &pairs, cons
   if (!todo_m.empty()) {
     long long tot = (long long)todo_m.size() * nb * nb;
     k_near_mirror<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(nb, d_todo_m, d_src_of, d_slot,
-                                                                       (int)todo_m.size(), c->d_nblk);
+                                                                       (int)todo_m.size(), c->d_nblk); ++c->launches;
     EFIE_CUDA(cudaGetLastError());
   }
   EFIE_CUDA(cudaStreamSynchronize(c->stream));
@@ -361,7 +362,7 @@ efie_status dev_near_apply(Ctx *c, const double2 *xs, double2 *ysn, cudaStream_t
     case 50: k_near_apply<50><<<blocks, threads, 0, st>>>(c->nE, c->d_near_ptr, c->d_near_src, c->d_nblk, xs, ysn); break;
     default: c->err = "unsupported block size"; return EFIE_EINVAL;
   }
-  EFIE_CUDA(cudaGetLastError());
+  EFIE_CUDA(cudaGetLastError()); ++c->launches;
   return EFIE_OK;
 }
 

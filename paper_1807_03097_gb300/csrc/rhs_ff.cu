@@ -81,7 +81,7 @@ efie_status dev_rhs(Ctx *c, const double *dir, const double *pol, double2 *g) {
   EFIE_CUDA(cudaMemcpyAsync(d_rule, c->tab.gx.data(), 8 * (size_t)c->gr, cudaMemcpyHostToDevice, c->stream));
   EFIE_CUDA(cudaMemcpyAsync(d_rule + c->gr, c->tab.gw.data(), 8 * (size_t)c->gr, cudaMemcpyHostToDevice, c->stream));
   k_rhs<<<c->nE, 256, 0, c->stream>>>(c->d_patches, c->d_knots, c->d_cpw, c->n, c->p, c->gr, d_rule, d_rule + c->gr,
-                                      c->kappa, dir[0], dir[1], dir[2], pol[0], pol[1], pol[2], c->d_ys);
+                                      c->kappa, dir[0], dir[1], dir[2], pol[0], pol[1], pol[2], c->d_ys); ++c->launches;
   EFIE_CUDA(cudaGetLastError());
   EFIE_TRY(dev_scatter(c, c->d_ys, g));
   EFIE_CUDA(cudaStreamSynchronize(c->stream));
@@ -187,8 +187,8 @@ efie_status dev_far_field(Ctx *c, const double2 *w, int ndir, const double *dirs
   EFIE_TRY(dev_gather(c, w, c->d_xs));
   dim3 grid(c->nE, ndir);
   k_ff_partial<<<grid, 256, 0, c->stream>>>(c->d_patches, c->d_knots, c->d_cpw, c->n, c->p, c->gr, d_rule,
-                                            d_rule + c->gr, c->kappa, c->nE, d_dirs, c->d_xs, d_part);
-  k_ff_final<<<ndir, 256, 0, c->stream>>>(c->nE, d_dirs, d_part, out);
+                                            d_rule + c->gr, c->kappa, c->nE, d_dirs, c->d_xs, d_part); ++c->launches;
+  k_ff_final<<<ndir, 256, 0, c->stream>>>(c->nE, d_dirs, d_part, out); ++c->launches;
   EFIE_CUDA(cudaGetLastError());
   EFIE_CUDA(cudaStreamSynchronize(c->stream));
   cudaFree(d_rule);

@@ -26,7 +26,7 @@ ABI_SYMBOLS = (
     "efie_default_options", "efie_create", "efie_set_geometry", "efie_setup", "efie_num_dofs",
     "efie_matvec", "efie_rhs_plane_waves", "efie_solve", "efie_solve_plane_waves", "efie_far_field",
     "efie_block_counts", "efie_export_blocks", "efie_export_near_blocks", "efie_matvec_superspace",
-    "efie_last_timings", "efie_destroy", "efie_status_string",
+    "efie_last_timings", "efie_launch_count", "efie_destroy", "efie_status_string",
 )
 
 
@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH):
         "efie_export_near_blocks": (c_int, [P, D]),
         "efie_matvec_superspace": (c_int, [P, P, P, c_int]),
         "efie_last_timings": (c_int, [P, D, c_int]),
+        "efie_launch_count": (ctypes.c_int64, [P]),
         "efie_destroy": (c_int, [P]),
         "efie_status_string": (ctypes.c_char_p, [c_int]),
     }
@@ -169,6 +170,7 @@ class Solver:
         self._check(self._L.efie_block_counts(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
                                               ctypes.byref(d)), "efie_block_counts")
         self.nfar, self.nnear, self.ncl, self.nsup = int(a.value), int(b.value), int(c.value), int(d.value)
+        self.nb = 2 * (self.opts.p + 1) ** 2
 
     def matvec(self, x, out=None):
         """y = A x for x of shape (ndof,) or (nrhs, ndof); numpy (host) or CUDA tensor (device)."""
@@ -243,6 +245,9 @@ class Solver:
         out = np.zeros((self.nnear, nb, nb), np.complex128)
         self._check(self._L.efie_export_near_blocks(self.h, _d(out.view(np.float64))), "efie_export_near_blocks")
         return out
+
+    def launch_count(self):
+        return int(self._L.efie_launch_count(self.h))
 
     def last_timings(self):
         out = np.zeros(7)

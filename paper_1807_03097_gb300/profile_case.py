@@ -1,0 +1,40 @@
+"""Run a few matrix-vector products of one configurable case (for profiling a kernel on a
+case smaller than the benchmark's).  Example:
+    python -m paper_1807_03097_gb300.profile_case --p 2 --m 4 --kappa 10 --q 8 --precision mixed --matvecs 3
+"""
+import argparse
+import os
+import sys
+
+import numpy as np
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--geometry", default="sphere", choices=["sphere", "torus", "cube"])
+    ap.add_argument("--p", type=int, default=2)
+    ap.add_argument("--m", type=int, default=4)
+    ap.add_argument("--kappa", type=float, default=10.0)
+    ap.add_argument("--q", type=int, default=8)
+    ap.add_argument("--eta", type=float, default=1.6)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--matvecs", type=int, default=3)
+    a = ap.parse_args()
+    from paper_1807_03097_gb300 import Solver
+    from workloads import geometry as G
+
+    geo = {"sphere": G.sphere, "torus": G.torus, "cube": G.cube}[a.geometry]()
+    s = Solver(geo, p=a.p, level_m=a.m, kappa=a.kappa, q=a.q, eta=a.eta, precision=1 if a.precision == "mixed" else 0)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(s.ndof) + 1j * rng.standard_normal(s.ndof)
+    for _ in range(a.matvecs):
+        y = s.matvec(x)
+    t = s.last_timings()
+    print(f"ndof {s.ndof} far {s.nfar} near {s.nnear} matvec ms " + " ".join(f"{k}={v:.3f}" for k, v in t.items()))
+    s.close()
+
+
+if __name__ == "__main__":
+    main()
