@@ -30,11 +30,12 @@ void release_device(Ctx *c) {
   dfree(c->d_ts_ptr); dfree(c->d_ts_col); dfree(c->d_ts_val);
   dfree(c->d_nodeX); dfree(c->d_nodeD); dfree(c->d_nodeXf); dfree(c->d_center);
   dfree(c->d_far_ptr); dfree(c->d_far_src); dfree(c->d_m2l_targets);
-  dfree(c->d_near_ptr); dfree(c->d_near_src); dfree(c->d_nblk);
+  dfree(c->d_near_ptr); dfree(c->d_near_src); dfree(c->d_nblk); dfree(c->d_nblkf);
   dfree(c->d_M); dfree(c->d_Md); dfree(c->d_E); dfree(c->d_Mf); dfree(c->d_Mdf); dfree(c->d_Ef);
   dfree(c->d_x); dfree(c->d_y); dfree(c->d_xs); dfree(c->d_ys); dfree(c->d_ysn);
   dfree(c->d_mom); dfree(c->d_src); dfree(c->d_acc); dfree(c->d_loc);
-  dfree(c->d_momf); dfree(c->d_srcf); dfree(c->d_locf); dfree(c->d_accm);
+  dfree(c->d_momf); dfree(c->d_srcf); dfree(c->d_locf); dfree(c->d_accm); dfree(c->d_accf);
+  dfree(c->d_nodeX4); dfree(c->d_pgeo); dfree(c->d_pph);
   dfree(c->d_V); dfree(c->d_H); dfree(c->d_h); dfree(c->d_h2); dfree(c->d_part); dfree(c->d_gs);
   dfree(c->d_w); dfree(c->d_r); dfree(c->d_b); dfree(c->d_sol);
   c->kr = 0;
@@ -281,6 +282,7 @@ efie_status efie_setup(efie_ctx *ctx) {
   std::vector<int> mirror;
   EFIE_TRY(host_classify_near(c, corners, pairs, mirror));
   EFIE_TRY(dev_near_quadrature(c, pairs, mirror));
+  if (c->opt.precision == EFIE_MIXED_FP32) EFIE_TRY(dev_near_blocks_f32(c));
   EFIE_TRY(dev_alloc_work(c));
   EFIE_CUDA(cudaStreamSynchronize(c->stream));
   c->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

@@ -96,8 +96,10 @@ struct Ctx {
   int *d_far_ptr = nullptr, *d_far_src = nullptr;  // CSR by target cluster
   int *d_m2l_targets = nullptr;
   int n_m2l_targets = 0;
+  bool m2l_reduce = true;  // FP32 M2L reduces phases explicitly (unless all are within +-100 pi)
   int *d_near_ptr = nullptr, *d_near_src = nullptr;  // CSR by target element
   double2 *d_nblk = nullptr;  // [nnear][nb (col)][nb (row)]
+  float2 *d_nblkf = nullptr;  // FP32 copy of the blocks (mixed-precision apply)
   std::vector<int> near_perm;  // CSR position -> index in nearl
 
   // tables on the device
@@ -112,8 +114,13 @@ struct Ctx {
   double2 *d_acc = nullptr;  // [ncl][4][nI]
   double2 *d_loc = nullptr;  // [ncl][3][nI]
   // work vectors (FP32 path)
-  float2 *d_momf = nullptr, *d_srcf = nullptr, *d_locf = nullptr;
-  double2 *d_accm = nullptr;  // mixed path accumulates each pair's FP32 sum in FP64
+  float2 *d_momf = nullptr, *d_locf = nullptr;
+  float4 *d_srcf = nullptr;   // [ncl][nI][2]: (u_x, u_y), (u_z, nu) folded source fields
+  float4 *d_accf = nullptr;   // [ncl][nI][2]: M2L results, same layout
+  float4 *d_nodeX4 = nullptr; // [ncl][nI] node offsets from the cluster centre (x, y, z, 0)
+  float4 *d_pgeo = nullptr;   // per far pair (CSR order): centre offset d = c_t - c_s, r0 = |d|
+  float2 *d_pph = nullptr;    // per far pair: e^{i kappa r0} / (4 pi)
+  double2 *d_accm = nullptr;
 
   // GMRES
   int kr = 0;  // allocated restart length
@@ -155,6 +162,7 @@ efie_status dev_rhs(Ctx *c, const double *dir, const double *pol, double2 *g);
 efie_status dev_far_field(Ctx *c, const double2 *w, int ndir, const double *dirs, double2 *out);
 efie_status dev_gmres(Ctx *c, const double2 *b, double2 *x, int *its, double *res, int *conv);
 efie_status dev_alloc_work(Ctx *c);
+efie_status dev_near_blocks_f32(Ctx *c);
 
 #define EFIE_CUDA(call)                                                              \
   do {                                                                               \

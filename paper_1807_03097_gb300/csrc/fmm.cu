@@ -260,83 +260,171 @@ __global__ void k_m2l_f64(const int *__restrict__ targets, const int *__restrict
   }
 }
 
-// ------------------------------------------------------------------------ a6 M2L (FP32)
-// Phase-split kernel: with centres c_t, c_s and r0 = |c_t - c_s|,
-//   G = e^{i kappa r0} e^{i kappa (r - r0)} / (4 pi r),
-// e^{i kappa r0} in FP64 once per pair; node offsets from the centres in FP32, and
-// r - r0 = (2 d.delta + |delta|^2) / (r + r0) (d = c_t - c_s, delta = offset difference)
-// without cancellation.  Each pair's FP32 sum is rotated by its FP64 phase and accumulated
-// in FP64.
-__global__ void k_m2l_f32(const int *__restrict__ targets, const int *__restrict__ fptr, const int *__restrict__ fsrc,
-                          int nI, double kappa, const double *__restrict__ center, const float *__restrict__ nodeXf,
-                          const float2 *__restrict__ src, double2 *__restrict__ acc) {
-  int t = targets[blockIdx.x];
-  extern __shared__ float smf[];
-  float *sX = smf;                        // [nI][3]
-  float2 *sS = (float2 *)(smf + 3 * nI + (3 * nI & 1));  // [4][nI]
-  __shared__ double sPh[2];
-  __shared__ float sD[4];
-  int mi = threadIdx.x;
-  float xt0 = 0, xt1 = 0, xt2 = 0;
-  if (mi < nI) {
-    xt0 = nodeXf[((size_t)t * nI + mi) * 3];
-    xt1 = nodeXf[((size_t)t * nI + mi) * 3 + 1];
-    xt2 = nodeXf[((size_t)t * nI + mi) * 3 + 2];
+// ------------------------------------------------------------------------ a6 M2L (FP32, node-major)
+// Folded source fields of the FP32 path, node-major: src[(id nI + m) 2] = (u_x, u_y),
+// src[(id nI + m) 2 + 1] = (u_z, nu).
+__global__ void k_fold_f32n(long long tot, int nI, const double *__restrict__ nodeD, const float2 *__restrict__ mom,
+                            float4 *__restrict__ src) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= tot) return;
+  int id = (int)(t / nI), mi = (int)(t % nI);
+  const double *D = nodeD + 6 * t;
+  const float2 *mm = mom + (size_t)id * 3 * nI;
+  float2 m0 = mm[mi], m1 = mm[nI + mi], nu = mm[2 * nI + mi];
+  float u[6];
+  for (int k = 0; k < 3; ++k) {
+    float d1 = (float)D[k], d2 = (float)D[3 + k];
+    u[2 * k] = d1 * m0.x + d2 * m1.x;
+    u[2 * k + 1] = d1 * m0.y + d2 * m1.y;
   }
-  const double ct0 = center[4 * t], ct1 = center[4 * t + 1], ct2 = center[4 * t + 2];
-  const float kf = (float)kappa;
-  double2 a0 = make_double2(0, 0), a1 = a0, a2 = a0, a3 = a0;
+  src[2 * t] = make_float4(u[0], u[1], u[2], u[3]);
+  src[2 * t + 1] = make_float4(u[4], u[5], nu.x, nu.y);
+}
+
+// Per far pair (CSR order): d = c_t - c_s and r0 = |d| in FP32, e^{i kappa r0} / (4 pi) from
+// FP64.  Computed once at setup.
+__global__ void k_pair_table(int ntarget, const int *__restrict__ targets, const int *__restrict__ fptr,
+                             const int *__restrict__ fsrc, const double *__restrict__ center, double kappa,
+                             float4 *__restrict__ pgeo, float2 *__restrict__ pph) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntarget) return;
+  int t = targets[i];
   for (int k = fptr[t]; k < fptr[t + 1]; ++k) {
     int s = fsrc[k];
-    __syncthreads();
-    for (int i = threadIdx.x; i < 3 * nI; i += blockDim.x) sX[i] = nodeXf[(size_t)s * nI * 3 + i];
-    for (int i = threadIdx.x; i < 4 * nI; i += blockDim.x) sS[i] = src[(size_t)s * 4 * nI + i];
-    if (threadIdx.x == 0) {
-      double d0 = ct0 - center[4 * s], d1 = ct1 - center[4 * s + 1], d2 = ct2 - center[4 * s + 2];
-      double r0 = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-      double sn, cs;
-      sincos(kappa * r0, &sn, &cs);
-      sPh[0] = cs * 0.25 / M_PI;
-      sPh[1] = sn * 0.25 / M_PI;
-      sD[0] = (float)d0;
-      sD[1] = (float)d1;
-      sD[2] = (float)d2;
-      sD[3] = (float)r0;
+    double d0 = center[4 * t] - center[4 * s], d1 = center[4 * t + 1] - center[4 * s + 1],
+           d2 = center[4 * t + 2] - center[4 * s + 2];
+    double r0 = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    double sn, cs;
+    sincos(kappa * r0, &sn, &cs);
+    pgeo[k] = make_float4((float)d0, (float)d1, (float)d2, (float)r0);
+    pph[k] = make_float2((float)(cs * 0.25 / M_PI), (float)(sn * 0.25 / M_PI));
+  }
+}
+
+// d = a * b + c on two FP32 lanes at once (Blackwell packed FMA)
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  unsigned long long A = *reinterpret_cast<unsigned long long *>(&a);
+  unsigned long long B = *reinterpret_cast<unsigned long long *>(&b);
+  unsigned long long C = *reinterpret_cast<unsigned long long *>(&c);
+  unsigned long long D;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(D) : "l"(A), "l"(B), "l"(C));
+  return *reinterpret_cast<float2 *>(&D);
+}
+
+// FP32 M2L, one warp per target cluster, lane owns target nodes m = lane + j T (j < NT,
+// T = ceil(nI / NT) <= 32).  With e = x_t - x_s (offsets from the cluster centres) and the
+// pair's centre offset d, r0 = |d|:
+//   num = 2 d.e + |e|^2 = r^2 - r0^2 (no cancellation), r = sqrt(r0^2 + num),
+//   r - r0 = num / (r + r0),  G = e^{i kappa r0}/(4 pi) * e^{i kappa (r - r0)} / r.
+// The pair factor e^{i kappa r0}/(4 pi) is applied to the source fields while they are
+// staged in shared memory, together with the rotated copy (-Im, Re) that lets a complex
+// multiply-add run as two packed FMAs.  REDUCE: phase reduced to [-pi, pi] by two-constant
+// Cody-Waite before the hardware sine / cosine; without it the host has checked that every
+// phase lies within +-100 pi.
+template <int NT, bool REDUCE>
+__global__ void __launch_bounds__(128) k_m2l_f32w(const int *__restrict__ targets, int ntarget,
+                                                  const int *__restrict__ fptr, const int *__restrict__ fsrc,
+                                                  const float4 *__restrict__ pgeo, const float2 *__restrict__ pph,
+                                                  int nI, float kappa, const float4 *__restrict__ nodeX4,
+                                                  const float4 *__restrict__ src, float4 *__restrict__ acc) {
+  extern __shared__ float4 sm4[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wg = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (wg >= ntarget) return;
+  float4 *sX = sm4 + (size_t)wib * 5 * nI;
+  float4 *sW = sX + nI;       // [nI][2]: (w0, w1), (w2, w3)
+  float4 *sR = sW + 2 * nI;   // [nI][2]: rotated (-Im, Re) copies
+  const int t = targets[wg];
+  const int T = (nI + NT - 1) / NT;
+  float xt[NT][3];
+  float2 a[NT][4];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    int mi = lane + j * T;
+    float4 x = (lane < T && mi < nI) ? nodeX4[(size_t)t * nI + mi] : make_float4(0.f, 0.f, 0.f, 0.f);
+    xt[j][0] = x.x;
+    xt[j][1] = x.y;
+    xt[j][2] = x.z;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a[j][q] = make_float2(0.f, 0.f);
+  }
+  const float inv2pi = 0.15915494309189535f, c1 = 6.28318548202514648f, c2 = -1.7484555e-7f;
+  for (int k = fptr[t]; k < fptr[t + 1]; ++k) {
+    const int s = fsrc[k];
+    const float4 g = pgeo[k];
+    const float2 ph = pph[k];
+    __syncwarp();
+    for (int i = lane; i < nI; i += 32) {
+      sX[i] = nodeX4[(size_t)s * nI + i];
+      float4 u = src[2 * ((size_t)s * nI + i)], v = src[2 * ((size_t)s * nI + i) + 1];
+      float4 pu = make_float4(ph.x * u.x - ph.y * u.y, ph.x * u.y + ph.y * u.x, ph.x * u.z - ph.y * u.w,
+                              ph.x * u.w + ph.y * u.z);
+      float4 pv = make_float4(ph.x * v.x - ph.y * v.y, ph.x * v.y + ph.y * v.x, ph.x * v.z - ph.y * v.w,
+                              ph.x * v.w + ph.y * v.z);
+      sW[2 * i] = pu;
+      sW[2 * i + 1] = pv;
+      sR[2 * i] = make_float4(-pu.y, pu.x, -pu.w, pu.z);
+      sR[2 * i + 1] = make_float4(-pv.y, pv.x, -pv.w, pv.z);
     }
-    __syncthreads();
-    if (mi < nI) {
-      const float d0 = sD[0], d1 = sD[1], d2 = sD[2], r0 = sD[3];
-      float b0x = 0, b0y = 0, b1x = 0, b1y = 0, b2x = 0, b2y = 0, b3x = 0, b3y = 0;
-      for (int mj = 0; mj < nI; ++mj) {
-        float e0 = xt0 - sX[3 * mj], e1 = xt1 - sX[3 * mj + 1], e2 = xt2 - sX[3 * mj + 2];
-        float v0 = d0 + e0, v1 = d1 + e1, v2 = d2 + e2;
-        float r2 = v0 * v0 + v1 * v1 + v2 * v2;
-        float r = sqrtf(r2);
-        float dr = (2.f * (d0 * e0 + d1 * e1 + d2 * e2) + (e0 * e0 + e1 * e1 + e2 * e2)) / (r + r0);
+    __syncwarp();
+    const float r0 = g.w, r0sq = g.w * g.w;
+#pragma unroll 2
+    for (int mj = 0; mj < nI; ++mj) {
+      const float4 xs = sX[mj], wa = sW[2 * mj], wb = sW[2 * mj + 1], ra = sR[2 * mj], rb = sR[2 * mj + 1];
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        float ex = xt[j][0] - xs.x, ey = xt[j][1] - xs.y, ez = xt[j][2] - xs.z;
+        float de = g.x * ex + g.y * ey + g.z * ez;
+        float ee = ex * ex + ey * ey + ez * ez;
+        float num = fmaf(2.f, de, ee);
+        float r2 = r0sq + num;
+        float rinv = rsqrtf(r2);
+        float r = r2 * rinv;
+        float phs = kappa * __fdividef(num, r + r0);
+        if (REDUCE) {
+          float kk = rintf(phs * inv2pi);
+          phs = fmaf(-kk, c1, phs);
+          phs = fmaf(-kk, c2, phs);
+        }
         float sn, cs;
-        sincosf(kf * dr, &sn, &cs);
-        float ir = 1.f / r;
-        float gr = cs * ir, gi = sn * ir;
-        float2 w0 = sS[mj], w1 = sS[nI + mj], w2 = sS[2 * nI + mj], w3 = sS[3 * nI + mj];
-        b0x += gr * w0.x - gi * w0.y; b0y += gr * w0.y + gi * w0.x;
-        b1x += gr * w1.x - gi * w1.y; b1y += gr * w1.y + gi * w1.x;
-        b2x += gr * w2.x - gi * w2.y; b2y += gr * w2.y + gi * w2.x;
-        b3x += gr * w3.x - gi * w3.y; b3y += gr * w3.y + gi * w3.x;
+        __sincosf(phs, &sn, &cs);
+        const float2 gr = make_float2(cs * rinv, cs * rinv), gi = make_float2(sn * rinv, sn * rinv);
+        a[j][0] = ffma2(gi, make_float2(ra.x, ra.y), ffma2(gr, make_float2(wa.x, wa.y), a[j][0]));
+        a[j][1] = ffma2(gi, make_float2(ra.z, ra.w), ffma2(gr, make_float2(wa.z, wa.w), a[j][1]));
+        a[j][2] = ffma2(gi, make_float2(rb.x, rb.y), ffma2(gr, make_float2(wb.x, wb.y), a[j][2]));
+        a[j][3] = ffma2(gi, make_float2(rb.z, rb.w), ffma2(gr, make_float2(wb.z, wb.w), a[j][3]));
       }
-      const double pr = sPh[0], pi = sPh[1];
-      a0.x += pr * b0x - pi * b0y; a0.y += pr * b0y + pi * b0x;
-      a1.x += pr * b1x - pi * b1y; a1.y += pr * b1y + pi * b1x;
-      a2.x += pr * b2x - pi * b2y; a2.y += pr * b2y + pi * b2x;
-      a3.x += pr * b3x - pi * b3y; a3.y += pr * b3y + pi * b3x;
     }
   }
-  if (mi < nI) {
-    double2 *o = acc + (size_t)t * 4 * nI;
-    o[mi] = a0;
-    o[nI + mi] = a1;
-    o[2 * nI + mi] = a2;
-    o[3 * nI + mi] = a3;
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    int mi = lane + j * T;
+    if (lane < T && mi < nI) {
+      acc[2 * ((size_t)t * nI + mi)] = make_float4(a[j][0].x, a[j][0].y, a[j][1].x, a[j][1].y);
+      acc[2 * ((size_t)t * nI + mi) + 1] = make_float4(a[j][2].x, a[j][2].y, a[j][3].x, a[j][3].y);
+    }
   }
+}
+
+__global__ void k_unfold_f32n(long long tot, int nI, float ik2, const double *__restrict__ nodeD,
+                              const float4 *__restrict__ acc, float2 *__restrict__ loc) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= tot) return;
+  int id = (int)(t / nI), mi = (int)(t % nI);
+  const double *D = nodeD + 6 * t;
+  float4 u = acc[2 * t], v = acc[2 * t + 1];
+  float cr[3] = {u.x, u.z, v.x}, ci[3] = {u.y, u.w, v.y};
+  float l0x = 0, l0y = 0, l1x = 0, l1y = 0;
+  for (int k = 0; k < 3; ++k) {
+    l0x += (float)D[k] * cr[k];
+    l0y += (float)D[k] * ci[k];
+    l1x += (float)D[3 + k] * cr[k];
+    l1y += (float)D[3 + k] * ci[k];
+  }
+  float2 *l = loc + (size_t)id * 3 * nI;
+  l[mi] = make_float2(l0x, l0y);
+  l[nI + mi] = make_float2(l1x, l1y);
+  l[2 * nI + mi] = make_float2(-ik2 * v.z, -ik2 * v.w);
 }
 
 // ------------------------------------------------------------------------ a7 L2L
@@ -440,6 +528,79 @@ __global__ void k_leaf_eval(int nE, int leaf_off, int p1, int q1, R h, const dou
 }
 
 // ------------------------------------------------------------------------ drivers
+constexpr int kM2LWarps = 4;
+
+static size_t m2l_f32_smem(int nI) { return sizeof(float4) * 5 * (size_t)nI * kM2LWarps; }
+
+template <bool RED>
+static efie_status launch_m2l_f32_t(Ctx *c, cudaStream_t st) {
+  const int nI = c->nI, NT = (nI + 31) / 32;
+  const unsigned blocks = (unsigned)((c->n_m2l_targets + kM2LWarps - 1) / kM2LWarps);
+  const size_t sm = m2l_f32_smem(nI);
+  const float kf = (float)c->kappa;
+  switch (NT) {
+#define EFIE_M2L_CASE(N)                                                                                      \
+  case N:                                                                                                    \
+    k_m2l_f32w<N, RED><<<blocks, 32 * kM2LWarps, sm, st>>>(c->d_m2l_targets, c->n_m2l_targets, c->d_far_ptr,  \
+                                                           c->d_far_src, c->d_pgeo, c->d_pph, nI, kf,          \
+                                                           c->d_nodeX4, c->d_srcf, c->d_accf);                 \
+    ++c->launches;                                                                                           \
+    break;
+    EFIE_M2L_CASE(1)
+    EFIE_M2L_CASE(2)
+    EFIE_M2L_CASE(3)
+    EFIE_M2L_CASE(4)
+    EFIE_M2L_CASE(5)
+    EFIE_M2L_CASE(6)
+    EFIE_M2L_CASE(7)
+    EFIE_M2L_CASE(8)
+    EFIE_M2L_CASE(9)
+    EFIE_M2L_CASE(10)
+#undef EFIE_M2L_CASE
+    default:
+      c->err = "q too large for the FP32 M2L kernel";
+      return EFIE_EINVAL;
+  }
+  return EFIE_OK;
+}
+
+static efie_status launch_m2l_f32(Ctx *c, cudaStream_t st) {
+  return c->m2l_reduce ? launch_m2l_f32_t<true>(c, st) : launch_m2l_f32_t<false>(c, st);
+}
+
+template <bool RED>
+static efie_status m2l_f32_attrs(int bytes) {
+  cudaError_t e = cudaSuccess;
+  for (auto f : {k_m2l_f32w<1, RED>, k_m2l_f32w<2, RED>, k_m2l_f32w<3, RED>, k_m2l_f32w<4, RED>, k_m2l_f32w<5, RED>,
+                 k_m2l_f32w<6, RED>, k_m2l_f32w<7, RED>, k_m2l_f32w<8, RED>, k_m2l_f32w<9, RED>, k_m2l_f32w<10, RED>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e == cudaSuccess ? EFIE_OK : EFIE_ECUDA;
+}
+
+// node offsets (float4) and the per-pair table of the FP32 M2L
+static efie_status m2l_f32_tables(Ctx *c) {
+  const size_t n = (size_t)c->ncl * c->nI;
+  std::vector<float> xf(3 * n);
+  EFIE_CUDA(cudaMemcpy(xf.data(), c->d_nodeXf, 12 * n, cudaMemcpyDeviceToHost));
+  std::vector<float4> x4(n);
+  for (size_t i = 0; i < n; ++i) x4[i] = make_float4(xf[3 * i], xf[3 * i + 1], xf[3 * i + 2], 0.f);
+  EFIE_TRY(dalloc(c, &c->d_nodeX4, n));
+  EFIE_CUDA(cudaMemcpy(c->d_nodeX4, x4.data(), 16 * n, cudaMemcpyHostToDevice));
+  EFIE_TRY(dalloc(c, &c->d_pgeo, (size_t)std::max(c->nfar, 1)));
+  EFIE_TRY(dalloc(c, &c->d_pph, (size_t)std::max(c->nfar, 1)));
+  EFIE_CUDA(cudaDeviceSynchronize());
+  if (c->n_m2l_targets > 0) {
+    k_pair_table<<<(c->n_m2l_targets + 127) / 128, 128, 0, c->stream>>>(c->n_m2l_targets, c->d_m2l_targets,
+                                                                        c->d_far_ptr, c->d_far_src, c->d_center,
+                                                                        c->kappa, c->d_pgeo, c->d_pph);
+    ++c->launches;
+    EFIE_CUDA(cudaGetLastError());
+  }
+  EFIE_TRY(m2l_f32_attrs<true>((int)m2l_f32_smem(kMaxQ1 * kMaxQ1)));
+  EFIE_TRY(m2l_f32_attrs<false>((int)m2l_f32_smem(kMaxQ1 * kMaxQ1)));
+  EFIE_CUDA(cudaStreamSynchronize(c->stream));
+  return EFIE_OK;
+}
 static size_t m2m_smem(int q1, size_t csz) { return sizeof(double) * 2 * kMaxQ1 * kMaxQ1 + csz * 24 * q1 * q1; }
 static size_t l2l_smem(int q1, size_t csz) { return sizeof(double) * 2 * kMaxQ1 * kMaxQ1 + csz * 9 * q1 * q1; }
 
@@ -456,23 +617,31 @@ static efie_status far_chain(Ctx *c, const double2 *xs, double2 *ys, C2<R> *mom,
     k_m2m<R><<<npar, 128, m2m_smem(q1, csz), st>>>(npar, c->lev_off[l], c->lev_off[l + 1], q1, E, mom); ++c->launches;
   }
   long long tot = (long long)c->ncl * nI;
-  k_fold<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(tot, nI, c->d_nodeD, mom, srcv); ++c->launches;
+  const unsigned gtot = (unsigned)((tot + 255) / 256);
+  if (sizeof(R) == 8) {
+    k_fold<double><<<gtot, 256, 0, st>>>(tot, nI, c->d_nodeD, (const double2 *)mom, (double2 *)srcv); ++c->launches;
+  } else {
+    k_fold_f32n<<<gtot, 256, 0, st>>>(tot, nI, c->d_nodeD, (const float2 *)mom, c->d_srcf); ++c->launches;
+  }
   cudaEventRecord(c->tm.ev[3], st);
-  int thr = ((nI + 31) / 32) * 32;
   if (c->n_m2l_targets > 0) {
     if (sizeof(R) == 8) {
+      int thr = ((nI + 31) / 32) * 32;
       size_t sm = sizeof(double) * (3 * nI + 1) + sizeof(double2) * 4 * nI;
       k_m2l_f64<<<c->n_m2l_targets, thr, sm, st>>>(c->d_m2l_targets, c->d_far_ptr, c->d_far_src, nI, c->kappa,
                                                    c->d_nodeX, (const double2 *)srcv, c->d_acc); ++c->launches;
     } else {
-      size_t sm = sizeof(float) * (3 * nI + 1) + sizeof(float2) * 4 * nI;
-      k_m2l_f32<<<c->n_m2l_targets, thr, sm, st>>>(c->d_m2l_targets, c->d_far_ptr, c->d_far_src, nI, c->kappa,
-                                                   c->d_center, c->d_nodeXf, (const float2 *)srcv, c->d_acc); ++c->launches;
+      EFIE_TRY(launch_m2l_f32(c, st));
     }
   }
   cudaEventRecord(c->tm.ev[4], st);
-  k_unfold<R, double2><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(tot, nI, (R)(1.0 / (c->kappa * c->kappa)),
-                                                                     c->d_nodeD, c->d_acc, loc); ++c->launches;
+  if (sizeof(R) == 8) {
+    k_unfold<double, double2><<<gtot, 256, 0, st>>>(tot, nI, 1.0 / (c->kappa * c->kappa), c->d_nodeD, c->d_acc,
+                                                    (double2 *)loc); ++c->launches;
+  } else {
+    k_unfold_f32n<<<gtot, 256, 0, st>>>(tot, nI, (float)(1.0 / (c->kappa * c->kappa)), c->d_nodeD, c->d_accf,
+                                        (float2 *)loc); ++c->launches;
+  }
   for (int l = 0; l < m; ++l) {
     int npar = c->np << (2 * l);
     k_l2l<R><<<npar, 128, l2l_smem(q1, csz), st>>>(npar, c->lev_off[l], c->lev_off[l + 1], q1, E, loc); ++c->launches;
@@ -502,7 +671,7 @@ static efie_status superspace_apply(Ctx *c, const double2 *xs, double2 *ys, doub
   EFIE_CUDA(cudaEventRecord(c->tm.ev[2], c->stream2));
   EFIE_CUDA(cudaEventRecord(c->join, c->stream2));
   if (c->opt.precision == EFIE_MIXED_FP32) {
-    EFIE_TRY(far_chain<float>(c, xs, ys, c->d_momf, c->d_srcf, c->d_locf, c->d_M, c->d_Md, c->d_E));
+    EFIE_TRY(far_chain<float>(c, xs, ys, c->d_momf, nullptr, c->d_locf, c->d_M, c->d_Md, c->d_E));
   } else {
     EFIE_TRY(far_chain<double>(c, xs, ys, c->d_mom, c->d_src, c->d_loc, c->d_M, c->d_Md, c->d_E));
   }
@@ -559,8 +728,11 @@ efie_status dev_alloc_work(Ctx *c) {
   EFIE_CUDA(cudaMemset(c->d_acc, 0, sizeof(double2) * ncl * 4 * nI));
   if (c->opt.precision == EFIE_MIXED_FP32) {
     EFIE_TRY(dalloc(c, &c->d_momf, ncl * 3 * nI));
-    EFIE_TRY(dalloc(c, &c->d_srcf, ncl * 4 * nI));
+    EFIE_TRY(dalloc(c, &c->d_srcf, ncl * 2 * nI));
+    EFIE_TRY(dalloc(c, &c->d_accf, ncl * 2 * nI));
+    EFIE_CUDA(cudaMemset(c->d_accf, 0, sizeof(float4) * ncl * 2 * nI));
     EFIE_TRY(dalloc(c, &c->d_locf, ncl * 3 * nI));
+    EFIE_TRY(m2l_f32_tables(c));
   } else {
     EFIE_TRY(dalloc(c, &c->d_mom, ncl * 3 * nI));
     EFIE_TRY(dalloc(c, &c->d_src, ncl * 4 * nI));

@@ -365,6 +365,12 @@ efie_status host_build_trees(Ctx *c) {
     }
   }
   c->nfar = (int)c->far.size() / 3;
+  // largest phase kappa (r - r0) of the FP32 M2L: |r - r0| <= |offset_t| + |offset_s|, the
+  // offsets bounded by the ball radii (with a margin for the sampled radius)
+  double maxph = 0.0;
+  for (int f = 0; f < c->nfar; ++f)
+    maxph = std::max(maxph, c->kappa * 1.5 * (c->ball[4 * c->far[3 * f + 1] + 3] + c->ball[4 * c->far[3 * f + 2] + 3]));
+  c->m2l_reduce = !(maxph < 100.0 * M_PI);
   c->nnear = (int)c->nearl.size() / 2;
 
   // far pairs as CSR over target clusters (all levels in one list)
@@ -378,6 +384,9 @@ efie_status host_build_trees(Ctx *c) {
   std::vector<int> targets;
   for (int k = 0; k < c->ncl; ++k)
     if (fptr[k + 1] > fptr[k]) targets.push_back(k);
+  // longest source lists first: the M2L kernels take targets in this order
+  std::stable_sort(targets.begin(), targets.end(),
+                   [&](int a, int b) { return fptr[a + 1] - fptr[a] > fptr[b + 1] - fptr[b]; });
   c->n_m2l_targets = (int)targets.size();
   EFIE_TRY(dalloc(c, &c->d_far_ptr, fptr.size()));
   EFIE_TRY(dalloc(c, &c->d_far_src, fsrc.size()));

@@ -304,43 +304,69 @@ efie_status dev_near_quadrature(Ctx *c, const std::vector<NearPair> &pairs, cons
   return EFIE_OK;
 }
 
-// y*_e = sum over near sources e' of N_{e e'} x*_{e'}; one warp per target element, lane r
-// owns rows r and r + 32; blocks are column-major so that a warp reads each column as one
-// contiguous run.
-template <int NB>
-__global__ void k_near_apply(int nE, const int *__restrict__ ptr, const int *__restrict__ src,
-                             const double2 *__restrict__ blocks, const double2 *__restrict__ xs,
-                             double2 *__restrict__ ysn) {
-  constexpr int RPL = (NB + 31) / 32;
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= nE) return;
-  double2 acc[RPL];
+// y*_e = sum over near sources e' of N_{e e'} x*_{e'} (a9).  One block of 4 warps per target
+// element; the element's source blocks are dealt round-robin to lane groups of GS lanes
+// (GS = 8, 16 or 32 >= nb rows, 32/GS groups per warp); lane r of a group owns rows r and
+// r + 32.  Blocks are column-major, so a group reads each column as one contiguous run.
+// The partial rows of the groups and warps are summed in shared memory in a fixed order.
+template <class T> struct CT;
+template <> struct CT<double> { using V = double2; };
+template <> struct CT<float> { using V = float2; };
+
+constexpr int kApplyWarps = 4;
+
+template <class T, int NB>
+__global__ void __launch_bounds__(32 * kApplyWarps) k_near_apply(int nE, const int *__restrict__ ptr,
+                                                                 const int *__restrict__ src,
+                                                                 const typename CT<T>::V *__restrict__ blocks,
+                                                                 const double2 *__restrict__ xs,
+                                                                 double2 *__restrict__ ysn) {
+  using V = typename CT<T>::V;
+  constexpr int GS = NB <= 8 ? 8 : (NB <= 16 ? 16 : 32);
+  constexpr int NG = 32 / GS;                 // groups per warp
+  constexpr int RPL = (NB + GS - 1) / GS;     // rows per lane
+  constexpr int XPL = (NB + GS - 1) / GS;     // x entries per lane
+  __shared__ T red[kApplyWarps * NG][NB][2];
+  const int e = blockIdx.x;
+  if (e >= nE) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / GS, r0 = lane % GS;
+  const int gid = warp * NG + g, ngroups = kApplyWarps * NG;
+  T ar[RPL], ai[RPL];
 #pragma unroll
-  for (int t = 0; t < RPL; ++t) acc[t] = make_double2(0.0, 0.0);
-  for (int k = ptr[warp]; k < ptr[warp + 1]; ++k) {
-    const double2 *B = blocks + (size_t)k * NB * NB;
-    const double2 *x = xs + (size_t)src[k] * NB;
-    double2 xl[RPL];
+  for (int t = 0; t < RPL; ++t) ar[t] = ai[t] = T(0);
+  const int k0 = ptr[e], k1 = ptr[e + 1];
+  // every group walks the same number of iterations so that the shuffles stay uniform
+  for (int kb = k0; kb < k1; kb += ngroups) {
+    const int k = kb + gid;
+    const bool act = k < k1;
+    const V *B = blocks + (size_t)(act ? k : k0) * NB * NB;
+    const double2 *x = xs + (size_t)src[act ? k : k0] * NB;
+    T xr[XPL], xi[XPL];
 #pragma unroll
-    for (int t = 0; t < RPL; ++t) {
-      int cidx = lane + 32 * t;
-      xl[t] = cidx < NB ? x[cidx] : make_double2(0.0, 0.0);
+    for (int t = 0; t < XPL; ++t) {
+      int cidx = r0 + GS * t;
+      double2 v = (act && cidx < NB) ? x[cidx] : make_double2(0.0, 0.0);
+      xr[t] = (T)v.x;
+      xi[t] = (T)v.y;
     }
 #pragma unroll
-    for (int tc = 0; tc < RPL; ++tc) {
-      const int ncol = (NB - 32 * tc) < 32 ? (NB - 32 * tc) : 32;
-#pragma unroll 4
+    for (int tc = 0; tc < XPL; ++tc) {
+      constexpr int dummy = 0;
+      (void)dummy;
+      const int ncol = (NB - GS * tc) < GS ? (NB - GS * tc) : GS;
+#pragma unroll 6
       for (int c0 = 0; c0 < ncol; ++c0) {
-        const int cc = 32 * tc + c0;
-        double xr = __shfl_sync(0xffffffffu, xl[tc].x, c0);
-        double xi = __shfl_sync(0xffffffffu, xl[tc].y, c0);
+        const int cc = GS * tc + c0;
+        T vr = __shfl_sync(0xffffffffu, xr[tc], g * GS + c0);
+        T vi = __shfl_sync(0xffffffffu, xi[tc], g * GS + c0);
 #pragma unroll
         for (int t = 0; t < RPL; ++t) {
-          int rr = lane + 32 * t;
-          if (rr < NB) {
-            double2 b = B[cc * NB + rr];
-            acc[t].x += b.x * xr - b.y * xi;
-            acc[t].y += b.x * xi + b.y * xr;
+          int rr = r0 + GS * t;
+          if (act && rr < NB) {
+            V b = B[cc * NB + rr];
+            ar[t] += b.x * vr - b.y * vi;
+            ai[t] += b.x * vi + b.y * vr;
           }
         }
       }
@@ -348,21 +374,60 @@ __global__ void k_near_apply(int nE, const int *__restrict__ ptr, const int *__r
   }
 #pragma unroll
   for (int t = 0; t < RPL; ++t) {
-    int rr = lane + 32 * t;
-    if (rr < NB) ysn[(size_t)warp * NB + rr] = acc[t];
+    int rr = r0 + GS * t;
+    if (rr < NB) {
+      red[gid][rr][0] = ar[t];
+      red[gid][rr][1] = ai[t];
+    }
+  }
+  __syncthreads();
+  for (int rr = threadIdx.x; rr < NB; rr += blockDim.x) {
+    double sr = 0.0, si = 0.0;
+    for (int q = 0; q < ngroups; ++q) {
+      sr += (double)red[q][rr][0];
+      si += (double)red[q][rr][1];
+    }
+    ysn[(size_t)e * NB + rr] = make_double2(sr, si);
   }
 }
 
+__global__ void k_blocks_to_f32(size_t n, const double2 *__restrict__ in, float2 *__restrict__ out) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+efie_status dev_near_blocks_f32(Ctx *c) {
+  size_t n = (size_t)c->nnear * c->nb * c->nb;
+  EFIE_TRY(dalloc(c, &c->d_nblkf, n));
+  k_blocks_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, c->d_nblk, c->d_nblkf); ++c->launches;
+  EFIE_CUDA(cudaGetLastError());
+  return EFIE_OK;
+}
+
 efie_status dev_near_apply(Ctx *c, const double2 *xs, double2 *ysn, cudaStream_t st) {
-  int threads = 128, blocks = (c->nE * 32 + threads - 1) / threads;
+  const bool f32 = c->opt.precision == EFIE_MIXED_FP32 && c->d_nblkf;
+  const int threads = 32 * kApplyWarps;
   switch (c->nb) {
-    case 8: k_near_apply<8><<<blocks, threads, 0, st>>>(c->nE, c->d_near_ptr, c->d_near_src, c->d_nblk, xs, ysn); break;
-    case 18: k_near_apply<18><<<blocks, threads, 0, st>>>(c->nE, c->d_near_ptr, c->d_near_src, c->d_nblk, xs, ysn); break;
-    case 32: k_near_apply<32><<<blocks, threads, 0, st>>>(c->nE, c->d_near_ptr, c->d_near_src, c->d_nblk, xs, ysn); break;
-    case 50: k_near_apply<50><<<blocks, threads, 0, st>>>(c->nE, c->d_near_ptr, c->d_near_src, c->d_nblk, xs, ysn); break;
-    default: c->err = "unsupported block size"; return EFIE_EINVAL;
+#define EFIE_APPLY_CASE(NBV)                                                                                   \
+  case NBV:                                                                                                   \
+    if (f32)                                                                                                  \
+      k_near_apply<float, NBV><<<c->nE, threads, 0, st>>>(c->nE, c->d_near_ptr, c->d_near_src, c->d_nblkf, xs, \
+                                                          ysn);                                              \
+    else                                                                                                      \
+      k_near_apply<double, NBV><<<c->nE, threads, 0, st>>>(c->nE, c->d_near_ptr, c->d_near_src, c->d_nblk, xs, \
+                                                           ysn);                                             \
+    break;
+    EFIE_APPLY_CASE(8)
+    EFIE_APPLY_CASE(18)
+    EFIE_APPLY_CASE(32)
+    EFIE_APPLY_CASE(50)
+#undef EFIE_APPLY_CASE
+    default:
+      c->err = "unsupported block size";
+      return EFIE_EINVAL;
   }
-  EFIE_CUDA(cudaGetLastError()); ++c->launches;
+  ++c->launches;
+  EFIE_CUDA(cudaGetLastError());
   return EFIE_OK;
 }
 
