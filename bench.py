@@ -271,7 +271,7 @@ def run_gpu(args):
             "frac": achieved / fp32_peak, "traffic": None,
             "peak_note": "FP32 SIMT: 152 SMs x 128 lanes x 2 flop x max SM clock (derived, not measured)",
             "work": f"{n_eval:.3e} kernel entries x {flops_per_eval:.0f} flop per matvec", "m2l_ms": m2l_ms}
-    near_bytes = s.nnear * s.nb * s.nb * 16 + 2 * s.nsup * 16
+    near_bytes = s.nnear * s.nb * s.nb * (8 if prec else 16) + 2 * s.nsup * 16
     near_roof = {"kernel": "k_near_apply", "bound": "hbm", "achieved": near_bytes / (mv["near"] * 1e-3) / 1e9,
                  "peak": pk.get("hbm_gbs"), "unit": "GB/s", "near_ms": mv["near"], "bytes": near_bytes}
     near_roof["frac"] = near_roof["achieved"] / near_roof["peak"]

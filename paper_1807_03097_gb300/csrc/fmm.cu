@@ -301,6 +301,17 @@ __global__ void k_pair_table(int ntarget, const int *__restrict__ targets, const
   }
 }
 
+// s + e = a + b exactly (Knuth two-sum, branch-free); used for the compensated FP32
+// accumulation of per-pair partial sums, which keeps the long sums over all source
+// clusters close to FP64 accuracy
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b) {
+  float s = hi + b;
+  float bp = s - hi;
+  float err = (hi - (s - bp)) + (b - bp);
+  hi = s;
+  lo += err;
+}
+
 // d = a * b + c on two FP32 lanes at once (Blackwell packed FMA)
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
   unsigned long long A = *reinterpret_cast<unsigned long long *>(&a);
@@ -337,7 +348,7 @@ __global__ void __launch_bounds__(128) k_m2l_f32w(const int *__restrict__ target
   const int t = targets[wg];
   const int T = (nI + NT - 1) / NT;
   float xt[NT][3];
-  float2 a[NT][4];
+  float ah[NT][8], al[NT][8];  // compensated accumulators over all source clusters
 #pragma unroll
   for (int j = 0; j < NT; ++j) {
     int mi = lane + j * T;
@@ -346,7 +357,7 @@ __global__ void __launch_bounds__(128) k_m2l_f32w(const int *__restrict__ target
     xt[j][1] = x.y;
     xt[j][2] = x.z;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) a[j][q] = make_float2(0.f, 0.f);
+    for (int q = 0; q < 8; ++q) ah[j][q] = al[j][q] = 0.f;
   }
   const float inv2pi = 0.15915494309189535f, c1 = 6.28318548202514648f, c2 = -1.7484555e-7f;
   for (int k = fptr[t]; k < fptr[t + 1]; ++k) {
@@ -368,6 +379,11 @@ __global__ void __launch_bounds__(128) k_m2l_f32w(const int *__restrict__ target
     }
     __syncwarp();
     const float r0 = g.w, r0sq = g.w * g.w;
+    float2 a[NT][4];  // this pair's partial sums (q + 1)^2 terms
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a[j][q] = make_float2(0.f, 0.f);
 #pragma unroll 2
     for (int mj = 0; mj < nI; ++mj) {
       const float4 xs = sX[mj], wa = sW[2 * mj], wb = sW[2 * mj + 1], ra = sR[2 * mj], rb = sR[2 * mj + 1];
@@ -395,13 +411,23 @@ __global__ void __launch_bounds__(128) k_m2l_f32w(const int *__restrict__ target
         a[j][3] = ffma2(gi, make_float2(rb.z, rb.w), ffma2(gr, make_float2(wb.z, wb.w), a[j][3]));
       }
     }
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        two_sum_acc(ah[j][2 * q], al[j][2 * q], a[j][q].x);
+        two_sum_acc(ah[j][2 * q + 1], al[j][2 * q + 1], a[j][q].y);
+      }
   }
 #pragma unroll
   for (int j = 0; j < NT; ++j) {
     int mi = lane + j * T;
     if (lane < T && mi < nI) {
-      acc[2 * ((size_t)t * nI + mi)] = make_float4(a[j][0].x, a[j][0].y, a[j][1].x, a[j][1].y);
-      acc[2 * ((size_t)t * nI + mi) + 1] = make_float4(a[j][2].x, a[j][2].y, a[j][3].x, a[j][3].y);
+      float o[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) o[q] = ah[j][q] + al[j][q];
+      acc[2 * ((size_t)t * nI + mi)] = make_float4(o[0], o[1], o[2], o[3]);
+      acc[2 * ((size_t)t * nI + mi) + 1] = make_float4(o[4], o[5], o[6], o[7]);
     }
   }
 }

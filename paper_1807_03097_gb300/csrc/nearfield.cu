@@ -9,8 +9,8 @@
 
 namespace efie {
 
-constexpr int kQC = 32;          // quadrature points staged per chunk
-constexpr int kQuadThreads = 256;
+constexpr int kQC = 64;          // quadrature points staged per chunk
+constexpr int kQuadThreads = 2 * kQC;  // one thread per (point, side) in the geometry phase
 
 struct QuadArgs {
   const PatchDesc *patches;
@@ -77,8 +77,8 @@ __device__ inline void canonical_point(int kind, int g, const double *x, const d
 }
 
 // One block per element pair.  Each chunk of kQC points: threads [0, kQC) evaluate the
-// target element, [kQC, 2 kQC) the source element, then every thread accumulates its
-// block entries: B[r][c] += G w (sum_k U_k[r] V_k[c]) with U_k = h^2 d_alpha F_k psi_r
+// target element, [kQC, 2 kQC) the source element (every thread of the block), then every
+// thread accumulates its block entries: B[r][c] += G w (sum_k U_k[r] V_k[c]) with U_k = h^2 d_alpha F_k psi_r
 // (k < 3), U_3 = h d_alpha psi_r, V_3 = -kappa^-2 h d_beta psi_c.
 template <int P>
 __global__ void __launch_bounds__(kQuadThreads) k_near_quad(QuadArgs A) {
@@ -332,9 +332,9 @@ __global__ void __launch_bounds__(32 * kApplyWarps) k_near_apply(int nE, const i
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane / GS, r0 = lane % GS;
   const int gid = warp * NG + g, ngroups = kApplyWarps * NG;
-  T ar[RPL], ai[RPL];
+  T ar[RPL], ai[RPL], cr[RPL], ci[RPL];  // running sums and (FP32) compensation terms
 #pragma unroll
-  for (int t = 0; t < RPL; ++t) ar[t] = ai[t] = T(0);
+  for (int t = 0; t < RPL; ++t) ar[t] = ai[t] = cr[t] = ci[t] = T(0);
   const int k0 = ptr[e], k1 = ptr[e + 1];
   // every group walks the same number of iterations so that the shuffles stay uniform
   for (int kb = k0; kb < k1; kb += ngroups) {
@@ -350,10 +350,11 @@ __global__ void __launch_bounds__(32 * kApplyWarps) k_near_apply(int nE, const i
       xr[t] = (T)v.x;
       xi[t] = (T)v.y;
     }
+    T pr[RPL], pim[RPL];  // this source block's contribution
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) pr[t] = pim[t] = T(0);
 #pragma unroll
     for (int tc = 0; tc < XPL; ++tc) {
-      constexpr int dummy = 0;
-      (void)dummy;
       const int ncol = (NB - GS * tc) < GS ? (NB - GS * tc) : GS;
 #pragma unroll 6
       for (int c0 = 0; c0 < ncol; ++c0) {
@@ -365,19 +366,31 @@ __global__ void __launch_bounds__(32 * kApplyWarps) k_near_apply(int nE, const i
           int rr = r0 + GS * t;
           if (act && rr < NB) {
             V b = B[cc * NB + rr];
-            ar[t] += b.x * vr - b.y * vi;
-            ai[t] += b.x * vi + b.y * vr;
+            pr[t] += b.x * vr - b.y * vi;
+            pim[t] += b.x * vi + b.y * vr;
           }
         }
       }
+    }
+    // per-source partial sums enter the running sums with two-sum compensation (FP32)
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      T sr = ar[t] + pr[t], si = ai[t] + pim[t];
+      if (sizeof(T) == 4) {
+        T br = sr - ar[t], bi = si - ai[t];
+        cr[t] += (ar[t] - (sr - br)) + (pr[t] - br);
+        ci[t] += (ai[t] - (si - bi)) + (pim[t] - bi);
+      }
+      ar[t] = sr;
+      ai[t] = si;
     }
   }
 #pragma unroll
   for (int t = 0; t < RPL; ++t) {
     int rr = r0 + GS * t;
     if (rr < NB) {
-      red[gid][rr][0] = ar[t];
-      red[gid][rr][1] = ai[t];
+      red[gid][rr][0] = ar[t] + cr[t];
+      red[gid][rr][1] = ai[t] + ci[t];
     }
   }
   __syncthreads();

@@ -26,13 +26,21 @@ def main():
     from workloads import geometry as G
 
     geo = {"sphere": G.sphere, "torus": G.torus, "cube": G.cube}[a.geometry]()
+    import time
+
+    t0 = time.perf_counter()
     s = Solver(geo, p=a.p, level_m=a.m, kappa=a.kappa, q=a.q, eta=a.eta, precision=1 if a.precision == "mixed" else 0)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    s.setup()
+    t_setup2 = time.perf_counter() - t0
     rng = np.random.default_rng(0)
     x = rng.standard_normal(s.ndof) + 1j * rng.standard_normal(s.ndof)
     for _ in range(a.matvecs):
         y = s.matvec(x)
     t = s.last_timings()
-    print(f"ndof {s.ndof} far {s.nfar} near {s.nnear} matvec ms " + " ".join(f"{k}={v:.3f}" for k, v in t.items()))
+    print(f"ndof {s.ndof} far {s.nfar} near {s.nnear} setup s {t_setup:.3f} (again {t_setup2:.3f}) matvec ms "
+          + " ".join(f"{k}={v:.3f}" for k, v in t.items()))
     s.close()
 
 
