@@ -167,6 +167,24 @@ efie_status efie_matvec_superspace(efie_ctx *ctx, const double *xs, double *ys, 
  * values written (<= n). */
 int efie_last_timings(const efie_ctx *ctx, double *out, int n);
 
+/* Far field like efie_far_field, for callers that must not allocate device memory during
+ * the call (a process running under a fixed device-memory budget owned by another
+ * allocator, or one that cannot afford cudaMalloc / cudaFree synchronising the device while
+ * its other work is in flight).  The paper has no counterpart; this is a library service.
+ *  w_dev      [ndof] complex, device memory (one right-hand side)
+ *  dirs_dev   [ndir][3] unit directions, device memory
+ *  e_inf_dev  [ndir][3] complex output, device memory
+ * Nothing is allocated: the T gather is fused into the kernel and the partial sums use one
+ * file-scope device array of 2^18 complex doubles (4 MiB) that every GPU loading the library
+ * holds until the process exits.  Limit: 3 * ndir * ceil(elements / 16) <= 2^18, else
+ * EFIE_EINVAL.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture.  All calls on a device share the array and each call rewrites the part it uses
+ * in full; calls that overlap on the GPU (other streams or other contexts on the same
+ * device) race on it.  Ordered on the context stream; returns when the result is complete. */
+efie_status efie_far_field_noalloc(efie_ctx *ctx, const double *w_dev, int ndir, const double *dirs_dev,
+                                   double *e_inf_dev);
+
 /* Number of CUDA kernels this context has launched since efie_create (all phases);
  * -1 for a NULL context. */
 int64_t efie_launch_count(const efie_ctx *ctx);

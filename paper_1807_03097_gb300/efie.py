@@ -26,7 +26,7 @@ ABI_SYMBOLS = (
     "efie_default_options", "efie_create", "efie_set_geometry", "efie_setup", "efie_num_dofs",
     "efie_matvec", "efie_rhs_plane_waves", "efie_solve", "efie_solve_plane_waves", "efie_far_field",
     "efie_block_counts", "efie_export_blocks", "efie_export_near_blocks", "efie_matvec_superspace",
-    "efie_last_timings", "efie_launch_count", "efie_destroy", "efie_status_string",
+    "efie_last_timings", "efie_launch_count", "efie_destroy", "efie_status_string", "efie_far_field_noalloc",
 )
 
 
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
         "efie_matvec_superspace": (c_int, [P, P, P, c_int]),
         "efie_last_timings": (c_int, [P, D, c_int]),
         "efie_launch_count": (ctypes.c_int64, [P]),
+        "efie_far_field_noalloc": (c_int, [P, P, c_int, P, P]),
         "efie_destroy": (c_int, [P]),
         "efie_status_string": (ctypes.c_char_p, [c_int]),
     }
@@ -232,6 +233,17 @@ class Solver:
         pw, kw = _ptr(w)
         po, _ = _ptr(out)
         self._check(self._L.efie_far_field(self.h, nrhs, pw, dirs.shape[0], _d(dirs), po, kw), "efie_far_field")
+        return out
+
+    def far_field_noalloc(self, w, dirs, out):
+        """Far field of one right-hand side without device allocation; w, dirs ([ndir, 3]) and
+        out ([ndir, 3] complex) must be CUDA tensors."""
+        pw, kw = _ptr(w)
+        pd, kd = _ptr(dirs)
+        po, ko = _ptr(out)
+        if not (kw == kd == ko == EFIE_PTR_DEVICE):
+            raise ValueError("far_field_noalloc takes device tensors only")
+        self._check(self._L.efie_far_field_noalloc(self.h, pw, dirs.shape[0], pd, po), "efie_far_field_noalloc")
         return out
 
     def blocks(self):
