@@ -186,7 +186,7 @@ def run_gpu(args):
     geo = G.sphere()
     stream = torch.cuda.current_stream()
     kw = dict(p=w["p"], level_m=w["level_m"], kappa=w["kappa"], q=w["q"], eta=w["eta"], gmres_tol=w["gmres_tol"],
-              gmres_restart=w["gmres_restart"], gmres_maxit=args.maxit)
+              gmres_restart=w["gmres_restart"], gmres_maxit=args.maxit, m2l_store=args.m2l_store)
     prec = 1 if args.precision == "mixed" else 0
     s = Solver(geo, stream=stream.cuda_stream, precision=prec, **kw)
     N = s.ndof
@@ -337,6 +337,8 @@ def main():
     ap.add_argument("--ref-iterations", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-steps", action="store_true", help="time the steps only (for launch-list profiling)")
+    ap.add_argument("--m2l-store", type=int, default=0, choices=[0, 1, 2],
+                    help="M2L coupling matrices: 0 auto (kept in HBM when they fit), 1 evaluated, 2 kept")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

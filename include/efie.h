@@ -77,6 +77,10 @@ typedef struct {
   double gmres_tol;  /* residual tolerance */
   int gmres_maxit;   /* total iteration cap */
   int tol_is_relative; /* 1: ||r|| <= tol ||b||, 0: ||r|| <= tol */
+  int m2l_store;     /* M2L coupling matrices: 0 automatic (FP64 form: kept in device memory
+                        when they take at most half of the free memory; FP32 form: evaluated
+                        in every product, which is faster than streaming them); 1 always
+                        evaluate; 2 always keep (EFIE_ENOMEM if they do not fit) */
 } efie_options;
 
 typedef struct {

@@ -35,7 +35,10 @@ void release_device(Ctx *c) {
   dfree(c->d_x); dfree(c->d_y); dfree(c->d_xs); dfree(c->d_ys); dfree(c->d_ysn);
   dfree(c->d_mom); dfree(c->d_src); dfree(c->d_acc); dfree(c->d_loc);
   dfree(c->d_momf); dfree(c->d_srcf); dfree(c->d_locf); dfree(c->d_accm); dfree(c->d_accf);
-  dfree(c->d_nodeX4); dfree(c->d_pgeo); dfree(c->d_pph);
+  dfree(c->d_nodeX4); dfree(c->d_pgeo); dfree(c->d_pph); dfree(c->d_far_tgt);
+  if (c->d_K) cudaFree(c->d_K);
+  c->d_K = nullptr;
+  c->k_stored = false;
   dfree(c->d_V); dfree(c->d_H); dfree(c->d_h); dfree(c->d_h2); dfree(c->d_part); dfree(c->d_gs);
   dfree(c->d_w); dfree(c->d_r); dfree(c->d_b); dfree(c->d_sol);
   c->kr = 0;
@@ -52,6 +55,7 @@ efie_status check_options(const efie_options *o) {
   if (o->precision != EFIE_FP64 && o->precision != EFIE_MIXED_FP32) return EFIE_EINVAL;
   if (o->quad_regular < 0 || o->quad_regular > 16 || o->quad_singular < 0 || o->quad_singular > 16) return EFIE_EINVAL;
   if (o->gmres_restart < 1 || o->gmres_maxit < 1 || !(o->gmres_tol > 0.0)) return EFIE_EINVAL;
+  if (o->m2l_store < 0 || o->m2l_store > 2) return EFIE_EINVAL;
   return EFIE_OK;
 }
 

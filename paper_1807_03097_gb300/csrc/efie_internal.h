@@ -96,7 +96,10 @@ struct Ctx {
   int *d_far_ptr = nullptr, *d_far_src = nullptr;  // CSR by target cluster
   int *d_m2l_targets = nullptr;
   int n_m2l_targets = 0;
-  bool m2l_reduce = true;  // FP32 M2L reduces phases explicitly (unless all are within +-100 pi)
+  bool m2l_reduce = true;
+  int *d_far_tgt = nullptr;   // target cluster of every far pair (CSR order)
+  void *d_K = nullptr;        // stored coupling matrices [pair][m'][m] (double2 or float2)
+  bool k_stored = false;  // FP32 M2L reduces phases explicitly (unless all are within +-100 pi)
   int *d_near_ptr = nullptr, *d_near_src = nullptr;  // CSR by target element
   double2 *d_nblk = nullptr;  // [nnear][nb (col)][nb (row)]
   float2 *d_nblkf = nullptr;  // FP32 copy of the blocks (mixed-precision apply)

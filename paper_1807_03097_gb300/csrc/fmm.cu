@@ -453,6 +453,170 @@ __global__ void k_unfold_f32n(long long tot, int nI, float ik2, const double *__
   l[2 * nI + mi] = make_float2(-ik2 * v.z, -ik2 * v.w);
 }
 
+// ------------------------------------------------------------------------ a6 M2L, stored matrices
+// When they fit in device memory, the coupling matrices of all admissible blocks are
+// evaluated once at setup, K[k][m'][m] = G(F_t(x_m) - F_s(x_m')) / (4 pi) (column m'
+// contiguous over the target nodes m), and every product streams them from HBM.
+
+__global__ void k_build_K_f64(long long total, int nI, const int *__restrict__ far_tgt, const int *__restrict__ fsrc,
+                              double kappa, const double *__restrict__ nodeX, double2 *__restrict__ K) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const long long nI2 = (long long)nI * nI;
+  const long long k = idx / nI2;
+  const int rem = (int)(idx - k * nI2), mj = rem / nI, mi = rem % nI;
+  const int t = far_tgt[k], s = fsrc[k];
+  const double *xt = nodeX + ((size_t)t * nI + mi) * 3, *xs = nodeX + ((size_t)s * nI + mj) * 3;
+  double dx = xt[0] - xs[0], dy = xt[1] - xs[1], dz = xt[2] - xs[2];
+  double r = sqrt(dx * dx + dy * dy + dz * dz);
+  double sn, cs;
+  sincos(kappa * r, &sn, &cs);
+  double f = 0.25 / (M_PI * r);
+  K[idx] = make_double2(f * cs, f * sn);
+}
+
+// FP32 matrices from the phase-split form with correctly rounded sqrt / division and the
+// full-range sine / cosine (evaluated once, so the accurate functions cost nothing per product).
+__global__ void k_build_K_f32(long long total, int nI, const int *__restrict__ far_tgt, const int *__restrict__ fsrc,
+                              const float4 *__restrict__ pgeo, const float2 *__restrict__ pph, float kappa,
+                              const float4 *__restrict__ nodeX4, float2 *__restrict__ K) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const long long nI2 = (long long)nI * nI;
+  const long long k = idx / nI2;
+  const int rem = (int)(idx - k * nI2), mj = rem / nI, mi = rem % nI;
+  const int t = far_tgt[k], s = fsrc[k];
+  const float4 g = pgeo[k];
+  const float2 ph = pph[k];
+  const float4 xt = nodeX4[(size_t)t * nI + mi], xs = nodeX4[(size_t)s * nI + mj];
+  float ex = xt.x - xs.x, ey = xt.y - xs.y, ez = xt.z - xs.z;
+  float num = 2.f * (g.x * ex + g.y * ey + g.z * ez) + (ex * ex + ey * ey + ez * ez);
+  float r = sqrtf(g.w * g.w + num);
+  float phs = kappa * (num / (r + g.w));
+  float sn, cs;
+  sincosf(phs, &sn, &cs);
+  float gr = cs / r, gi = sn / r;
+  K[idx] = make_float2(ph.x * gr - ph.y * gi, ph.x * gi + ph.y * gr);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(128) k_m2l_f32_stored(const int *__restrict__ targets, int ntarget,
+                                                        const int *__restrict__ fptr, const int *__restrict__ fsrc,
+                                                        const float2 *__restrict__ K, int nI,
+                                                        const float4 *__restrict__ src, float4 *__restrict__ acc) {
+  extern __shared__ float4 sm4[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wg = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (wg >= ntarget) return;
+  float4 *sW = sm4 + (size_t)wib * 4 * nI;  // [nI][2] fields, then [nI][2] rotated copies
+  float4 *sR = sW + 2 * nI;
+  const int t = targets[wg];
+  const int T = (nI + NT - 1) / NT;
+  float ah[NT][8], al[NT][8];
+#pragma unroll
+  for (int j = 0; j < NT; ++j)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ah[j][q] = al[j][q] = 0.f;
+  for (int k = fptr[t]; k < fptr[t + 1]; ++k) {
+    const int s = fsrc[k];
+    __syncwarp();
+    for (int i = lane; i < nI; i += 32) {
+      float4 u = src[2 * ((size_t)s * nI + i)], v = src[2 * ((size_t)s * nI + i) + 1];
+      sW[2 * i] = u;
+      sW[2 * i + 1] = v;
+      sR[2 * i] = make_float4(-u.y, u.x, -u.w, u.z);
+      sR[2 * i + 1] = make_float4(-v.y, v.x, -v.w, v.z);
+    }
+    __syncwarp();
+    const float2 *Kk = K + (size_t)k * nI * nI;
+    float2 a[NT][4];
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a[j][q] = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int mj = 0; mj < nI; ++mj) {
+      const float4 wa = sW[2 * mj], wb = sW[2 * mj + 1], ra = sR[2 * mj], rb = sR[2 * mj + 1];
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const int mi = lane + j * T;
+        const float2 kv = (lane < T && mi < nI) ? __ldcs(Kk + (size_t)mj * nI + mi) : make_float2(0.f, 0.f);
+        const float2 gr = make_float2(kv.x, kv.x), gi = make_float2(kv.y, kv.y);
+        a[j][0] = ffma2(gi, make_float2(ra.x, ra.y), ffma2(gr, make_float2(wa.x, wa.y), a[j][0]));
+        a[j][1] = ffma2(gi, make_float2(ra.z, ra.w), ffma2(gr, make_float2(wa.z, wa.w), a[j][1]));
+        a[j][2] = ffma2(gi, make_float2(rb.x, rb.y), ffma2(gr, make_float2(wb.x, wb.y), a[j][2]));
+        a[j][3] = ffma2(gi, make_float2(rb.z, rb.w), ffma2(gr, make_float2(wb.z, wb.w), a[j][3]));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        two_sum_acc(ah[j][2 * q], al[j][2 * q], a[j][q].x);
+        two_sum_acc(ah[j][2 * q + 1], al[j][2 * q + 1], a[j][q].y);
+      }
+  }
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    int mi = lane + j * T;
+    if (lane < T && mi < nI) {
+      float o[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) o[q] = ah[j][q] + al[j][q];
+      acc[2 * ((size_t)t * nI + mi)] = make_float4(o[0], o[1], o[2], o[3]);
+      acc[2 * ((size_t)t * nI + mi) + 1] = make_float4(o[4], o[5], o[6], o[7]);
+    }
+  }
+}
+
+// FP64 form with stored matrices: warp per target cluster, fields [cluster][4][node].
+template <int NT>
+__global__ void __launch_bounds__(128) k_m2l_f64_stored(const int *__restrict__ targets, int ntarget,
+                                                        const int *__restrict__ fptr, const int *__restrict__ fsrc,
+                                                        const double2 *__restrict__ K, int nI,
+                                                        const double2 *__restrict__ src, double2 *__restrict__ acc) {
+  extern __shared__ double2 smd2[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wg = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (wg >= ntarget) return;
+  double2 *sS = smd2 + (size_t)wib * 4 * nI;
+  const int t = targets[wg];
+  const int T = (nI + NT - 1) / NT;
+  double ar[NT][4], ai[NT][4];
+#pragma unroll
+  for (int j = 0; j < NT; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ar[j][q] = ai[j][q] = 0.0;
+  for (int k = fptr[t]; k < fptr[t + 1]; ++k) {
+    const int s = fsrc[k];
+    __syncwarp();
+    for (int i = lane; i < 4 * nI; i += 32) sS[i] = src[(size_t)s * 4 * nI + i];
+    __syncwarp();
+    const double2 *Kk = K + (size_t)k * nI * nI;
+#pragma unroll 2
+    for (int mj = 0; mj < nI; ++mj) {
+      double2 w[4] = {sS[mj], sS[nI + mj], sS[2 * nI + mj], sS[3 * nI + mj]};
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const int mi = lane + j * T;
+        const double2 kv = (lane < T && mi < nI) ? __ldcs(Kk + (size_t)mj * nI + mi) : make_double2(0.0, 0.0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          ar[j][q] += kv.x * w[q].x - kv.y * w[q].y;
+          ai[j][q] += kv.x * w[q].y + kv.y * w[q].x;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    int mi = lane + j * T;
+    if (lane < T && mi < nI)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[(size_t)t * 4 * nI + q * nI + mi] = make_double2(ar[j][q], ai[j][q]);
+  }
+}
+
 // ------------------------------------------------------------------------ a7 L2L
 // child_c(f, m2', m1') += sum_{m2} E[c2][m2][m2'] sum_{m1} E[c1][m1][m1'] parent(f, m2, m1)
 template <class R>
@@ -594,6 +758,89 @@ static efie_status launch_m2l_f32(Ctx *c, cudaStream_t st) {
   return c->m2l_reduce ? launch_m2l_f32_t<true>(c, st) : launch_m2l_f32_t<false>(c, st);
 }
 
+static efie_status launch_m2l_stored(Ctx *c, cudaStream_t st, bool f32) {
+  const int nI = c->nI, NT = (nI + 31) / 32;
+  const unsigned blocks = (unsigned)((c->n_m2l_targets + kM2LWarps - 1) / kM2LWarps);
+  const size_t sm = (f32 ? sizeof(float4) * 4 : sizeof(double2) * 4) * (size_t)nI * kM2LWarps;
+  switch (NT) {
+#define EFIE_M2LS_CASE(N)                                                                                      \
+  case N:                                                                                                     \
+    if (f32)                                                                                                  \
+      k_m2l_f32_stored<N><<<blocks, 32 * kM2LWarps, sm, st>>>(c->d_m2l_targets, c->n_m2l_targets, c->d_far_ptr, \
+                                                              c->d_far_src, (const float2 *)c->d_K, nI,        \
+                                                              c->d_srcf, c->d_accf);                          \
+    else                                                                                                      \
+      k_m2l_f64_stored<N><<<blocks, 32 * kM2LWarps, sm, st>>>(c->d_m2l_targets, c->n_m2l_targets, c->d_far_ptr, \
+                                                              c->d_far_src, (const double2 *)c->d_K, nI,       \
+                                                              c->d_src, c->d_acc);                            \
+    ++c->launches;                                                                                            \
+    break;
+    EFIE_M2LS_CASE(1)
+    EFIE_M2LS_CASE(2)
+    EFIE_M2LS_CASE(3)
+    EFIE_M2LS_CASE(4)
+    EFIE_M2LS_CASE(5)
+    EFIE_M2LS_CASE(6)
+    EFIE_M2LS_CASE(7)
+    EFIE_M2LS_CASE(8)
+    EFIE_M2LS_CASE(9)
+    EFIE_M2LS_CASE(10)
+#undef EFIE_M2LS_CASE
+    default:
+      c->err = "q too large for the stored-matrix M2L kernel";
+      return EFIE_EINVAL;
+  }
+  return EFIE_OK;
+}
+
+// Decide whether the coupling matrices are kept (m2l_store option) and evaluate them.
+static efie_status m2l_store_matrices(Ctx *c) {
+  if (c->d_K) cudaFree(c->d_K);
+  c->d_K = nullptr;
+  c->k_stored = false;
+  if (c->nfar == 0 || c->opt.m2l_store == 1) return EFIE_OK;
+  const bool f32 = c->opt.precision == EFIE_MIXED_FP32;
+  const size_t nI2 = (size_t)c->nI * c->nI;
+  const size_t bytes = (size_t)c->nfar * nI2 * (f32 ? sizeof(float2) : sizeof(double2));
+  size_t freeb = 0, totb = 0;
+  EFIE_CUDA(cudaMemGetInfo(&freeb, &totb));
+  // auto: keep them for the FP64 form only (evaluating FP64 sine / cosine / sqrt is the
+  // bottleneck of that form on this GPU, while the FP32 form evaluates faster than HBM can
+  // stream the stored matrices)
+  if (c->opt.m2l_store == 0 && (f32 || bytes > freeb / 2)) return EFIE_OK;
+  if (cudaMalloc(&c->d_K, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    c->d_K = nullptr;
+    if (c->opt.m2l_store == 2) {
+      c->err = "coupling matrices do not fit in device memory";
+      return EFIE_ENOMEM;
+    }
+    return EFIE_OK;
+  }
+  const long long total = (long long)c->nfar * (long long)nI2;
+  const unsigned grid = (unsigned)((total + 255) / 256);
+  if (f32)
+    k_build_K_f32<<<grid, 256, 0, c->stream>>>(total, c->nI, c->d_far_tgt, c->d_far_src, c->d_pgeo, c->d_pph,
+                                               (float)c->kappa, c->d_nodeX4, (float2 *)c->d_K);
+  else
+    k_build_K_f64<<<grid, 256, 0, c->stream>>>(total, c->nI, c->d_far_tgt, c->d_far_src, c->kappa, c->d_nodeX,
+                                               (double2 *)c->d_K);
+  ++c->launches;
+  EFIE_CUDA(cudaGetLastError());
+  EFIE_CUDA(cudaStreamSynchronize(c->stream));
+  const int smb = (int)(sizeof(double2) * 4 * kMaxQ1 * kMaxQ1 * kM2LWarps);
+  for (auto f : {k_m2l_f32_stored<1>, k_m2l_f32_stored<2>, k_m2l_f32_stored<3>, k_m2l_f32_stored<4>,
+                 k_m2l_f32_stored<5>, k_m2l_f32_stored<6>, k_m2l_f32_stored<7>, k_m2l_f32_stored<8>,
+                 k_m2l_f32_stored<9>, k_m2l_f32_stored<10>})
+    EFIE_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+  for (auto f : {k_m2l_f64_stored<1>, k_m2l_f64_stored<2>, k_m2l_f64_stored<3>, k_m2l_f64_stored<4>,
+                 k_m2l_f64_stored<5>, k_m2l_f64_stored<6>, k_m2l_f64_stored<7>, k_m2l_f64_stored<8>,
+                 k_m2l_f64_stored<9>, k_m2l_f64_stored<10>})
+    EFIE_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+  c->k_stored = true;
+  return EFIE_OK;
+}
+
 template <bool RED>
 static efie_status m2l_f32_attrs(int bytes) {
   cudaError_t e = cudaSuccess;
@@ -650,7 +897,9 @@ static efie_status far_chain(Ctx *c, const double2 *xs, double2 *ys, C2<R> *mom,
     k_fold_f32n<<<gtot, 256, 0, st>>>(tot, nI, c->d_nodeD, (const float2 *)mom, c->d_srcf); ++c->launches;
   }
   cudaEventRecord(c->tm.ev[3], st);
-  if (c->n_m2l_targets > 0) {
+  if (c->n_m2l_targets > 0 && c->k_stored) {
+    EFIE_TRY(launch_m2l_stored(c, st, sizeof(R) == 4));
+  } else if (c->n_m2l_targets > 0) {
     if (sizeof(R) == 8) {
       int thr = ((nI + 31) / 32) * 32;
       size_t sm = sizeof(double) * (3 * nI + 1) + sizeof(double2) * 4 * nI;
@@ -771,7 +1020,8 @@ efie_status dev_alloc_work(Ctx *c) {
   EFIE_CUDA(cudaMemcpy(c->d_Md, c->tab.Md.data(), 8 * c->tab.Md.size(), cudaMemcpyHostToDevice));
   EFIE_CUDA(cudaMemcpy(c->d_E, c->tab.E.data(), 8 * c->tab.E.size(), cudaMemcpyHostToDevice));
   EFIE_CUDA(cudaDeviceSynchronize());
-  return dev_set_kernel_attrs(c);
+  EFIE_TRY(dev_set_kernel_attrs(c));
+  return m2l_store_matrices(c);
 }
 
 }  // namespace efie

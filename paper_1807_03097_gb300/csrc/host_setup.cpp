@@ -388,6 +388,11 @@ efie_status host_build_trees(Ctx *c) {
   std::stable_sort(targets.begin(), targets.end(),
                    [&](int a, int b) { return fptr[a + 1] - fptr[a] > fptr[b + 1] - fptr[b]; });
   c->n_m2l_targets = (int)targets.size();
+  std::vector<int> ftgt(std::max(c->nfar, 1), 0);
+  for (int k = 0; k < c->ncl; ++k)
+    for (int f = fptr[k]; f < fptr[k + 1]; ++f) ftgt[f] = k;
+  EFIE_TRY(dalloc(c, &c->d_far_tgt, ftgt.size()));
+  EFIE_CUDA(cudaMemcpy(c->d_far_tgt, ftgt.data(), ftgt.size() * 4, cudaMemcpyHostToDevice));
   EFIE_TRY(dalloc(c, &c->d_far_ptr, fptr.size()));
   EFIE_TRY(dalloc(c, &c->d_far_src, fsrc.size()));
   EFIE_TRY(dalloc(c, &c->d_m2l_targets, targets.size()));

@@ -16,16 +16,18 @@ def big():
 
     geo = G.sphere()
     kw = dict(p=2, level_m=5, kappa=10.0, q=8, eta=1.6)
-    s64 = Solver(geo, **kw)
-    s32 = Solver(geo, precision=1, **kw)
+    s64 = Solver(geo, m2l_store=2, **kw)
+    s32 = Solver(geo, precision=1, m2l_store=2, **kw)
+    s32e = Solver(geo, precision=1, m2l_store=1, **kw)
     r = O.Problem(geo, p=2, m=5, kappa=10.0, q=8, eta=1.6)
-    yield s64, s32, r
+    yield s64, s32, s32e, r
     s64.close()
     s32.close()
+    s32e.close()
 
 
 def test_fullsize_counts(big):
-    s64, s32, r = big
+    s64, s32, s32e, r = big
     assert s64.ndof == r.ndof == 2 * 6 * (32 + 2 - 1) ** 2 == 13068
     far, near = s64.blocks()
     assert len(far) == len(r.far_pairs()) and len(near) == len(r.near_pairs())
@@ -33,11 +35,12 @@ def test_fullsize_counts(big):
 
 
 def test_fullsize_sampled_rows(big):
-    s64, s32, r = big
+    s64, s32, s32e, r = big
     rng = np.random.default_rng(42)
     xs = rng.standard_normal(s64.nsup) + 1j * rng.standard_normal(s64.nsup)
     y64 = s64.matvec_superspace(xs).reshape(-1, s64.nb if hasattr(s64, "nb") else 18)
     y32 = s32.matvec_superspace(xs).reshape(y64.shape)
+    y32e = s32e.matvec_superspace(xs).reshape(y64.shape)
     # corner elements of two patches, an edge element, interior elements
     n2 = 32 * 32
     elems = np.array([0, 5, n2 - 1, 3 * n2 + 517, 5 * n2 + 1000])
@@ -45,3 +48,4 @@ def test_fullsize_sampled_rows(big):
     scale = np.abs(rows).max()
     assert np.abs(y64[elems] - rows).max() / scale < 1e-11
     assert np.abs(y32[elems] - rows).max() / scale < 1e-5
+    assert np.abs(y32e[elems] - rows).max() / scale < 1e-5

@@ -29,15 +29,19 @@ def relmax(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-@pytest.fixture(scope="module", params=list(CASES))
+@pytest.fixture(scope="module", params=[(c, st) for c in CASES for st in (1, 2)],
+                ids=[f"{c}-{'evaluated' if st == 1 else 'stored'}" for c in CASES for st in (1, 2)])
 def pair(request):
+    """The FP64 library with M2L coupling matrices evaluated in every product (m2l_store=1)
+    or kept in device memory (m2l_store=2), and the oracle."""
     from paper_1807_03097_gb300 import Solver
 
-    mk, p, m, k, q, eta = CASES[request.param]
+    name, store = request.param
+    mk, p, m, k, q, eta = CASES[name]
     geo = mk()
-    s = Solver(geo, p=p, level_m=m, kappa=k, q=q, eta=eta)
+    s = Solver(geo, p=p, level_m=m, kappa=k, q=q, eta=eta, m2l_store=store)
     r = O.Problem(geo, p=p, m=m, kappa=k, q=q, eta=eta)
-    yield request.param, s, r
+    yield name, s, r
     s.close()
 
 
@@ -101,12 +105,13 @@ def test_device_pointers_match_host_pointers(pair):
     assert np.array_equal(yd.cpu().numpy(), yh)
 
 
-def test_mixed_precision_matvec():
+@pytest.mark.parametrize("store", [1, 2], ids=["evaluated", "stored"])
+def test_mixed_precision_matvec(store):
     from paper_1807_03097_gb300 import Solver
 
     for mk, p, m, k, q in [(G.sphere, 1, 2, 1.0, 4), (G.torus, 2, 1, 2.0, 5)]:
         geo = mk()
-        s = Solver(geo, p=p, level_m=m, kappa=k, q=q, eta=1.6, precision=1)
+        s = Solver(geo, p=p, level_m=m, kappa=k, q=q, eta=1.6, precision=1, m2l_store=store)
         r = O.Problem(geo, p=p, m=m, kappa=k, q=q, eta=1.6)
         rng = np.random.default_rng(3)
         x = rng.standard_normal(s.ndof) + 1j * rng.standard_normal(s.ndof)
