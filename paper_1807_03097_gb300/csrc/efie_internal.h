@@ -96,7 +96,7 @@ struct Ctx {
   int *d_far_ptr = nullptr, *d_far_src = nullptr;  // CSR by target cluster
   int *d_m2l_targets = nullptr;
   int n_m2l_targets = 0;
-  bool m2l_reduce = true;
+  int m2l_mode = 2;  // FP32 M2L phase: 0 direct kappa r - kappa r0, 1 split, 2 split + explicit reduction
   int *d_far_tgt = nullptr;   // target cluster of every far pair (CSR order)
   void *d_K = nullptr;        // stored coupling matrices [pair][m'][m] (double2 or float2)
   bool k_stored = false;  // FP32 M2L reduces phases explicitly (unless all are within +-100 pi)

@@ -329,11 +329,13 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
 //   r - r0 = num / (r + r0),  G = e^{i kappa r0}/(4 pi) * e^{i kappa (r - r0)} / r.
 // The pair factor e^{i kappa r0}/(4 pi) is applied to the source fields while they are
 // staged in shared memory, together with the rotated copy (-Im, Re) that lets a complex
-// multiply-add run as two packed FMAs.  REDUCE: phase reduced to [-pi, pi] by two-constant
-// Cody-Waite before the hardware sine / cosine; without it the host has checked that every
-// phase lies within +-100 pi.
-template <int NT, bool REDUCE>
-__global__ void __launch_bounds__(128) k_m2l_f32w(const int *__restrict__ targets, int ntarget,
+// multiply-add run as two packed FMAs.  MODE 2: phase reduced to [-pi, pi] by two-constant
+// Cody-Waite before the hardware sine / cosine; MODE 1: the host has checked that every
+// phase lies within +-100 pi; MODE 0 (direct): the host has checked that
+// kappa * max r * 2^-24 < 2e-6, and the phase is taken as kappa r - kappa r0 with
+// r = |d + x_t - x_s| (a fixed perturbation of the matrix, below 2e-6 rad per entry).
+template <int NT, int MODE>
+__global__ void __launch_bounds__(128, (NT <= 3 ? 4 : 2)) k_m2l_f32w(const int *__restrict__ targets, int ntarget,
                                                   const int *__restrict__ fptr, const int *__restrict__ fsrc,
                                                   const float4 *__restrict__ pgeo, const float2 *__restrict__ pph,
                                                   int nI, float kappa, const float4 *__restrict__ nodeX4,
@@ -378,7 +380,14 @@ __global__ void __launch_bounds__(128) k_m2l_f32w(const int *__restrict__ target
       sR[2 * i + 1] = make_float4(-pv.y, pv.x, -pv.w, pv.z);
     }
     __syncwarp();
-    const float r0 = g.w, r0sq = g.w * g.w;
+    const float r0 = g.w, r0sq = g.w * g.w, kr0 = kappa * g.w;
+    float ut[NT][3];  // d + x_t (direct mode)
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      ut[j][0] = g.x + xt[j][0];
+      ut[j][1] = g.y + xt[j][1];
+      ut[j][2] = g.z + xt[j][2];
+    }
     float2 a[NT][4];  // this pair's partial sums (q + 1)^2 terms
 #pragma unroll
     for (int j = 0; j < NT; ++j)
@@ -389,18 +398,26 @@ __global__ void __launch_bounds__(128) k_m2l_f32w(const int *__restrict__ target
       const float4 xs = sX[mj], wa = sW[2 * mj], wb = sW[2 * mj + 1], ra = sR[2 * mj], rb = sR[2 * mj + 1];
 #pragma unroll
       for (int j = 0; j < NT; ++j) {
-        float ex = xt[j][0] - xs.x, ey = xt[j][1] - xs.y, ez = xt[j][2] - xs.z;
-        float de = g.x * ex + g.y * ey + g.z * ez;
-        float ee = ex * ex + ey * ey + ez * ez;
-        float num = fmaf(2.f, de, ee);
-        float r2 = r0sq + num;
-        float rinv = rsqrtf(r2);
-        float r = r2 * rinv;
-        float phs = kappa * __fdividef(num, r + r0);
-        if (REDUCE) {
-          float kk = rintf(phs * inv2pi);
-          phs = fmaf(-kk, c1, phs);
-          phs = fmaf(-kk, c2, phs);
+        float rinv, phs;
+        if (MODE == 0) {
+          float vx = ut[j][0] - xs.x, vy = ut[j][1] - xs.y, vz = ut[j][2] - xs.z;
+          float r2 = vx * vx + vy * vy + vz * vz;
+          rinv = rsqrtf(r2);
+          phs = fmaf(kappa, r2 * rinv, -kr0);
+        } else {
+          float ex = xt[j][0] - xs.x, ey = xt[j][1] - xs.y, ez = xt[j][2] - xs.z;
+          float de = g.x * ex + g.y * ey + g.z * ez;
+          float ee = ex * ex + ey * ey + ez * ez;
+          float num = fmaf(2.f, de, ee);
+          float r2 = r0sq + num;
+          rinv = rsqrtf(r2);
+          float r = r2 * rinv;
+          phs = kappa * __fdividef(num, r + r0);
+          if (MODE == 2) {
+            float kk = rintf(phs * inv2pi);
+            phs = fmaf(-kk, c1, phs);
+            phs = fmaf(-kk, c2, phs);
+          }
         }
         float sn, cs;
         __sincosf(phs, &sn, &cs);
@@ -722,7 +739,7 @@ constexpr int kM2LWarps = 4;
 
 static size_t m2l_f32_smem(int nI) { return sizeof(float4) * 5 * (size_t)nI * kM2LWarps; }
 
-template <bool RED>
+template <int MODE>
 static efie_status launch_m2l_f32_t(Ctx *c, cudaStream_t st) {
   const int nI = c->nI, NT = (nI + 31) / 32;
   const unsigned blocks = (unsigned)((c->n_m2l_targets + kM2LWarps - 1) / kM2LWarps);
@@ -731,7 +748,7 @@ static efie_status launch_m2l_f32_t(Ctx *c, cudaStream_t st) {
   switch (NT) {
 #define EFIE_M2L_CASE(N)                                                                                      \
   case N:                                                                                                    \
-    k_m2l_f32w<N, RED><<<blocks, 32 * kM2LWarps, sm, st>>>(c->d_m2l_targets, c->n_m2l_targets, c->d_far_ptr,  \
+    k_m2l_f32w<N, MODE><<<blocks, 32 * kM2LWarps, sm, st>>>(c->d_m2l_targets, c->n_m2l_targets, c->d_far_ptr,  \
                                                            c->d_far_src, c->d_pgeo, c->d_pph, nI, kf,          \
                                                            c->d_nodeX4, c->d_srcf, c->d_accf);                 \
     ++c->launches;                                                                                           \
@@ -755,7 +772,9 @@ static efie_status launch_m2l_f32_t(Ctx *c, cudaStream_t st) {
 }
 
 static efie_status launch_m2l_f32(Ctx *c, cudaStream_t st) {
-  return c->m2l_reduce ? launch_m2l_f32_t<true>(c, st) : launch_m2l_f32_t<false>(c, st);
+  if (c->m2l_mode == 0) return launch_m2l_f32_t<0>(c, st);
+  if (c->m2l_mode == 1) return launch_m2l_f32_t<1>(c, st);
+  return launch_m2l_f32_t<2>(c, st);
 }
 
 static efie_status launch_m2l_stored(Ctx *c, cudaStream_t st, bool f32) {
@@ -841,11 +860,12 @@ static efie_status m2l_store_matrices(Ctx *c) {
   return EFIE_OK;
 }
 
-template <bool RED>
+template <int MODE>
 static efie_status m2l_f32_attrs(int bytes) {
   cudaError_t e = cudaSuccess;
-  for (auto f : {k_m2l_f32w<1, RED>, k_m2l_f32w<2, RED>, k_m2l_f32w<3, RED>, k_m2l_f32w<4, RED>, k_m2l_f32w<5, RED>,
-                 k_m2l_f32w<6, RED>, k_m2l_f32w<7, RED>, k_m2l_f32w<8, RED>, k_m2l_f32w<9, RED>, k_m2l_f32w<10, RED>})
+  for (auto f : {k_m2l_f32w<1, MODE>, k_m2l_f32w<2, MODE>, k_m2l_f32w<3, MODE>, k_m2l_f32w<4, MODE>,
+                 k_m2l_f32w<5, MODE>, k_m2l_f32w<6, MODE>, k_m2l_f32w<7, MODE>, k_m2l_f32w<8, MODE>,
+                 k_m2l_f32w<9, MODE>, k_m2l_f32w<10, MODE>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   return e == cudaSuccess ? EFIE_OK : EFIE_ECUDA;
 }
@@ -869,8 +889,9 @@ static efie_status m2l_f32_tables(Ctx *c) {
     ++c->launches;
     EFIE_CUDA(cudaGetLastError());
   }
-  EFIE_TRY(m2l_f32_attrs<true>((int)m2l_f32_smem(kMaxQ1 * kMaxQ1)));
-  EFIE_TRY(m2l_f32_attrs<false>((int)m2l_f32_smem(kMaxQ1 * kMaxQ1)));
+  EFIE_TRY(m2l_f32_attrs<0>((int)m2l_f32_smem(kMaxQ1 * kMaxQ1)));
+  EFIE_TRY(m2l_f32_attrs<1>((int)m2l_f32_smem(kMaxQ1 * kMaxQ1)));
+  EFIE_TRY(m2l_f32_attrs<2>((int)m2l_f32_smem(kMaxQ1 * kMaxQ1)));
   EFIE_CUDA(cudaStreamSynchronize(c->stream));
   return EFIE_OK;
 }

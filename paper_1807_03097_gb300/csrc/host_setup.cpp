@@ -367,10 +367,16 @@ efie_status host_build_trees(Ctx *c) {
   c->nfar = (int)c->far.size() / 3;
   // largest phase kappa (r - r0) of the FP32 M2L: |r - r0| <= |offset_t| + |offset_s|, the
   // offsets bounded by the ball radii (with a margin for the sampled radius)
-  double maxph = 0.0;
-  for (int f = 0; f < c->nfar; ++f)
-    maxph = std::max(maxph, c->kappa * 1.5 * (c->ball[4 * c->far[3 * f + 1] + 3] + c->ball[4 * c->far[3 * f + 2] + 3]));
-  c->m2l_reduce = !(maxph < 100.0 * M_PI);
+  // and the largest distance kappa r, which bounds the FP32 rounding of a direct phase
+  double maxph = 0.0, maxkr = 0.0;
+  for (int f = 0; f < c->nfar; ++f) {
+    const double *bt = &c->ball[4 * c->far[3 * f + 1]], *bs = &c->ball[4 * c->far[3 * f + 2]];
+    maxph = std::max(maxph, c->kappa * 1.5 * (bt[3] + bs[3]));
+    maxkr = std::max(maxkr, c->kappa * (pdist(bt, bs) + 1.5 * (bt[3] + bs[3])));
+  }
+  if (!(maxph < 100.0 * M_PI)) c->m2l_mode = 2;
+  else if (maxkr * std::ldexp(1.0, -24) < 2e-6) c->m2l_mode = 0;
+  else c->m2l_mode = 1;
   c->nnear = (int)c->nearl.size() / 2;
 
   // far pairs as CSR over target clusters (all levels in one list)
