@@ -43,6 +43,7 @@ extern "C" {
 typedef int efie_status;
 #define EFIE_OK 0
 #define EFIE_NOT_CONVERGED 1  /* GMRES reached gmres_maxit; output holds the last iterate */
+#define EFIE_PENDING 2        /* efie_server_poll: the request has not finished yet */
 #define EFIE_EINVAL -1        /* invalid argument (null pointer, size or option out of range) */
 #define EFIE_ENOMEM -2        /* device or host allocation failed */
 #define EFIE_EGEOMETRY -3     /* open, non-manifold, inward-oriented or mismatched patches */
@@ -195,6 +196,54 @@ int64_t efie_launch_count(const efie_ctx *ctx);
 
 /* Releases all device and host memory of the context (NULL is accepted). */
 efie_status efie_destroy(efie_ctx *ctx);
+
+/* ---------------------------------------------------------------------------------------
+ * Serving: a request loop that admits scattering solves of different geometries, sizes and
+ * wavenumbers while others run.  Requests wait in a queue; whenever a slot is free, the
+ * oldest queued request whose estimated device-memory footprint (near-field blocks, Krylov
+ * basis, cluster data) fits the remaining budget is admitted (so small requests may pass a
+ * large one that does not fit yet; a request larger than the whole budget runs alone).
+ * Each admitted request runs the ordinary per-context path (efie_create, set_geometry,
+ * setup, solve_plane_waves, far_field) on its own worker thread and CUDA stream, so the
+ * work of several requests overlaps on the GPU.  Results do not depend on what else runs:
+ * every reduction has a fixed order. */
+typedef struct efie_server efie_server;
+
+typedef struct {
+  int n_patches;           /* geometry as in efie_set_geometry (host, deep-copied at submit) */
+  const int *deg, *ncp;
+  const double *knots, *cp, *w;
+  efie_options opt;        /* discretisation and solver options of this request */
+  int nrhs;                /* incident plane waves */
+  const double *dir, *pol; /* [nrhs][3] */
+  int ndir;                /* far-field directions (0: none) */
+  const double *ff_dirs;   /* [ndir][3] */
+  double *w_out;           /* [nrhs][2 N (2^m + p - 1)^2] complex, caller-owned; must stay valid
+                              until efie_server_poll has returned EFIE_OK for this ticket */
+  double *e_inf_out;       /* [nrhs][ndir][3] complex, caller-owned (ndir > 0) */
+} efie_request;
+
+typedef struct {
+  efie_status status;      /* status of the solve (EFIE_OK, EFIE_NOT_CONVERGED or an error) */
+  int iterations;          /* largest GMRES iteration count over the request's waves */
+  double residual;
+  int64_t ndof;
+  double queue_ms;         /* submit -> admitted */
+  double latency_ms;       /* submit -> result in the caller's buffers */
+  double setup_ms, solve_ms;
+} efie_result;
+
+/* Starts max_slots worker threads on the current CUDA device with a device-memory budget in
+ * bytes.  Errors: EFIE_EINVAL (max_slots outside 1..64, zero budget), EFIE_ECUDA. */
+efie_status efie_server_create(efie_server **out, size_t hbm_budget_bytes, int max_slots);
+/* Queues a request (non-blocking) and returns its ticket.  Errors: EFIE_EINVAL. */
+efie_status efie_server_submit(efie_server *srv, const efie_request *req, uint64_t *ticket);
+/* EFIE_PENDING while the request is queued or running; EFIE_OK once its outputs are in the
+ * caller's buffers, with *res filled (the ticket is then released); EFIE_EINVAL for an
+ * unknown ticket. */
+efie_status efie_server_poll(efie_server *srv, uint64_t ticket, efie_result *res);
+/* Waits for every queued and running request, then stops the workers. */
+efie_status efie_server_destroy(efie_server *srv);
 
 /* Static description of a status code. */
 const char *efie_status_string(efie_status s);

@@ -16,7 +16,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libefie.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["abi.cu", "geom.cu", "nearfield.cu", "fmm.cu", "gmres.cu", "rhs_ff.cu", "noalloc.cu", "host_setup.cpp"]
+SOURCES = ["abi.cu", "geom.cu", "nearfield.cu", "fmm.cu", "gmres.cu", "rhs_ff.cu", "noalloc.cu", "host_setup.cpp", "server.cpp"]
 
 
 def nvcc() -> str:
@@ -43,7 +43,7 @@ def build(verbose: bool = False, extra=()) -> str:
     os.makedirs(OUT, exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, list(extra)), SOURCES))
-    cmd = [nvcc(), "-shared", *ARCH, "-o", LIB, *objs, "-lcudart"]
+    cmd = [nvcc(), "-shared", *ARCH, "-o", LIB, *objs, "-lcudart", "-Xcompiler", "-pthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

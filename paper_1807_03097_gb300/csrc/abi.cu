@@ -73,6 +73,7 @@ const char *efie_status_string(efie_status s) {
     case EFIE_ECUDA: return "CUDA error";
     case EFIE_ESTATE: return "call out of order";
     case EFIE_ETIMEOUT: return "device wait timed out";
+    case EFIE_PENDING: return "request pending";
     default: return "unknown status";
   }
 }

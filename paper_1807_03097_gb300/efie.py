@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libefie.so")
 
 EFIE_OK = 0
 EFIE_NOT_CONVERGED = 1
+EFIE_PENDING = 2
 EFIE_FP64 = 0
 EFIE_MIXED_FP32 = 1
 EFIE_PTR_HOST = 0
@@ -27,6 +28,7 @@ ABI_SYMBOLS = (
     "efie_matvec", "efie_rhs_plane_waves", "efie_solve", "efie_solve_plane_waves", "efie_far_field",
     "efie_block_counts", "efie_export_blocks", "efie_export_near_blocks", "efie_matvec_superspace",
     "efie_last_timings", "efie_launch_count", "efie_destroy", "efie_status_string", "efie_far_field_noalloc",
+    "efie_server_create", "efie_server_submit", "efie_server_poll", "efie_server_destroy",
 )
 
 
@@ -39,6 +41,19 @@ class EfieOptions(ctypes.Structure):
 
 class EfieSolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("residual", ctypes.c_double),
+                ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+
+
+class EfieRequest(ctypes.Structure):
+    _fields_ = [("n_patches", ctypes.c_int), ("deg", ctypes.c_void_p), ("ncp", ctypes.c_void_p),
+                ("knots", ctypes.c_void_p), ("cp", ctypes.c_void_p), ("w", ctypes.c_void_p), ("opt", EfieOptions),
+                ("nrhs", ctypes.c_int), ("dir", ctypes.c_void_p), ("pol", ctypes.c_void_p), ("ndir", ctypes.c_int),
+                ("ff_dirs", ctypes.c_void_p), ("w_out", ctypes.c_void_p), ("e_inf_out", ctypes.c_void_p)]
+
+
+class EfieResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("residual", ctypes.c_double),
+                ("ndof", ctypes.c_int64), ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
                 ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double)]
 
 
@@ -81,6 +96,10 @@ def load(path: str = LIB_PATH):
         "efie_last_timings": (c_int, [P, D, c_int]),
         "efie_launch_count": (ctypes.c_int64, [P]),
         "efie_far_field_noalloc": (c_int, [P, P, c_int, P, P]),
+        "efie_server_create": (c_int, [ctypes.POINTER(P), ctypes.c_size_t, c_int]),
+        "efie_server_submit": (c_int, [P, ctypes.POINTER(EfieRequest), ctypes.POINTER(ctypes.c_uint64)]),
+        "efie_server_poll": (c_int, [P, ctypes.c_uint64, ctypes.POINTER(EfieResult)]),
+        "efie_server_destroy": (c_int, [P]),
         "efie_destroy": (c_int, [P]),
         "efie_status_string": (ctypes.c_char_p, [c_int]),
     }
@@ -265,3 +284,72 @@ class Solver:
         out = np.zeros(7)
         n = self._L.efie_last_timings(self.h, _d(out), 7)
         return dict(zip(["total", "gather", "near", "moments_m2m", "m2l", "l2l_eval", "scatter"], out[:n]))
+
+
+class Server:
+    """Serving loop of the library: submit scattering requests, poll for results."""
+
+    def __init__(self, hbm_budget_bytes, max_slots):
+        self._L = load()
+        h = ctypes.c_void_p()
+        st = self._L.efie_server_create(ctypes.byref(h), int(hbm_budget_bytes), int(max_slots))
+        if st < 0:
+            raise EfieError(st, "efie_server_create", self._L)
+        self.h = h
+        self._keep = {}
+
+    def submit(self, patches, dirs, pols, ff_dirs=None, **opts):
+        """Queue a request; returns a ticket.  Output arrays are allocated here and returned
+        by poll()."""
+        from workloads.geometry import flatten
+
+        deg, ncp, knots, cp, w = flatten(patches)
+        o = options(**opts)
+        dirs = np.ascontiguousarray(dirs, float).reshape(-1, 3)
+        pols = np.ascontiguousarray(pols, float).reshape(-1, 3)
+        n = 1 << o.level_m
+        ndof = 2 * len(patches) * (n + o.p - 1) ** 2
+        w_out = np.zeros((dirs.shape[0], ndof), np.complex128)
+        ff = None if ff_dirs is None else np.ascontiguousarray(ff_dirs, float).reshape(-1, 3)
+        e_out = None if ff is None else np.zeros((dirs.shape[0], ff.shape[0], 3), np.complex128)
+        req = EfieRequest(len(patches), deg.ctypes.data, ncp.ctypes.data, knots.ctypes.data, cp.ctypes.data,
+                          w.ctypes.data, o, dirs.shape[0], dirs.ctypes.data, pols.ctypes.data,
+                          0 if ff is None else ff.shape[0], None if ff is None else ff.ctypes.data,
+                          w_out.ctypes.data, None if e_out is None else e_out.ctypes.data)
+        t = ctypes.c_uint64()
+        st = self._L.efie_server_submit(self.h, ctypes.byref(req), ctypes.byref(t))
+        if st < 0:
+            raise EfieError(st, "efie_server_submit", self._L)
+        self._keep[t.value] = (w_out, e_out)
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending, else (result struct, w [nrhs][ndof], e_inf or None)."""
+        r = EfieResult()
+        st = self._L.efie_server_poll(self.h, ctypes.c_uint64(ticket), ctypes.byref(r))
+        if st == EFIE_PENDING:
+            return None
+        if st < 0:
+            raise EfieError(st, "efie_server_poll", self._L)
+        w_out, e_out = self._keep.pop(ticket)
+        return r, w_out, e_out
+
+    def wait(self, ticket, poll_s=0.002):
+        import time
+
+        while True:
+            out = self.poll(ticket)
+            if out is not None:
+                return out
+            time.sleep(poll_s)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.efie_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
