@@ -325,6 +325,76 @@ def run_gpu(args):
     return 0
 
 
+# ---------------------------------------------------------------------------- serving
+SERVING = {
+    "workload": "serving_poisson50_mixed_1e-5",
+    "arrivals": "Poisson, mean 50 requests/s, seed 1809",
+    "requests": 32,
+    "geometries": "6-patch sphere (radius U[0.5,2]), 6-patch cube (side U[1,3]), 16-patch torus (R=2a, r=a/2)",
+    "p": "U{1,2,3}", "kappa": "U[1,30], geometry scaled so that the electrical size kappa*a is U[1,6]",
+    "directions": "U{1..16} seeded plane waves per request", "q": 6, "eta": 1.6, "gmres_tol": 1e-5,
+    "precision": "mixed", "dofs": "1e3 .. 3e4 per request (refinement level drawn among those in range)",
+}
+
+
+def serving_requests(n, seed=1809):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    t = 0.0
+    for i in range(n):
+        t += rng.exponential(1.0 / 50.0)
+        kind = rng.integers(0, 3)
+        p = int(rng.integers(1, 4))
+        kappa = float(rng.uniform(1.0, 30.0))
+        ka = float(rng.uniform(1.0, 6.0))
+        a = ka / kappa
+        if kind == 0:
+            geo, npch = G.sphere(radius=a), 6
+        elif kind == 1:
+            geo, npch = G.cube(side=2 * a), 6
+        else:
+            geo, npch = G.torus(R=2 * a, r=a / 2), 16
+        # refinement giving 1e3 .. 3e4 DOFs
+        cand = [m for m in range(1, 8) if 1000 <= 2 * npch * ((1 << m) + p - 1) ** 2 <= 30000]
+        m = int(cand[int(rng.integers(0, len(cand)))])
+        nd = int(rng.integers(1, 17))
+        d, pol = G.plane_waves(nd, seed=seed * 1000 + i)
+        reqs.append(dict(t=t, geo=geo, dirs=d, pols=pol,
+                         opt=dict(p=p, level_m=m, kappa=kappa, q=6, eta=1.6, precision=1, gmres_tol=1e-5,
+                                  gmres_maxit=2000)))
+    return reqs
+
+
+def run_serving(args):
+    import torch
+    from paper_1807_03097_gb300.efie import Server
+
+    torch.cuda.set_device(0)
+    reqs = serving_requests(SERVING["requests"])
+    srv = Server(hbm_budget_bytes=64 << 30, max_slots=args.slots)
+    t0 = time.perf_counter()
+    tickets = []
+    for r in reqs:
+        now = time.perf_counter() - t0
+        if r["t"] > now:
+            time.sleep(r["t"] - now)
+        tickets.append(srv.submit(r["geo"], r["dirs"], r["pols"], None, **r["opt"]))
+    res = [srv.wait(t) for t in tickets]
+    makespan = time.perf_counter() - t0
+    srv.close()
+    lat = np.array([x[0].latency_ms for x in res])
+    nsolve = sum(len(r["dirs"]) for r in reqs)
+    ok = sum(1 for x in res if x[0].status == 0)
+    line = {"metric": "serving: solves/s and p50/p99 request latency (mixed precision, GMRES 1e-5)",
+            "value": nsolve / makespan, "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
+            "requests": len(reqs), "requests_converged": ok, "plane_wave_solves": nsolve,
+            "makespan_s": makespan, "latency_ms_p50": float(np.percentile(lat, 50)),
+            "latency_ms_p99": float(np.percentile(lat, 99)), "slots": args.slots,
+            "dofs": [int(x[0].ndof) for x in res], "data": "synthetic", "config": SERVING}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -337,11 +407,15 @@ def main():
     ap.add_argument("--ref-iterations", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-steps", action="store_true", help="time the steps only (for launch-list profiling)")
+    ap.add_argument("--workload", default="solve", choices=["solve", "serving"])
+    ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--m2l-store", type=int, default=0, choices=[0, 1, 2],
                     help="M2L coupling matrices: 0 auto (kept in HBM when they fit), 1 evaluated, 2 kept")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_gpu(args)
 
 
