@@ -3,6 +3,7 @@
 // other translation units.
 #include <chrono>
 #include <cmath>
+#include <vector>
 #include <cstring>
 #include <new>
 
@@ -11,6 +12,7 @@
 using namespace efie;
 
 namespace efie {
+efie_status dev_batch_alloc(Ctx *c, int R);
 efie_status dev_scatter(Ctx *c, const double2 *ys, double2 *y);
 efie_status dev_gather(Ctx *c, const double2 *x, double2 *xs);
 efie_status dev_norms(Ctx *c, int N, const double2 *v, double *out);
@@ -41,6 +43,9 @@ void release_device(Ctx *c) {
   c->k_stored = false;
   dfree(c->d_V); dfree(c->d_H); dfree(c->d_h); dfree(c->d_h2); dfree(c->d_part); dfree(c->d_gs);
   dfree(c->d_w); dfree(c->d_r); dfree(c->d_b); dfree(c->d_sol);
+  dfree(c->d_xB); dfree(c->d_yB); dfree(c->d_xsB); dfree(c->d_ysB); dfree(c->d_ysnB);
+  dfree(c->d_momB); dfree(c->d_srcB); dfree(c->d_accB); dfree(c->d_locB);
+  c->batch_cap = 0;
   c->kr = 0;
   c->part_cap = 0;
 }
@@ -133,6 +138,9 @@ efie_status efie_destroy(efie_ctx *ctx) {
   if (c->stream2) cudaStreamSynchronize(c->stream2);
   release_device(c);
   if (c->h_res) cudaFreeHost(c->h_res);
+  if (c->h_resB) cudaFreeHost(c->h_resB);
+  c->h_resB = nullptr;
+  c->h_resB_cap = 0;
   if (c->tm.made)
     for (int i = 0; i < 8; ++i) cudaEventDestroy(c->tm.ev[i]);
   if (c->fork) cudaEventDestroy(c->fork);
@@ -347,6 +355,34 @@ efie_status efie_matvec(efie_ctx *ctx, int nrhs, const double *x, double *y, int
   if (!c->setup_done) return EFIE_ESTATE;
   cudaSetDevice(c->device);
   const size_t N = c->ndof;
+  if (nrhs > 1 && c->opt.precision == EFIE_MIXED_FP32) {
+    // all right-hand sides in one pass, in chunks of 64
+    for (int r0 = 0; r0 < nrhs; r0 += 64) {
+      const int R = std::min(64, nrhs - r0);
+      const double2 *xr = reinterpret_cast<const double2 *>(x) + r0 * N;
+      double2 *yr = reinterpret_cast<double2 *>(y) + r0 * N;
+      const double2 *xp[64];
+      double2 *yp[64];
+      if (ptr_kind == EFIE_PTR_HOST) {
+        EFIE_TRY(dev_batch_alloc(c, R));
+        for (int r = 0; r < R; ++r) {
+          xp[r] = c->d_xB + r * N;
+          yp[r] = c->d_yB + r * N;
+        }
+        EFIE_CUDA(cudaMemcpyAsync(c->d_xB, xr, 16 * N * R, cudaMemcpyHostToDevice, c->stream));
+        EFIE_TRY(dev_matvec_batch(c, R, xp, yp));
+        EFIE_CUDA(cudaMemcpyAsync(yr, c->d_yB, 16 * N * R, cudaMemcpyDeviceToHost, c->stream));
+      } else {
+        for (int r = 0; r < R; ++r) {
+          xp[r] = xr + r * N;
+          yp[r] = yr + r * N;
+        }
+        EFIE_TRY(dev_matvec_batch(c, R, xp, yp));
+      }
+    }
+    EFIE_CUDA(cudaStreamSynchronize(c->stream));
+    return EFIE_OK;
+  }
   for (int r = 0; r < nrhs; ++r) {
     const double2 *xr = reinterpret_cast<const double2 *>(x) + r * N;
     double2 *yr = reinterpret_cast<double2 *>(y) + r * N;
@@ -417,6 +453,68 @@ efie_status efie_rhs_plane_waves(efie_ctx *ctx, int nrhs, const double *dir, con
   return EFIE_OK;
 }
 
+// Several right-hand sides in the mixed form: lockstep GMRES over chunks of systems whose
+// Krylov bases fit in the free device memory, so every step applies one batched matvec.
+static efie_status solve_batched(Ctx *c, int nrhs, const double *b, double *x, int ptr_kind, const double *dir,
+                                 const double *pol, int *its_max, int *all_conv, double *worst) {
+  const size_t N = c->ndof;
+  size_t fr = 0, tot = 0;
+  EFIE_CUDA(cudaMemGetInfo(&fr, &tot));
+  const size_t per = gmres_batch_bytes_per_system(c) + 32 * N + size_t(40) * c->nsup +
+                     size_t(80) * c->ncl * c->nI;
+  int chunk = (int)std::min<size_t>(64, (size_t)(0.8 * (double)fr) / std::max<size_t>(per, 1));
+  if (chunk < 1) {
+    c->err = "solve: the Krylov basis of one system does not fit in the free device memory";
+    return EFIE_ENOMEM;
+  }
+  chunk = std::min(chunk, nrhs);
+  EFIE_TRY(dev_batch_alloc(c, chunk));
+  double2 *d_bb = nullptr, *d_xx = nullptr;
+  struct Guard {
+    double2 **a, **b;
+    ~Guard() {
+      if (*a) cudaFree(*a);
+      if (*b) cudaFree(*b);
+    }
+  } guard{&d_bb, &d_xx};
+  EFIE_TRY(dalloc(c, &d_bb, (size_t)chunk * N));
+  if (ptr_kind == EFIE_PTR_HOST) EFIE_TRY(dalloc(c, &d_xx, (size_t)chunk * N));
+  std::vector<const double2 *> bp(chunk);
+  std::vector<double2 *> xp(chunk);
+  std::vector<int> its(chunk), conv(chunk);
+  std::vector<double> res(chunk);
+  for (int r0 = 0; r0 < nrhs; r0 += chunk) {
+    const int R = std::min(chunk, nrhs - r0);
+    for (int r = 0; r < R; ++r) {
+      const int g = r0 + r;
+      double2 *bd = d_bb + (size_t)r * N;
+      if (dir) {
+        EFIE_TRY(dev_rhs(c, dir + 3 * g, pol + 3 * g, bd));
+        bp[r] = bd;
+      } else if (ptr_kind == EFIE_PTR_HOST) {
+        EFIE_CUDA(cudaMemcpyAsync(bd, reinterpret_cast<const double2 *>(b) + g * N, 16 * N, cudaMemcpyHostToDevice,
+                                  c->stream));
+        bp[r] = bd;
+      } else {
+        bp[r] = reinterpret_cast<const double2 *>(b) + g * N;
+      }
+      xp[r] = ptr_kind == EFIE_PTR_HOST ? d_xx + (size_t)r * N : reinterpret_cast<double2 *>(x) + g * N;
+    }
+    EFIE_TRY(dev_gmres_batch(c, R, bp.data(), xp.data(), its.data(), res.data(), conv.data()));
+    if (ptr_kind == EFIE_PTR_HOST) {
+      EFIE_CUDA(cudaMemcpyAsync(reinterpret_cast<double2 *>(x) + r0 * N, d_xx, 16 * N * R, cudaMemcpyDeviceToHost,
+                                c->stream));
+      EFIE_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    for (int r = 0; r < R; ++r) {
+      *its_max = std::max(*its_max, its[r]);
+      *worst = std::max(*worst, res[r]);
+      if (!conv[r]) *all_conv = 0;
+    }
+  }
+  return EFIE_OK;
+}
+
 static efie_status solve_impl(Ctx *c, int nrhs, const double *b, double *x, int ptr_kind, efie_solve_info *info,
                               const double *dir, const double *pol) {
   const size_t N = c->ndof;
@@ -425,6 +523,11 @@ static efie_status solve_impl(Ctx *c, int nrhs, const double *b, double *x, int 
   int its_max = 0, all_conv = 1;
   double worst = 0.0;
   auto t0 = std::chrono::steady_clock::now();
+  if (nrhs > 1 && c->opt.precision == EFIE_MIXED_FP32) {
+    EFIE_TRY(solve_batched(c, nrhs, b, x, ptr_kind, dir, pol, &its_max, &all_conv, &worst));
+    if (!all_conv) result = EFIE_NOT_CONVERGED;
+    nrhs = 0;
+  }
   for (int r = 0; r < nrhs; ++r) {
     double2 *xr = reinterpret_cast<double2 *>(x) + r * N;
     const double2 *br = b ? reinterpret_cast<const double2 *>(b) + r * N : nullptr;

@@ -99,7 +99,13 @@ struct Ctx {
   int m2l_mode = 2;  // FP32 M2L phase: 0 direct kappa r - kappa r0, 1 split, 2 split + explicit reduction
   int *d_far_tgt = nullptr;   // target cluster of every far pair (CSR order)
   void *d_K = nullptr;        // stored coupling matrices [pair][m'][m] (double2 or float2)
-  bool k_stored = false;  // FP32 M2L reduces phases explicitly (unless all are within +-100 pi)
+  bool k_stored = false;
+  // several right-hand sides (mixed form)
+  int batch_cap = 0;
+  double *h_resB = nullptr;  // pinned residual estimates of a lockstep batch
+  int h_resB_cap = 0;
+  double2 *d_xB = nullptr, *d_yB = nullptr, *d_xsB = nullptr, *d_ysB = nullptr, *d_ysnB = nullptr;
+  float2 *d_momB = nullptr, *d_srcB = nullptr, *d_accB = nullptr, *d_locB = nullptr;  // FP32 M2L reduces phases explicitly (unless all are within +-100 pi)
   int *d_near_ptr = nullptr, *d_near_src = nullptr;  // CSR by target element
   double2 *d_nblk = nullptr;  // [nnear][nb (col)][nb (row)]
   float2 *d_nblkf = nullptr;  // FP32 copy of the blocks (mixed-precision apply)
@@ -166,6 +172,12 @@ efie_status dev_far_field(Ctx *c, const double2 *w, int ndir, const double *dirs
 efie_status dev_gmres(Ctx *c, const double2 *b, double2 *x, int *its, double *res, int *conv);
 efie_status dev_alloc_work(Ctx *c);
 efie_status dev_near_blocks_f32(Ctx *c);
+// Y[r] = A X[r] for r < R (host arrays of device pointers); one pass in the mixed form
+efie_status dev_matvec_batch(Ctx *c, int R, const double2 *const *X, double2 *const *Y);
+// R independent GMRES solves advanced in lockstep, one batched matvec per step
+size_t gmres_batch_bytes_per_system(const Ctx *c);
+efie_status dev_gmres_batch(Ctx *c, int R, const double2 *const *b, double2 *const *x, int *its, double *res,
+                            int *conv);
 
 #define EFIE_CUDA(call)                                                              \
   do {                                                                               \

@@ -1046,3 +1046,255 @@ efie_status dev_alloc_work(Ctx *c) {
 }
 
 }  // namespace efie
+
+// ========================================================================================
+// Several right-hand sides at once (mixed form).  The cheap stages run once per right-hand
+// side; the M2L evaluates the coupling tile G(m, m') of every admissible block once into
+// shared memory and applies it to the 4 fields of up to kRB right-hand sides.
+namespace efie {
+
+constexpr int kRB = 8;             // right-hand sides per M2L block
+constexpr int kFB = 4 * kRB;       // fields per M2L block
+constexpr int kMultiThreads = 256;
+constexpr int kMultiMaxNI = 144;   // (q + 1)^2 limit of the shared-memory tile
+
+// node-major folded sources of all right-hand sides: src[(id nI + m) ld + 4 r + {x, y, z, div}].
+// The row stride ld = 4 x (allocated right-hand sides) does not change with R, so rows of
+// clusters that receive no M2L stay zero whatever the number of right-hand sides of earlier
+// products.
+__global__ void k_fold_multi(long long tot, int nI, int R, int ld, size_t mstride, const double *__restrict__ nodeD,
+                             const float2 *__restrict__ mom, float2 *__restrict__ src) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= tot) return;
+  const int id = (int)(t / nI), mi = (int)(t % nI);
+  const double *D = nodeD + 6 * t;
+  for (int r = 0; r < R; ++r) {
+    const float2 *mm = mom + r * mstride + (size_t)id * 3 * nI;
+    float2 m0 = mm[mi], m1 = mm[nI + mi], nu = mm[2 * nI + mi];
+    float2 *o = src + (size_t)t * ld + 4 * r;
+    for (int k = 0; k < 3; ++k) {
+      float d1 = (float)D[k], d2 = (float)D[3 + k];
+      o[k] = make_float2(d1 * m0.x + d2 * m1.x, d1 * m0.y + d2 * m1.y);
+    }
+    o[3] = nu;
+  }
+}
+
+__global__ void k_unfold_multi(long long tot, int nI, int R, int ld, size_t lstride, float ik2,
+                               const double *__restrict__ nodeD,
+                               const float2 *__restrict__ acc, float2 *__restrict__ loc) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= tot) return;
+  const int id = (int)(t / nI), mi = (int)(t % nI);
+  const double *D = nodeD + 6 * t;
+  for (int r = 0; r < R; ++r) {
+    const float2 *a = acc + (size_t)t * ld + 4 * r;
+    float l0x = 0, l0y = 0, l1x = 0, l1y = 0;
+    for (int k = 0; k < 3; ++k) {
+      l0x += (float)D[k] * a[k].x;
+      l0y += (float)D[k] * a[k].y;
+      l1x += (float)D[3 + k] * a[k].x;
+      l1y += (float)D[3 + k] * a[k].y;
+    }
+    float2 *l = loc + r * lstride + (size_t)id * 3 * nI;
+    l[mi] = make_float2(l0x, l0y);
+    l[nI + mi] = make_float2(l1x, l1y);
+    l[2 * nI + mi] = make_float2(-ik2 * a[3].x, -ik2 * a[3].y);
+  }
+}
+
+// One block per (target cluster, group of kRB right-hand sides).  Thread t owns field
+// f = t % kFB of the group and the target nodes m = t / kFB + 8 k.  For every source cluster:
+// stage its node offsets and the group's fields, evaluate the (q+1)^4 tile of
+// e^{i kappa r0}/(4 pi) e^{i kappa (r - r0)}/r (same phase forms as the single-field kernel)
+// into shared memory, multiply-accumulate, and add the pair's FP32 partial sums to the
+// running sums with two-sum compensation.
+template <int KM>
+__global__ void __launch_bounds__(kMultiThreads) k_m2l_f32_multi(
+    const int *__restrict__ targets, const int *__restrict__ fptr, const int *__restrict__ fsrc,
+    const float4 *__restrict__ pgeo, const float2 *__restrict__ pph, int nI, float kappa, int mode,
+    const float4 *__restrict__ nodeX4, int F, int ld, const float2 *__restrict__ src, float2 *__restrict__ acc) {
+  extern __shared__ float4 smm[];
+  float4 *sXt = smm;                              // [nI]
+  float4 *sXs = sXt + nI;                         // [nI]
+  float2 *sS = (float2 *)(sXs + nI);              // [nI][kFB]
+  float2 *sG = sS + (size_t)nI * kFB;             // [nI][nI] (row: target node)
+  const int t = targets[blockIdx.x];
+  const int f0 = blockIdx.y * kFB;
+  const int tid = threadIdx.x, f = tid % kFB, mg = tid / kFB;
+  const bool fval = f0 + f < F;
+  for (int i = tid; i < nI; i += blockDim.x) sXt[i] = nodeX4[(size_t)t * nI + i];
+  float ah[KM][2], al[KM][2];
+#pragma unroll
+  for (int k = 0; k < KM; ++k) ah[k][0] = ah[k][1] = al[k][0] = al[k][1] = 0.f;
+  const float inv2pi = 0.15915494309189535f, c1 = 6.28318548202514648f, c2 = -1.7484555e-7f;
+  for (int kk = fptr[t]; kk < fptr[t + 1]; ++kk) {
+    const int s = fsrc[kk];
+    const float4 g = pgeo[kk];
+    const float2 ph = pph[kk];
+    __syncthreads();
+    for (int i = tid; i < nI; i += blockDim.x) sXs[i] = nodeX4[(size_t)s * nI + i];
+    for (int i = tid; i < nI * kFB; i += blockDim.x) {
+      const int mj = i / kFB, ff = i % kFB;
+      sS[i] = (f0 + ff < F) ? src[((size_t)s * nI + mj) * ld + f0 + ff] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const float r0 = g.w, r0sq = g.w * g.w, kr0 = kappa * g.w;
+    for (int e = tid; e < nI * nI; e += blockDim.x) {
+      const int mi = e / nI, mj = e % nI;
+      const float4 xt = sXt[mi], xs = sXs[mj];
+      float ex = xt.x - xs.x, ey = xt.y - xs.y, ez = xt.z - xs.z, rinv, phs;
+      if (mode == 0) {
+        float vx = g.x + ex, vy = g.y + ey, vz = g.z + ez;
+        float r2 = vx * vx + vy * vy + vz * vz;
+        rinv = rsqrtf(r2);
+        phs = fmaf(kappa, r2 * rinv, -kr0);
+      } else {
+        float num = fmaf(2.f, g.x * ex + g.y * ey + g.z * ez, ex * ex + ey * ey + ez * ez);
+        float r2 = r0sq + num;
+        rinv = rsqrtf(r2);
+        phs = kappa * __fdividef(num, r2 * rinv + r0);
+        if (mode == 2) {
+          float q = rintf(phs * inv2pi);
+          phs = fmaf(-q, c1, phs);
+          phs = fmaf(-q, c2, phs);
+        }
+      }
+      float sn, cs;
+      __sincosf(phs, &sn, &cs);
+      const float gr = cs * rinv, gi = sn * rinv;
+      sG[e] = make_float2(ph.x * gr - ph.y * gi, ph.x * gi + ph.y * gr);
+    }
+    __syncthreads();
+    float pr[KM], pim[KM];
+#pragma unroll
+    for (int k = 0; k < KM; ++k) pr[k] = pim[k] = 0.f;
+    for (int mj = 0; mj < nI; ++mj) {
+      const float2 sv = sS[mj * kFB + f];
+#pragma unroll
+      for (int k = 0; k < KM; ++k) {
+        const int mi = mg + 8 * k;
+        if (mi < nI) {
+          const float2 gv = sG[mi * nI + mj];
+          pr[k] = fmaf(gv.x, sv.x, fmaf(-gv.y, sv.y, pr[k]));
+          pim[k] = fmaf(gv.x, sv.y, fmaf(gv.y, sv.x, pim[k]));
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+      two_sum_acc(ah[k][0], al[k][0], pr[k]);
+      two_sum_acc(ah[k][1], al[k][1], pim[k]);
+    }
+  }
+  if (fval) {
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+      const int mi = mg + 8 * k;
+      if (mi < nI) acc[((size_t)t * nI + mi) * ld + f0 + f] = make_float2(ah[k][0] + al[k][0], ah[k][1] + al[k][1]);
+    }
+  }
+}
+
+static size_t multi_smem(int nI) {
+  return sizeof(float4) * 2 * nI + sizeof(float2) * ((size_t)nI * kFB + (size_t)nI * nI);
+}
+
+efie_status dev_batch_alloc(Ctx *c, int R) {
+  if (R <= c->batch_cap) return EFIE_OK;
+  const size_t ncl = c->ncl, nI = c->nI;
+  EFIE_TRY(dalloc(c, &c->d_xB, (size_t)R * c->ndof));
+  EFIE_TRY(dalloc(c, &c->d_yB, (size_t)R * c->ndof));
+  EFIE_TRY(dalloc(c, &c->d_xsB, (size_t)R * c->nsup));
+  EFIE_TRY(dalloc(c, &c->d_ysB, (size_t)R * c->nsup));
+  EFIE_TRY(dalloc(c, &c->d_ysnB, (size_t)R * c->nsup));
+  EFIE_TRY(dalloc(c, &c->d_momB, (size_t)R * ncl * 3 * nI));
+  EFIE_TRY(dalloc(c, &c->d_srcB, (size_t)R * ncl * 4 * nI));
+  EFIE_TRY(dalloc(c, &c->d_accB, (size_t)R * ncl * 4 * nI));
+  EFIE_CUDA(cudaMemset(c->d_accB, 0, sizeof(float2) * (size_t)R * ncl * 4 * nI));
+  EFIE_TRY(dalloc(c, &c->d_locB, (size_t)R * ncl * 3 * nI));
+  const int sm = (int)multi_smem(kMultiMaxNI);
+  for (auto fn : {k_m2l_f32_multi<1>, k_m2l_f32_multi<2>, k_m2l_f32_multi<4>, k_m2l_f32_multi<8>,
+                  k_m2l_f32_multi<12>, k_m2l_f32_multi<16>, k_m2l_f32_multi<18>})
+    EFIE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  c->batch_cap = R;
+  return EFIE_OK;
+}
+
+// Y[r] = A X[r], r < R (host arrays of device pointers).
+efie_status dev_matvec_batch(Ctx *c, int R, const double2 *const *X, double2 *const *Y) {
+  if (c->opt.precision != EFIE_MIXED_FP32 || c->nI > kMultiMaxNI || R == 1) {
+    for (int r = 0; r < R; ++r) EFIE_TRY(dev_matvec(c, X[r], Y[r]));
+    return EFIE_OK;
+  }
+  EFIE_TRY(dev_batch_alloc(c, R));
+  cudaStream_t st = c->stream;
+  const int nI = c->nI, q1 = c->q1, p1 = c->p1, m = c->m;
+  const float h = (float)(1.0 / c->n);
+  const size_t mstride = (size_t)c->ncl * 3 * nI;
+  for (int r = 0; r < R; ++r) {
+    double2 *xs = c->d_xsB + (size_t)r * c->nsup;
+    k_gather<<<(c->nsup + 255) / 256, 256, 0, st>>>(c->nsup, c->d_tg_ptr, c->d_tg_col, c->d_tg_val,
+                                                    X[r], xs); ++c->launches;
+  }
+  EFIE_CUDA(cudaEventRecord(c->fork, st));
+  EFIE_CUDA(cudaStreamWaitEvent(c->stream2, c->fork, 0));
+  for (int r = 0; r < R; ++r)
+    EFIE_TRY(dev_near_apply(c, c->d_xsB + (size_t)r * c->nsup, c->d_ysnB + (size_t)r * c->nsup, c->stream2));
+  EFIE_CUDA(cudaEventRecord(c->join, c->stream2));
+  for (int r = 0; r < R; ++r) {
+    float2 *mom = c->d_momB + r * mstride;
+    k_leaf_moments<float><<<c->nE, 128, 0, st>>>(c->nE, c->lev_off[m], p1, q1, h, c->d_M, c->d_Md,
+                                                 c->d_xsB + (size_t)r * c->nsup, mom); ++c->launches;
+    for (int l = m - 1; l >= 0; --l) {
+      int npar = c->np << (2 * l);
+      k_m2m<float><<<npar, 128, m2m_smem(q1, sizeof(float2)), st>>>(npar, c->lev_off[l], c->lev_off[l + 1], q1, c->d_E,
+                                                                    mom); ++c->launches;
+    }
+  }
+  const long long tot = (long long)c->ncl * nI;
+  const unsigned gtot = (unsigned)((tot + 255) / 256);
+  const int ld = 4 * c->batch_cap;
+  k_fold_multi<<<gtot, 256, 0, st>>>(tot, nI, R, ld, mstride, c->d_nodeD, c->d_momB, c->d_srcB); ++c->launches;
+  if (c->n_m2l_targets > 0) {
+    const int F = 4 * R, KM = (nI + 7) / 8;
+    dim3 grid(c->n_m2l_targets, (F + kFB - 1) / kFB);
+    const size_t sm = multi_smem(nI);
+    const float kf = (float)c->kappa;
+#define EFIE_MULTI(K)                                                                                        \
+  k_m2l_f32_multi<K><<<grid, kMultiThreads, sm, st>>>(c->d_m2l_targets, c->d_far_ptr, c->d_far_src, c->d_pgeo, \
+                                                     c->d_pph, nI, kf, c->m2l_mode, c->d_nodeX4, F, ld, c->d_srcB, \
+                                                     c->d_accB);
+    if (KM <= 1) { EFIE_MULTI(1) }
+    else if (KM <= 2) { EFIE_MULTI(2) }
+    else if (KM <= 4) { EFIE_MULTI(4) }
+    else if (KM <= 8) { EFIE_MULTI(8) }
+    else if (KM <= 12) { EFIE_MULTI(12) }
+    else if (KM <= 16) { EFIE_MULTI(16) }
+    else { EFIE_MULTI(18) }
+#undef EFIE_MULTI
+    ++c->launches;
+  }
+  k_unfold_multi<<<gtot, 256, 0, st>>>(tot, nI, R, ld, mstride, (float)(1.0 / (c->kappa * c->kappa)), c->d_nodeD,
+                                       c->d_accB, c->d_locB); ++c->launches;
+  for (int r = 0; r < R; ++r) {
+    float2 *loc = c->d_locB + r * mstride;
+    for (int l = 0; l < m; ++l) {
+      int npar = c->np << (2 * l);
+      k_l2l<float><<<npar, 128, l2l_smem(q1, sizeof(float2)), st>>>(npar, c->lev_off[l], c->lev_off[l + 1], q1, c->d_E,
+                                                                    loc); ++c->launches;
+    }
+    k_leaf_eval<float><<<c->nE, 128, 0, st>>>(c->nE, c->lev_off[m], p1, q1, h, c->d_M, c->d_Md, loc,
+                                              c->d_ysB + (size_t)r * c->nsup); ++c->launches;
+  }
+  EFIE_CUDA(cudaStreamWaitEvent(st, c->join, 0));
+  for (int r = 0; r < R; ++r) {
+    k_scatter<<<(c->ndof + 255) / 256, 256, 0, st>>>(c->ndof, c->d_ts_ptr, c->d_ts_col, c->d_ts_val,
+                                                     c->d_ysB + (size_t)r * c->nsup, c->d_ysnB + (size_t)r * c->nsup,
+                                                     Y[r]); ++c->launches;
+  }
+  EFIE_CUDA(cudaGetLastError());
+  return EFIE_OK;
+}
+
+}  // namespace efie

@@ -3,7 +3,10 @@
 // Gram-Schmidt applied twice (CGS2) with deterministic two-stage reductions (fixed order,
 // independent of launch timing), Givens rotations and back substitution on the device.
 // Only the residual estimate (8 bytes) crosses to the host per iteration.
+#include <algorithm>
 #include <cmath>
+#include <string>
+#include <vector>
 
 #include "efie_internal.h"
 
@@ -312,6 +315,206 @@ efie_status dev_norms(Ctx *c, int N, const double2 *v, double *out) {
   EFIE_CUDA(cudaMemcpyAsync(c->h_res, c->d_h, sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
   EFIE_CUDA(cudaStreamSynchronize(c->stream));
   *out = std::sqrt(std::max(c->h_res[0], 0.0));
+  return EFIE_OK;
+}
+
+}  // namespace efie
+
+// ========================================================================================
+// R independent systems advanced in lockstep: every step collects the one matvec each
+// unfinished system needs (A v_j during Arnoldi, A x for a restart or the final residual
+// check), applies them in one batched pass, then runs each system's Gram-Schmidt, Givens and
+// back-substitution exactly as the single-system solver does.  One host synchronisation per
+// step reads all residual estimates.
+namespace efie {
+
+namespace {
+enum Phase { kStart, kArnoldi, kConfirm, kDone };
+
+struct GSys {
+  const double2 *b = nullptr;
+  double2 *x = nullptr;
+  double2 *V = nullptr, *H = nullptr, *h = nullptr, *h2 = nullptr, *w = nullptr, *r = nullptr, *sol = nullptr;
+  double *gs = nullptr;
+  double bn = 0, target = 0, res = 0;
+  int its = 0, conv = 0, j = 0, phase = kStart;
+  bool r_ready = false;  // r holds b (first cycle) or b - A x (after a failed check)
+};
+
+struct DevBlock {
+  std::vector<void *> p;
+  ~DevBlock() {
+    for (void *q : p) cudaFree(q);
+  }
+  template <class T>
+  efie_status get(Ctx *c, T **out, size_t n) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+    if (e != cudaSuccess) {
+      c->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+      return EFIE_ENOMEM;
+    }
+    p.push_back(q);
+    *out = static_cast<T *>(q);
+    return EFIE_OK;
+  }
+};
+}  // namespace
+
+size_t gmres_batch_bytes_per_system(const Ctx *c) {
+  const size_t N = c->ndof, kr = std::max(1, std::min(c->opt.gmres_restart, c->opt.gmres_maxit));
+  return 16 * ((kr + 1) * N + (kr + 1) * kr + 3 * (kr + 1) + 2 * N) + 8 * (5 * kr + 4);
+}
+
+efie_status dev_gmres_batch(Ctx *c, int R, const double2 *const *b, double2 *const *x, int *its_out,
+                            double *res_out, int *conv_out) {
+  const int N = c->ndof;
+  const int kr = std::max(1, std::min(c->opt.gmres_restart, c->opt.gmres_maxit));
+  const int maxit = c->opt.gmres_maxit;
+  cudaStream_t st = c->stream;
+  const int blk = 256, grid = (N + blk - 1) / blk;
+  DevBlock mem;
+  std::vector<GSys> S(R);
+  for (int i = 0; i < R; ++i) {
+    GSys &s = S[i];
+    s.b = b[i];
+    s.x = x[i];
+    EFIE_TRY(mem.get(c, &s.V, (size_t)(kr + 1) * N));
+    EFIE_TRY(mem.get(c, &s.H, (size_t)(kr + 1) * kr));
+    EFIE_TRY(mem.get(c, &s.h, (size_t)kr + 1));
+    EFIE_TRY(mem.get(c, &s.h2, (size_t)kr + 1));
+    EFIE_TRY(mem.get(c, &s.sol, (size_t)kr + 1));
+    EFIE_TRY(mem.get(c, &s.w, (size_t)N));
+    EFIE_TRY(mem.get(c, &s.r, (size_t)N));
+    EFIE_TRY(mem.get(c, &s.gs, (size_t)2 + 5 * kr + 2));
+  }
+  if (c->h_resB_cap < 4 * R) {
+    if (c->h_resB) cudaFreeHost(c->h_resB);
+    c->h_resB = nullptr;
+    c->h_resB_cap = 0;
+    EFIE_CUDA(cudaMallocHost((void **)&c->h_resB, 4 * R * sizeof(double)));
+    c->h_resB_cap = 4 * R;
+  }
+  double *hr = c->h_resB;
+  // ||b|| of every system
+  for (int i = 0; i < R; ++i) {
+    EFIE_TRY(dots(c, N, 1, S[i].b, N, S[i].b, S[i].h));
+    EFIE_CUDA(cudaMemcpyAsync(hr + 4 * i, S[i].h, sizeof(double2), cudaMemcpyDeviceToHost, st));
+    EFIE_CUDA(cudaMemsetAsync(S[i].x, 0, sizeof(double2) * N, st));
+  }
+  EFIE_CUDA(cudaStreamSynchronize(st));
+  for (int i = 0; i < R; ++i) {
+    GSys &s = S[i];
+    s.bn = std::sqrt(std::max(hr[4 * i], 0.0));
+    s.target = c->opt.tol_is_relative ? c->opt.gmres_tol * s.bn : c->opt.gmres_tol;
+    s.res = s.bn;
+    if (s.bn == 0.0) {
+      s.conv = 1;
+      s.phase = kDone;
+    } else {
+      EFIE_CUDA(cudaMemcpyAsync(s.r, s.b, sizeof(double2) * N, cudaMemcpyDeviceToDevice, st));
+      s.r_ready = true;
+    }
+  }
+  std::vector<const double2 *> in;
+  std::vector<double2 *> out;
+  std::vector<int> who;
+  for (;;) {
+    in.clear();
+    out.clear();
+    who.clear();
+    for (int i = 0; i < R; ++i) {
+      GSys &s = S[i];
+      if (s.phase == kArnoldi) {
+        in.push_back(s.V + (size_t)s.j * N);
+        out.push_back(s.w);
+        who.push_back(i);
+      } else if ((s.phase == kStart && !s.r_ready) || s.phase == kConfirm) {
+        in.push_back(s.x);
+        out.push_back(s.r);
+        who.push_back(i);
+      }
+    }
+    bool any = false;
+    for (const GSys &s : S) any |= s.phase != kDone;
+    if (!any) break;
+    if (!in.empty()) EFIE_TRY(dev_matvec_batch(c, (int)in.size(), in.data(), out.data()));
+    for (int i : who)
+      if (S[i].phase != kArnoldi) {
+        k_residual<<<grid, blk, 0, st>>>(N, S[i].b, S[i].r); ++c->launches;
+      }
+    for (int i = 0; i < R; ++i) {
+      GSys &s = S[i];
+      if (s.phase == kStart) {
+        EFIE_TRY(dots(c, N, 1, s.r, N, s.r, s.h));
+        k_givens_init<<<1, 1, 0, st>>>(s.gs, kr, s.h); ++c->launches;
+        k_scale_copy<<<grid, blk, 0, st>>>(N, s.r, s.gs, 0, s.V); ++c->launches;
+        EFIE_CUDA(cudaMemcpyAsync(hr + 4 * i, s.gs, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      } else if (s.phase == kArnoldi) {
+        const int j = s.j;
+        EFIE_TRY(dots(c, N, j + 1, s.V, N, s.w, s.h));
+        k_combine<<<grid, blk, sizeof(double2) * (j + 1), st>>>(N, j + 1, s.V, N, s.h, -1.0, s.w); ++c->launches;
+        EFIE_TRY(dots(c, N, j + 1, s.V, N, s.w, s.h2));
+        k_combine<<<grid, blk, sizeof(double2) * (j + 1), st>>>(N, j + 1, s.V, N, s.h2, -1.0, s.w); ++c->launches;
+        EFIE_TRY(dots(c, N, 1, s.w, N, s.w, s.h2 + kr));
+        k_givens_step<<<1, 1, 0, st>>>(j, kr, s.h, s.h2, s.h2 + kr, s.H, s.gs); ++c->launches;
+        k_scale_copy<<<grid, blk, 0, st>>>(N, s.w, s.gs, 0, s.V + (size_t)(j + 1) * N); ++c->launches;
+        EFIE_CUDA(cudaMemcpyAsync(hr + 4 * i, s.gs, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      } else if (s.phase == kConfirm) {
+        EFIE_TRY(dots(c, N, 1, s.r, N, s.r, s.h));
+        EFIE_CUDA(cudaMemcpyAsync(hr + 4 * i, s.h, sizeof(double2), cudaMemcpyDeviceToHost, st));
+      }
+    }
+    EFIE_CUDA(cudaGetLastError());
+    EFIE_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < R; ++i) {
+      GSys &s = S[i];
+      if (s.phase == kStart) {
+        s.r_ready = false;
+        s.res = hr[4 * i + 1];
+        if (s.res <= s.target) {
+          s.conv = 1;
+          s.phase = kDone;
+        } else if (s.its >= maxit) {
+          s.phase = kDone;
+        } else {
+          s.phase = kArnoldi;
+          s.j = 0;
+        }
+      } else if (s.phase == kArnoldi) {
+        ++s.its;
+        s.res = hr[4 * i + 1];
+        const int jd = s.j + 1;
+        const bool nan = !(s.res == s.res);
+        if (s.res <= s.target || nan || jd == kr || s.its >= maxit) {
+          k_backsolve<<<1, 32, 0, st>>>(jd, kr, s.H, s.gs, s.sol); ++c->launches;
+          k_combine<<<grid, blk, sizeof(double2) * jd, st>>>(N, jd, s.V, N, s.sol, 1.0, s.x); ++c->launches;
+          if (s.res <= s.target) s.phase = kConfirm;
+          else if (nan || s.its >= maxit) s.phase = kDone;
+          else s.phase = kStart;
+        } else {
+          s.j = jd;
+        }
+      } else if (s.phase == kConfirm) {
+        s.res = std::sqrt(std::max(hr[4 * i], 0.0));
+        if (s.res <= s.target * 1.05) {
+          s.conv = 1;
+          s.phase = kDone;
+        } else if (!(s.res == s.res) || s.its >= maxit) {
+          s.phase = kDone;
+        } else {
+          s.phase = kStart;
+          s.r_ready = true;
+        }
+      }
+    }
+  }
+  EFIE_CUDA(cudaStreamSynchronize(st));
+  for (int i = 0; i < R; ++i) {
+    its_out[i] = S[i].its;
+    res_out[i] = c->opt.tol_is_relative ? (S[i].bn > 0 ? S[i].res / S[i].bn : 0.0) : S[i].res;
+    conv_out[i] = S[i].conv;
+  }
   return EFIE_OK;
 }
 
