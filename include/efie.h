@@ -82,6 +82,10 @@ typedef struct {
                         when they take at most half of the free memory; FP32 form: evaluated
                         in every product, which is faster than streaming them); 1 always
                         evaluate; 2 always keep (EFIE_ENOMEM if they do not fit) */
+  int m2l_batch;     /* M2L of a product with several right-hand sides in the mixed form:
+                        0 automatic (tensor cores when q <= 10, else FP32 on the CUDA cores),
+                        1 FP32 on the CUDA cores, 2 tensor cores (split TF32 with FP32
+                        accumulation, q <= 10; EFIE_EINVAL at setup otherwise) */
 } efie_options;
 
 typedef struct {

@@ -44,7 +44,7 @@ void release_device(Ctx *c) {
   dfree(c->d_V); dfree(c->d_H); dfree(c->d_h); dfree(c->d_h2); dfree(c->d_part); dfree(c->d_gs);
   dfree(c->d_w); dfree(c->d_r); dfree(c->d_b); dfree(c->d_sol);
   dfree(c->d_xB); dfree(c->d_yB); dfree(c->d_xsB); dfree(c->d_ysB); dfree(c->d_ysnB);
-  dfree(c->d_momB); dfree(c->d_srcB); dfree(c->d_accB); dfree(c->d_locB);
+  dfree(c->d_momB); dfree(c->d_srcB); dfree(c->d_accB); dfree(c->d_locB); dfree(c->d_tc_err);
   c->batch_cap = 0;
   c->kr = 0;
   c->part_cap = 0;
@@ -61,6 +61,8 @@ efie_status check_options(const efie_options *o) {
   if (o->quad_regular < 0 || o->quad_regular > 16 || o->quad_singular < 0 || o->quad_singular > 16) return EFIE_EINVAL;
   if (o->gmres_restart < 1 || o->gmres_maxit < 1 || !(o->gmres_tol > 0.0)) return EFIE_EINVAL;
   if (o->m2l_store < 0 || o->m2l_store > 2) return EFIE_EINVAL;
+  if (o->m2l_batch < 0 || o->m2l_batch > 2) return EFIE_EINVAL;
+  if (o->m2l_batch == 2 && (o->q + 1) * (o->q + 1) > 128) return EFIE_EINVAL;
   return EFIE_OK;
 }
 
@@ -381,7 +383,7 @@ efie_status efie_matvec(efie_ctx *ctx, int nrhs, const double *x, double *y, int
       }
     }
     EFIE_CUDA(cudaStreamSynchronize(c->stream));
-    return EFIE_OK;
+    return m2l_tc_check(c);
   }
   for (int r = 0; r < nrhs; ++r) {
     const double2 *xr = reinterpret_cast<const double2 *>(x) + r * N;

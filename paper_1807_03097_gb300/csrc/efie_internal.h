@@ -105,7 +105,8 @@ struct Ctx {
   double *h_resB = nullptr;  // pinned residual estimates of a lockstep batch
   int h_resB_cap = 0;
   double2 *d_xB = nullptr, *d_yB = nullptr, *d_xsB = nullptr, *d_ysB = nullptr, *d_ysnB = nullptr;
-  float2 *d_momB = nullptr, *d_srcB = nullptr, *d_accB = nullptr, *d_locB = nullptr;  // FP32 M2L reduces phases explicitly (unless all are within +-100 pi)
+  float2 *d_momB = nullptr, *d_srcB = nullptr, *d_accB = nullptr, *d_locB = nullptr;
+  int *d_tc_err = nullptr;   // set by a tensor-core M2L whose pipeline wait ran out  // FP32 M2L reduces phases explicitly (unless all are within +-100 pi)
   int *d_near_ptr = nullptr, *d_near_src = nullptr;  // CSR by target element
   double2 *d_nblk = nullptr;  // [nnear][nb (col)][nb (row)]
   float2 *d_nblkf = nullptr;  // FP32 copy of the blocks (mixed-precision apply)
@@ -176,6 +177,11 @@ efie_status dev_near_blocks_f32(Ctx *c);
 efie_status dev_matvec_batch(Ctx *c, int R, const double2 *const *X, double2 *const *Y);
 // R independent GMRES solves advanced in lockstep, one batched matvec per step
 size_t gmres_batch_bytes_per_system(const Ctx *c);
+// tensor-core M2L of a batch (m2l_tc.cu)
+bool m2l_tc_supported(const Ctx *c);
+efie_status m2l_tc_prepare(Ctx *c);
+efie_status launch_m2l_tc(Ctx *c, cudaStream_t st, int F, int ld, const float2 *src, float2 *acc);
+efie_status m2l_tc_check(Ctx *c);
 efie_status dev_gmres_batch(Ctx *c, int R, const double2 *const *b, double2 *const *x, int *its, double *res,
                             int *conv);
 

@@ -1213,6 +1213,7 @@ efie_status dev_batch_alloc(Ctx *c, int R) {
   EFIE_TRY(dalloc(c, &c->d_accB, (size_t)R * ncl * 4 * nI));
   EFIE_CUDA(cudaMemset(c->d_accB, 0, sizeof(float2) * (size_t)R * ncl * 4 * nI));
   EFIE_TRY(dalloc(c, &c->d_locB, (size_t)R * ncl * 3 * nI));
+  if (c->opt.precision == EFIE_MIXED_FP32 && m2l_tc_supported(c)) EFIE_TRY(m2l_tc_prepare(c));
   const int sm = (int)multi_smem(kMultiMaxNI);
   for (auto fn : {k_m2l_f32_multi<1>, k_m2l_f32_multi<2>, k_m2l_f32_multi<4>, k_m2l_f32_multi<8>,
                   k_m2l_f32_multi<12>, k_m2l_f32_multi<16>, k_m2l_f32_multi<18>})
@@ -1223,7 +1224,7 @@ efie_status dev_batch_alloc(Ctx *c, int R) {
 
 // Y[r] = A X[r], r < R (host arrays of device pointers).
 efie_status dev_matvec_batch(Ctx *c, int R, const double2 *const *X, double2 *const *Y) {
-  if (c->opt.precision != EFIE_MIXED_FP32 || c->nI > kMultiMaxNI || R == 1) {
+  if (c->opt.precision != EFIE_MIXED_FP32 || R == 1 || (c->nI > kMultiMaxNI && !m2l_tc_supported(c))) {
     for (int r = 0; r < R; ++r) EFIE_TRY(dev_matvec(c, X[r], Y[r]));
     return EFIE_OK;
   }
@@ -1256,7 +1257,10 @@ efie_status dev_matvec_batch(Ctx *c, int R, const double2 *const *X, double2 *co
   const unsigned gtot = (unsigned)((tot + 255) / 256);
   const int ld = 4 * c->batch_cap;
   k_fold_multi<<<gtot, 256, 0, st>>>(tot, nI, R, ld, mstride, c->d_nodeD, c->d_momB, c->d_srcB); ++c->launches;
-  if (c->n_m2l_targets > 0) {
+  const bool use_tc = c->opt.m2l_batch != 1 && m2l_tc_supported(c);
+  if (c->n_m2l_targets > 0 && use_tc) {
+    EFIE_TRY(launch_m2l_tc(c, st, 4 * R, ld, c->d_srcB, c->d_accB));
+  } else if (c->n_m2l_targets > 0) {
     const int F = 4 * R, KM = (nI + 7) / 8;
     dim3 grid(c->n_m2l_targets, (F + kFB - 1) / kFB);
     const size_t sm = multi_smem(nI);

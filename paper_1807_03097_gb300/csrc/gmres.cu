@@ -510,6 +510,7 @@ efie_status dev_gmres_batch(Ctx *c, int R, const double2 *const *b, double2 *con
     }
   }
   EFIE_CUDA(cudaStreamSynchronize(st));
+  EFIE_TRY(m2l_tc_check(c));
   for (int i = 0; i < R; ++i) {
     its_out[i] = S[i].its;
     res_out[i] = c->opt.tol_is_relative ? (S[i].bn > 0 ? S[i].res / S[i].bn : 0.0) : S[i].res;

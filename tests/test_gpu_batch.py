@@ -27,21 +27,30 @@ def random_block(n, ndof, seed):
     return rng.standard_normal((n, ndof)) + 1j * rng.standard_normal((n, ndof))
 
 
-@pytest.mark.parametrize("case", [
-    # (geometry, p, m, kappa, q, nrhs): ragged field groups (11 -> 44 fields = 32 + 12),
-    # a torus, the largest tile held in shared memory (q = 11, 144 nodes), and q = 12, where
-    # the tile no longer fits and every right-hand side takes the single-field kernel
-    (G.sphere, 2, 2, 3.0, 6, 11),
-    (G.torus, 2, 1, 2.0, 5, 3),
-    (G.sphere, 1, 1, 2.0, 11, 9),
-    (G.sphere, 1, 1, 2.0, 12, 2),
-], ids=["sphere_p2_m2_q6_r11", "torus_p2_m1_q5_r3", "sphere_p1_m1_q11_r9", "sphere_p1_m1_q12_r2"])
-def test_batched_matvec_vs_oracle(case):
+MATVEC_CASES = {
+    # (geometry, p, m, kappa, q, nrhs): ragged field groups (11 -> 44 fields), a torus, 20
+    # right-hand sides (80 fields: a full and a ragged tensor-core group), the largest
+    # tensor-core tile (q = 10, 121 nodes), the largest CUDA-core tile (q = 11, 144 nodes),
+    # and q = 12, where every right-hand side takes the single-field kernel
+    "sphere_p2_m2_q6_r11": (G.sphere, 2, 2, 3.0, 6, 11),
+    "torus_p2_m1_q5_r3": (G.torus, 2, 1, 2.0, 5, 3),
+    "sphere_p1_m2_q8_r20": (G.sphere, 1, 2, 4.0, 8, 20),
+    "sphere_p1_m1_q10_r17": (G.sphere, 1, 1, 2.0, 10, 17),
+    "sphere_p1_m1_q11_r9": (G.sphere, 1, 1, 2.0, 11, 9),
+    "sphere_p1_m1_q12_r2": (G.sphere, 1, 1, 2.0, 12, 2),
+}
+# m2l_batch: 1 CUDA cores, 2 tensor cores (q <= 10)
+MATVEC_PARAMS = [(c, b) for c in MATVEC_CASES for b in (1, 2) if b == 1 or MATVEC_CASES[c][4] <= 10]
+
+
+@pytest.mark.parametrize("name,batch", MATVEC_PARAMS,
+                         ids=[f"{c}-{'cuda' if b == 1 else 'tensor'}" for c, b in MATVEC_PARAMS])
+def test_batched_matvec_vs_oracle(name, batch):
     from paper_1807_03097_gb300 import Solver
 
-    mk, p, m, k, q, nrhs = case
+    mk, p, m, k, q, nrhs = MATVEC_CASES[name]
     geo = mk()
-    s = Solver(geo, p=p, level_m=m, kappa=k, q=q, eta=1.6, precision=1)
+    s = Solver(geo, p=p, level_m=m, kappa=k, q=q, eta=1.6, precision=1, m2l_batch=batch)
     r = O.Problem(geo, p=p, m=m, kappa=k, q=q, eta=1.6)
     x = random_block(nrhs, s.ndof, 21)
     y = s.matvec(x)
@@ -50,6 +59,14 @@ def test_batched_matvec_vs_oracle(case):
         assert rel2(y[i], yr[i]) < TOL32, (i, rel2(y[i], yr[i]))
         assert rel2(y[i], s.matvec(x[i])) < TOL32
     s.close()
+
+
+def test_tensor_core_m2l_rejects_large_q():
+    from paper_1807_03097_gb300 import Solver
+    from paper_1807_03097_gb300.efie import EfieError
+
+    with pytest.raises(EfieError):
+        Solver(G.sphere(), p=1, level_m=1, kappa=1.0, q=11, eta=1.6, precision=1, m2l_batch=2)
 
 
 def test_batched_matvec_more_than_one_chunk():
