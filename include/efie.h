@@ -251,6 +251,10 @@ efie_status efie_server_destroy(efie_server *srv);
 
 /* Static description of a status code. */
 const char *efie_status_string(efie_status s);
+/* Detail of the last failed call on ctx (the failing CUDA call and its error string, or the
+ * reason for EFIE_EINVAL / EFIE_ETIMEOUT); "" if none.  Owned by ctx, valid until the next
+ * call on ctx. */
+const char *efie_last_error(const efie_ctx *ctx);
 
 #ifdef __cplusplus
 }

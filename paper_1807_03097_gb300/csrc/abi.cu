@@ -70,6 +70,11 @@ efie_status check_options(const efie_options *o) {
 
 extern "C" {
 
+const char *efie_last_error(const efie_ctx *ctx) {
+  const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+  return c ? c->err.c_str() : "";
+}
+
 const char *efie_status_string(efie_status s) {
   switch (s) {
     case EFIE_OK: return "ok";

@@ -9,15 +9,15 @@
 //   Re C^T = D1[0:64] - D2[64:128],  Im C^T = D1[64:128] + D2[0:64].
 // Each FP32 operand is split as hi + lo with hi in TF32; the three products hi*hi, hi*lo and
 // lo*hi carry about 21 bits.  The tensor core rounds its accumulator more coarsely than an
-// FP32 add, so each block pair gets a fresh accumulator and the pair's result is added to
-// FP32 registers (two tensor-memory buffers: the MMAs of pair p+1 run while pair p drains).
+// FP32 add, so each block pair gets a fresh accumulator D, and the pair's result is added to
+// running sums S in tensor memory with FP32 adds on the CUDA cores.
 //
-// Warp roles in a block of 288 threads: warps 0-7 stage operands (A from the folded moments,
-// B by evaluating e^{i kappa |x - y|} / (4 pi |x - y|) with the same phase forms as the CUDA
-// core kernels), drain the accumulators and write the result; warp 8 allocates tensor memory
-// and one of its lanes issues the MMAs.  Operands go through two shared-memory stages of 32
-// source nodes each, handed over with mbarriers; every wait is bounded and a wait that runs
-// out sets an error flag for the host.
+// A block has 16 warps.  All of them stage operands (A from the folded moments, B by
+// evaluating e^{i kappa |x - y|} / (4 pi |x - y|) with the same phase forms as the CUDA-core
+// kernels), fold D into S and write the result; warp 0 also allocates tensor memory, and its
+// lane 0 issues the MMAs of a stage once every warp has staged it.  Operands go through two
+// shared-memory stages of 32 source nodes each, handed over with mbarriers; every wait is
+// bounded and a wait that runs out sets an error flag for the host.
 #include "efie_internal.h"
 #include "tc.cuh"
 
@@ -25,9 +25,9 @@ namespace efie {
 
 namespace {
 
-constexpr int kTcFields = 64;       // fields per block (MMA rows = 2 x 64)
-constexpr int kTcProducers = 256;   // threads of warps 0-7
-constexpr int kTcThreads = kTcProducers + 32;
+constexpr int kTcFields = 64;      // fields per block (MMA rows = 2 x 64)
+constexpr int kTcWarps = 16;
+constexpr int kTcThreads = 32 * kTcWarps;
 constexpr long long kTcWaitCycles = 1ll << 31;  // about a second
 
 template <int NP>
@@ -37,15 +37,16 @@ struct TcLayout {
   static constexpr uint32_t kStage = 2 * kA + 4 * kB;  // A hi, A lo, Re B hi/lo, Im B hi/lo
   static constexpr uint32_t kNodes = 2 * kStage;       // target node positions, float4 [NP]
   static constexpr uint32_t kBars = kNodes + 16 * NP;
-  static constexpr uint32_t kBytes = kBars + 80;
-  static constexpr uint32_t kCols = 4 * NP <= 256 ? 256 : 512;  // tensor-memory columns
+  static constexpr uint32_t kBytes = kBars + 64;
+  static constexpr uint32_t kCols = 4 * NP <= 256 ? 256 : 512;  // D1, D2, S1, S2
   static_assert(2 * 128 * (NP + 1) * 4 <= 2 * kStage, "epilogue staging must fit in the stages");
 };
 
-__device__ __forceinline__ float2 kernel_entry(int mode, float4 g, float2 ph, float kappa, float4 xt, float4 xs) {
+template <int MODE>
+__device__ __forceinline__ float2 kernel_entry(float4 g, float2 ph, float kappa, float4 xt, float4 xs) {
   const float inv2pi = 0.15915494309189535f, c1 = 6.28318548202514648f, c2 = -1.7484555e-7f;
   float ex = xt.x - xs.x, ey = xt.y - xs.y, ez = xt.z - xs.z, rinv, phs;
-  if (mode == 0) {
+  if (MODE == 0) {
     float vx = g.x + ex, vy = g.y + ey, vz = g.z + ez;
     float r2 = vx * vx + vy * vy + vz * vz;
     rinv = rsqrtf(r2);
@@ -55,7 +56,7 @@ __device__ __forceinline__ float2 kernel_entry(int mode, float4 g, float2 ph, fl
     float r2 = g.w * g.w + num;
     rinv = rsqrtf(r2);
     phs = kappa * __fdividef(num, r2 * rinv + g.w);
-    if (mode == 2) {
+    if (MODE == 2) {
       float q = rintf(phs * inv2pi);
       phs = fmaf(-q, c1, phs);
       phs = fmaf(-q, c2, phs);
@@ -67,28 +68,44 @@ __device__ __forceinline__ float2 kernel_entry(int mode, float4 g, float2 ph, fl
   return make_float2(ph.x * gr - ph.y * gi, ph.x * gi + ph.y * gr);
 }
 
-__device__ __forceinline__ void st4(uint8_t *base, uint32_t off, const float *v) {
-  *reinterpret_cast<float4 *>(base + off) = make_float4(v[0], v[1], v[2], v[3]);
+__device__ __forceinline__ void st2(uint8_t *base, uint32_t off, float a, float b) {
+  *reinterpret_cast<float2 *>(base + off) = make_float2(a, b);
 }
 
-__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// Read-only loads issued where they stand (volatile: the scheduler does not sink them towards
+// their use), so that the loads of the next stage overlap the evaluation of this one.
+__device__ __forceinline__ float4 ldg_pin(const float4 *p) {
+  float4 v;
+  asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float2 ldg_pin(const float2 *p) {
+  float2 v;
+  asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
 
 }  // namespace
 
-template <int NP>
+// Warp w of the 16 stages, in every stage, the source nodes j = 32 c + 4 (w % 8) + 2 (w / 8) + e
+// (e < 2): lane l the fields l and l + 32 (A rows f and 64 + f) and the target nodes
+// n = l + 32 k (B rows).  Tensor memory: D1 [0, NP), D2 [NP, 2 NP) hold the block pair in
+// flight, S1 [2 NP, 3 NP), S2 [3 NP, 4 NP) the running sums over the far list.
+template <int NP, int MODE>
 __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
     const int *__restrict__ targets, const int *__restrict__ fptr, const int *__restrict__ fsrc,
-    const float4 *__restrict__ pgeo, const float2 *__restrict__ pph, int nI, float kappa, int mode,
+    const float4 *__restrict__ pgeo, const float2 *__restrict__ pph, int nI, float kappa,
     const float4 *__restrict__ nodeX4, int F, int ld, const float2 *__restrict__ src, float2 *__restrict__ acc,
     int *__restrict__ err) {
   using L = TcLayout<NP>;
   extern __shared__ __align__(1024) uint8_t smem[];
   float4 *sXt = reinterpret_cast<float4 *>(smem + L::kNodes);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::kBars);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 8);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 6);
   const uint32_t b_full = tc::smem_u32(&bars[0]), b_empty = tc::smem_u32(&bars[2]);
-  const uint32_t b_tfull = tc::smem_u32(&bars[4]), b_tempty = tc::smem_u32(&bars[6]);
+  const uint32_t b_tfull = tc::smem_u32(&bars[4]), b_tempty = tc::smem_u32(&bars[5]);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int jq = warp & 7, jh = warp >> 3;  // this warp's source nodes: 4 jq + 2 jh + {0, 1}
   const int t = targets[blockIdx.x];
   const int f0 = blockIdx.y * kTcFields;
   const int k0 = fptr[t], nsrc = fptr[t + 1] - k0;
@@ -96,161 +113,225 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
 
   if (tid == 0) {
     for (int i = 0; i < 2; ++i) {
-      tc::mbar_init(b_full + 8 * i, kTcProducers);
+      tc::mbar_init(b_full + 8 * i, kTcThreads);
       tc::mbar_init(b_empty + 8 * i, 1);
-      tc::mbar_init(b_tfull + 8 * i, 1);
-      tc::mbar_init(b_tempty + 8 * i, kTcProducers);
     }
+    tc::mbar_init(b_tfull, 1);
+    tc::mbar_init(b_tempty, kTcThreads);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int i = tid; i < NP; i += blockDim.x) sXt[i] = i < nI ? nodeX4[(size_t)t * nI + i] : make_float4(0, 0, 0, 0);
-  if (warp == 8) tc::tmem_alloc(tc::smem_u32(tslot), L::kCols);
+  for (int i = tid; i < NP; i += kTcThreads) sXt[i] = i < nI ? nodeX4[(size_t)t * nI + i] : make_float4(0, 0, 0, 0);
+  // B rows n >= nI (padding up to NP) stay zero in both stages
+  for (int i = tid; i < 2 * 4 * (NP - nI) * 8; i += kTcThreads) {
+    const int kg = i & 7, n = nI + (i >> 3) % (NP - nI), tl = (i >> 3) / (NP - nI);
+    *reinterpret_cast<float4 *>(smem + (tl >> 2) * L::kStage + 2 * L::kA + (tl & 3) * L::kB +
+                                tc::tile_off(n, 4 * kg)) = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), L::kCols);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
+  const uint32_t idesc = tc::idesc_tf32(128, NP);
+  const int q = warp & 3, r4 = warp >> 2;  // lane quadrant and column quarter of the drain
+  const uint32_t tq = tbase + ((uint32_t)(32 * q) << 16);
 
-  if (warp < 8) {
-    // ---------------------------------------------------------------- producers + drain
-    constexpr int NBH = NP / 32;  // 16-column blocks per thread and accumulator
-    float d1[NBH][16], d2[NBH][16];
+  // S += D for block pair p (S = D for the first), then release D to the MMAs.  This thread
+  // covers lane 32 q + lane and the column blocks b = r4 + 4 i of D1/S1 and D2/S2.
+  auto drain = [&](int p) {
+    constexpr int NB = NP / 32;
+    if (!tc::mbar_wait(b_tfull, p & 1, kTcWaitCycles)) atomicOr(err, 1);
+    tc::fence_after_sync();
 #pragma unroll
-    for (int b = 0; b < NBH; ++b)
+    for (int half = 0; half < 2; ++half) {
+      uint32_t d[NB][8], sv[NB][8];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) d1[b][i] = d2[b][i] = 0.f;
-    const int q = warp & 3, h = warp >> 2;
-    auto drain = [&](int p) {
-      if (!tc::mbar_wait(b_tfull + 8 * (p & 1), (p >> 1) & 1, kTcWaitCycles)) atomicOr(err, 1);
-      tc::fence_after_sync();
-      const uint32_t col = tbase + ((uint32_t)(32 * q) << 16) + (p & 1) * 2 * NP;
-#pragma unroll
-      for (int b = 0; b < NBH; ++b) {
-        float v[16];
-        tc::tmem_ld16(col + 16 * (2 * b + h), v);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) d1[b][i] += v[i];
-        tc::tmem_ld16(col + NP + 16 * (2 * b + h), v);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) d2[b][i] += v[i];
+      for (int i = 0; i < NB; ++i) {
+        const uint32_t cd = tq + half * NP + 8 * (r4 + 4 * i);
+        tc::tmem_ld8_async(cd, d[i]);
+        if (p > 0) tc::tmem_ld8_async(cd + 2 * NP, sv[i]);
       }
-      tc::fence_before_sync();
-      tc::mbar_arrive(b_tempty + 8 * (p & 1));
-    };
-    for (int it = 0; it < T; ++it) {
-      const int st = it & 1, p = it / nchunk, c = it - p * nchunk;
-      if (it >= 2 && !tc::mbar_wait(b_empty + 8 * st, ((it >> 1) & 1) ^ 1, kTcWaitCycles)) atomicOr(err, 2);
-      uint8_t *sAh = smem + st * L::kStage, *sAl = sAh + L::kA;
-      uint8_t *sBrh = sAh + 2 * L::kA, *sBrl = sBrh + L::kB, *sBih = sBrl + L::kB, *sBil = sBih + L::kB;
-      const int s = fsrc[k0 + p];
-      // A: fields on rows (Re 0-63, Im 64-127), 32 source nodes on K
-      for (int task = tid; task < kTcFields * 8; task += kTcProducers) {
-        const int f = task & (kTcFields - 1), jq = task >> 6;
-        float rh[4], rl[4], ih[4], il[4];
+      tc::tmem_wait_ld();
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int j = 32 * c + 4 * jq + e;
-          float2 v = make_float2(0.f, 0.f);
-          if (j < nI && f0 + f < F) v = src[((size_t)s * nI + j) * ld + f0 + f];
-          tc::split_tf32(v.x, rh[e], rl[e]);
-          tc::split_tf32(v.y, ih[e], il[e]);
+      for (int i = 0; i < NB; ++i) {
+        tc::touch8(d[i]);
+        if (p > 0) {
+          tc::touch8(sv[i]);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) d[i][k] = __float_as_uint(__uint_as_float(d[i][k]) + __uint_as_float(sv[i][k]));
         }
-        st4(sAh, tc::tile_off(f, 4 * jq), rh);
-        st4(sAl, tc::tile_off(f, 4 * jq), rl);
-        st4(sAh, tc::tile_off(64 + f, 4 * jq), ih);
-        st4(sAl, tc::tile_off(64 + f, 4 * jq), il);
+        tc::tmem_st8_async(tq + half * NP + 8 * (r4 + 4 * i) + 2 * NP, d[i]);
       }
-      // B: target nodes on rows, 32 source nodes on K
-      const float4 g = pgeo[k0 + p];
-      const float2 ph = pph[k0 + p];
-      for (int task = tid; task < NP * 8; task += kTcProducers) {
-        const int n = task % NP, jq = task / NP;
-        float rh[4], rl[4], ih[4], il[4];
-        const float4 xt = sXt[n];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int j = 32 * c + 4 * jq + e;
-          float2 v = make_float2(0.f, 0.f);
-          if (n < nI && j < nI) v = kernel_entry(mode, g, ph, kappa, xt, nodeX4[(size_t)s * nI + j]);
-          tc::split_tf32(v.x, rh[e], rl[e]);
-          tc::split_tf32(v.y, ih[e], il[e]);
-        }
-        st4(sBrh, tc::tile_off(n, 4 * jq), rh);
-        st4(sBrl, tc::tile_off(n, 4 * jq), rl);
-        st4(sBih, tc::tile_off(n, 4 * jq), ih);
-        st4(sBil, tc::tile_off(n, 4 * jq), il);
-      }
-      tc::fence_proxy_async();
-      tc::mbar_arrive(b_full + 8 * st);
-      if (c == nchunk - 1 && p >= 1) drain(p - 1);
     }
-    if (nsrc >= 1) drain(nsrc - 1);
-    // ------------------------------------------------------------------- epilogue
-    // all MMAs are complete: the stage memory holds D1 and D2 as [128][NP + 1]
-    producers_sync();
-    float *sD1 = reinterpret_cast<float *>(smem), *sD2 = sD1 + 128 * (NP + 1);
-    const int m = 32 * q + lane;
-#pragma unroll
-    for (int b = 0; b < NBH; ++b)
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int col = 16 * (2 * b + h) + i;
-        sD1[m * (NP + 1) + col] = d1[b][i];
-        sD2[m * (NP + 1) + col] = d2[b][i];
-      }
-    producers_sync();
-    for (int idx = tid; idx < nI * kTcFields; idx += kTcProducers) {
-      const int f = idx & (kTcFields - 1), i = idx >> 6;
-      if (f0 + f >= F) continue;
-      const float re = sD1[f * (NP + 1) + i] - sD2[(64 + f) * (NP + 1) + i];
-      const float im = sD1[(64 + f) * (NP + 1) + i] + sD2[f * (NP + 1) + i];
-      acc[((size_t)t * nI + i) * ld + f0 + f] = make_float2(re, im);
+    tc::tmem_wait_st();
+    tc::fence_before_sync();
+    tc::mbar_arrive(b_tempty);
+  };
+
+  float4 cx[2], nx[2];
+  float2 ca[2][2], na[2][2];
+  float4 cg, ng = make_float4(0, 0, 0, 1);
+  float2 cph, nph = make_float2(0, 0);
+  int s_next = nsrc > 0 ? fsrc[k0] : 0;
+  int lp = 0, lc = 0;  // (pair, chunk) that load_stage fetches next
+  auto load_stage = [&]() {
+    if (lp >= nsrc) return;
+    const int p2 = lp, c2 = lc;
+    if (++lc == nchunk) {
+      lc = 0;
+      ++lp;
     }
-  } else if (lane == 0) {
-    // ---------------------------------------------------------------------- MMA issue
-    const uint32_t idesc = tc::idesc_tf32(128, NP);
-    for (int it = 0; it < T; ++it) {
-      const int st = it & 1, p = it / nchunk, c = it - p * nchunk;
-      if (c == 0 && p >= 2 && !tc::mbar_wait(b_tempty + 8 * (p & 1), ((p >> 1) & 1) ^ 1, kTcWaitCycles))
-        atomicOr(err, 4);
+    const int s2 = s_next;
+    if (lp < nsrc && lc == 0) s_next = fsrc[k0 + lp];
+    ng = pgeo[k0 + p2];
+    nph = pph[k0 + p2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int j = 32 * c2 + 4 * jq + 2 * jh + e;
+      const bool jv = j < nI;
+      nx[e] = jv ? ldg_pin(nodeX4 + (size_t)s2 * nI + j) : make_float4(0, 0, 0, 0);
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int f = lane + 32 * k;
+        na[k][e] = (jv && f0 + f < F) ? ldg_pin(src + ((size_t)s2 * nI + j) * ld + f0 + f) : make_float2(0.f, 0.f);
+      }
+    }
+  };
+  load_stage();
+  for (int it = 0, p = 0, c = 0; it < T; ++it, c = (c + 1 == nchunk) ? 0 : c + 1, p += (c == 0)) {
+    const int st = it & 1;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      cx[e] = nx[e];
+      ca[0][e] = na[0][e];
+      ca[1][e] = na[1][e];
+    }
+    cg = ng;
+    cph = nph;
+    load_stage();
+    if (it >= 2 && !tc::mbar_wait(b_empty + 8 * st, ((it >> 1) & 1) ^ 1, kTcWaitCycles)) atomicOr(err, 2);
+    uint8_t *sAh = smem + st * L::kStage, *sAl = sAh + L::kA;
+    uint8_t *sBrh = sAh + 2 * L::kA, *sBrl = sBrh + L::kB, *sBih = sBrl + L::kB, *sBil = sBih + L::kB;
+    const uint32_t kcol = 4 * jq + 2 * jh;
+    // A: fields on rows (Re 0-63, Im 64-127), this warp's 2 source nodes on K
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int f = lane + 32 * k;
+      float rh[2], rl[2], ih[2], il[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        tc::split_tf32(ca[k][e].x, rh[e], rl[e]);
+        tc::split_tf32(ca[k][e].y, ih[e], il[e]);
+      }
+      st2(sAh, tc::tile_off(f, kcol), rh[0], rh[1]);
+      st2(sAl, tc::tile_off(f, kcol), rl[0], rl[1]);
+      st2(sAh, tc::tile_off(64 + f, kcol), ih[0], ih[1]);
+      st2(sAl, tc::tile_off(64 + f, kcol), il[0], il[1]);
+    }
+    // B: target nodes on rows, this warp's 2 source nodes on K
+    const int jb = 32 * c + (int)kcol;
+#pragma unroll
+    for (int k = 0; k < NP / 32; ++k) {
+      const int n = lane + 32 * k;
+      if (n >= nI) continue;  // padding rows, zero since the start
+      const float4 xt = sXt[n];
+      float rh[2], rl[2], ih[2], il[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const float2 gv = jb + e < nI ? kernel_entry<MODE>(cg, cph, kappa, xt, cx[e]) : make_float2(0.f, 0.f);
+        tc::split_tf32(gv.x, rh[e], rl[e]);
+        tc::split_tf32(gv.y, ih[e], il[e]);
+      }
+      st2(sBrh, tc::tile_off(n, kcol), rh[0], rh[1]);
+      st2(sBrl, tc::tile_off(n, kcol), rl[0], rl[1]);
+      st2(sBih, tc::tile_off(n, kcol), ih[0], ih[1]);
+      st2(sBil, tc::tile_off(n, kcol), il[0], il[1]);
+    }
+    tc::fence_proxy_async();
+    tc::mbar_arrive(b_full + 8 * st);
+    // the previous pair's MMAs are done by now: fold it into the running sums
+    if (c == 0 && p >= 1) drain(p - 1);
+    if (warp == 0 && lane == 0) {
+      // MMAs of this stage: D1 (+)= A Re B^T and D2 (+)= A Im B^T, three split products each
+      if (c == 0 && p >= 1 && !tc::mbar_wait(b_tempty, (p - 1) & 1, kTcWaitCycles)) atomicOr(err, 4);
       if (!tc::mbar_wait(b_full + 8 * st, (it >> 1) & 1, kTcWaitCycles)) atomicOr(err, 8);
       tc::fence_after_sync();
       const int ksteps = min(4, (nI - 32 * c + 7) / 8);
-      const uint32_t ah = tc::smem_u32(smem + st * L::kStage), al = ah + L::kA;
+      const uint32_t ah = tc::smem_u32(sAh), al = ah + L::kA;
       const uint32_t brh = ah + 2 * L::kA, brl = brh + L::kB, bih = brl + L::kB, bil = bih + L::kB;
-      const uint32_t d1 = tbase + (p & 1) * 2 * NP, d2 = d1 + NP;
+      const uint32_t d1c = tbase, d2c = tbase + NP;
       for (int ks = 0; ks < ksteps; ++ks) {
         const uint32_t o = ks * tc::kKStepBytes, accum = (c > 0 || ks > 0) ? 1u : 0u;
         const uint64_t dah = tc::smem_desc(ah + o), dal = tc::smem_desc(al + o);
-        tc::mma_tf32(d1, dah, tc::smem_desc(brh + o), idesc, accum);
-        tc::mma_tf32(d1, dah, tc::smem_desc(brl + o), idesc, 1u);
-        tc::mma_tf32(d1, dal, tc::smem_desc(brh + o), idesc, 1u);
-        tc::mma_tf32(d2, dah, tc::smem_desc(bih + o), idesc, accum);
-        tc::mma_tf32(d2, dah, tc::smem_desc(bil + o), idesc, 1u);
-        tc::mma_tf32(d2, dal, tc::smem_desc(bih + o), idesc, 1u);
+        tc::mma_tf32(d1c, dah, tc::smem_desc(brh + o), idesc, accum);
+        tc::mma_tf32(d1c, dah, tc::smem_desc(brl + o), idesc, 1u);
+        tc::mma_tf32(d1c, dal, tc::smem_desc(brh + o), idesc, 1u);
+        tc::mma_tf32(d2c, dah, tc::smem_desc(bih + o), idesc, accum);
+        tc::mma_tf32(d2c, dah, tc::smem_desc(bil + o), idesc, 1u);
+        tc::mma_tf32(d2c, dal, tc::smem_desc(bih + o), idesc, 1u);
       }
       tc::mma_commit(b_empty + 8 * st);
-      if (c == nchunk - 1) tc::mma_commit(b_tfull + 8 * (p & 1));
+      if (c == nchunk - 1) tc::mma_commit(b_tfull);
     }
+    __syncwarp();
+  }
+  if (nsrc >= 1) drain(nsrc - 1);
+  // ------------------------------------------------------------------------- epilogue
+  // every MMA is complete and drained: stage the sums as [128][NP + 1] in the stage memory
+  __syncthreads();
+  float *sS1 = reinterpret_cast<float *>(smem), *sS2 = sS1 + 128 * (NP + 1);
+  const int m = 32 * q + lane;
+  if (nsrc >= 1) {
+    tc::fence_after_sync();
+#pragma unroll 1
+    for (int b = r4; b < NP / 8; b += 4) {
+      float v[8];
+      tc::tmem_ld8(tq + 2 * NP + 8 * b, v);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) sS1[m * (NP + 1) + 8 * b + i] = v[i];
+      tc::tmem_ld8(tq + 3 * NP + 8 * b, v);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) sS2[m * (NP + 1) + 8 * b + i] = v[i];
+    }
+  } else {
+    for (int b = r4; b < NP / 8; b += 4)
+      for (int i = 0; i < 8; ++i) sS1[m * (NP + 1) + 8 * b + i] = sS2[m * (NP + 1) + 8 * b + i] = 0.f;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < nI * kTcFields; idx += kTcThreads) {
+    const int f = idx & (kTcFields - 1), i = idx >> 6;
+    if (f0 + f >= F) continue;
+    const float re = sS1[f * (NP + 1) + i] - sS2[(64 + f) * (NP + 1) + i];
+    const float im = sS1[(64 + f) * (NP + 1) + i] + sS2[f * (NP + 1) + i];
+    acc[((size_t)t * nI + i) * ld + f0 + f] = make_float2(re, im);
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 8) tc::tmem_dealloc(tbase, L::kCols);
+  if (warp == 0) tc::tmem_dealloc(tbase, L::kCols);
+}
+
+template <int NP, int MODE>
+static efie_status tc_attr() {
+  cudaError_t e = cudaFuncSetAttribute(k_m2l_tc<NP, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)TcLayout<NP>::kBytes);
+  return e == cudaSuccess ? EFIE_OK : EFIE_ECUDA;
 }
 
 template <int NP>
-static efie_status tc_attr() {
-  cudaError_t e = cudaFuncSetAttribute(k_m2l_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)TcLayout<NP>::kBytes);
-  return e == cudaSuccess ? EFIE_OK : EFIE_ECUDA;
+static efie_status tc_attrs() {
+  efie_status e = tc_attr<NP, 0>();
+  if (e == EFIE_OK) e = tc_attr<NP, 1>();
+  if (e == EFIE_OK) e = tc_attr<NP, 2>();
+  return e;
 }
 
 bool m2l_tc_supported(const Ctx *c) { return c->nI <= 128; }
 
 efie_status m2l_tc_prepare(Ctx *c) {
-  EFIE_TRY(tc_attr<64>());
-  EFIE_TRY(tc_attr<96>());
-  EFIE_TRY(tc_attr<128>());
+  EFIE_TRY(tc_attrs<64>());
+  EFIE_TRY(tc_attrs<96>());
+  EFIE_TRY(tc_attrs<128>());
   if (!c->d_tc_err) {
     EFIE_CUDA(cudaMalloc((void **)&c->d_tc_err, sizeof(int)));
     EFIE_CUDA(cudaMemset(c->d_tc_err, 0, sizeof(int)));
@@ -258,21 +339,28 @@ efie_status m2l_tc_prepare(Ctx *c) {
   return EFIE_OK;
 }
 
+template <int NP>
+static void launch_np(Ctx *c, cudaStream_t st, dim3 grid, int F, int ld, const float2 *src, float2 *acc) {
+  const float kf = (float)c->kappa;
+#define EFIE_TC(MV)                                                                                      \
+  k_m2l_tc<NP, MV><<<grid, kTcThreads, TcLayout<NP>::kBytes, st>>>(c->d_m2l_targets, c->d_far_ptr,          \
+                                                                   c->d_far_src, c->d_pgeo, c->d_pph, c->nI, \
+                                                                   kf, c->d_nodeX4, F, ld, src, acc, c->d_tc_err)
+  if (c->m2l_mode == 0) EFIE_TC(0);
+  else if (c->m2l_mode == 1) EFIE_TC(1);
+  else EFIE_TC(2);
+#undef EFIE_TC
+}
+
 // acc[t][i][f] for the targets of the M2L, f < F = 4 R, row stride ld (float2 entries)
 efie_status launch_m2l_tc(Ctx *c, cudaStream_t st, int F, int ld, const float2 *src, float2 *acc) {
   if (c->n_m2l_targets == 0) return EFIE_OK;
   const int nI = c->nI;
   dim3 grid(c->n_m2l_targets, (F + kTcFields - 1) / kTcFields);
-  const float kf = (float)c->kappa;
-#define EFIE_TC(NPV)                                                                                          \
-  k_m2l_tc<NPV><<<grid, kTcThreads, TcLayout<NPV>::kBytes, st>>>(c->d_m2l_targets, c->d_far_ptr, c->d_far_src, \
-                                                                 c->d_pgeo, c->d_pph, nI, kf, c->m2l_mode,     \
-                                                                 c->d_nodeX4, F, ld, src, acc, c->d_tc_err)
-  if (nI <= 64) EFIE_TC(64);
-  else if (nI <= 96) EFIE_TC(96);
-  else if (nI <= 128) EFIE_TC(128);
+  if (nI <= 64) launch_np<64>(c, st, grid, F, ld, src, acc);
+  else if (nI <= 96) launch_np<96>(c, st, grid, F, ld, src, acc);
+  else if (nI <= 128) launch_np<128>(c, st, grid, F, ld, src, acc);
   else return EFIE_EINVAL;
-#undef EFIE_TC
   ++c->launches;
   EFIE_CUDA(cudaGetLastError());
   return EFIE_OK;

@@ -27,7 +27,8 @@ ABI_SYMBOLS = (
     "efie_default_options", "efie_create", "efie_set_geometry", "efie_setup", "efie_num_dofs",
     "efie_matvec", "efie_rhs_plane_waves", "efie_solve", "efie_solve_plane_waves", "efie_far_field",
     "efie_block_counts", "efie_export_blocks", "efie_export_near_blocks", "efie_matvec_superspace",
-    "efie_last_timings", "efie_launch_count", "efie_destroy", "efie_status_string", "efie_far_field_noalloc",
+    "efie_last_timings", "efie_launch_count", "efie_destroy", "efie_status_string", "efie_last_error",
+    "efie_far_field_noalloc",
     "efie_server_create", "efie_server_submit", "efie_server_poll", "efie_server_destroy",
 )
 
@@ -59,10 +60,11 @@ class EfieResult(ctypes.Structure):
 
 
 class EfieError(RuntimeError):
-    def __init__(self, status, where, lib):
+    def __init__(self, status, where, lib, handle=None):
         self.status = status
         msg = lib.efie_status_string(status).decode()
-        super().__init__(f"{where}: status {status} ({msg})")
+        detail = lib.efie_last_error(handle).decode() if handle else ""
+        super().__init__(f"{where}: status {status} ({msg})" + (f": {detail}" if detail else ""))
 
 
 _lib = None
@@ -103,6 +105,7 @@ def load(path: str = LIB_PATH):
         "efie_server_destroy": (c_int, [P]),
         "efie_destroy": (c_int, [P]),
         "efie_status_string": (ctypes.c_char_p, [c_int]),
+        "efie_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -161,7 +164,7 @@ class Solver:
 
     def _check(self, st, where):
         if st < 0:
-            raise EfieError(st, where, self._L)
+            raise EfieError(st, where, self._L, getattr(self, "h", None))
         return st
 
     def close(self):
