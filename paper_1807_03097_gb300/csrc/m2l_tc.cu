@@ -9,8 +9,9 @@
 //   Re C^T = D1[0:64] - D2[64:128],  Im C^T = D1[64:128] + D2[0:64].
 // Each FP32 operand is split as hi + lo with hi in TF32; the three products hi*hi, hi*lo and
 // lo*hi carry about 21 bits.  The tensor core rounds its accumulator more coarsely than an
-// FP32 add, so each block pair gets a fresh accumulator D, and the pair's result is added to
-// running sums S in tensor memory with FP32 adds on the CUDA cores.
+// FP32 add, so every group of 4 block pairs gets a fresh accumulator D = [D1 D2] (one MMA of
+// N = 2 NP against B = [Re G; Im G]), and the group's result is added to running sums S in
+// tensor memory with FP32 adds on the CUDA cores.
 //
 // A block has 16 warps.  All of them stage operands (A from the folded moments, B by
 // evaluating e^{i kappa |x - y|} / (4 pi |x - y|) with the same phase forms as the CUDA-core
@@ -29,12 +30,13 @@ constexpr int kTcFields = 64;      // fields per block (MMA rows = 2 x 64)
 constexpr int kTcWarps = 16;
 constexpr int kTcThreads = 32 * kTcWarps;
 constexpr long long kTcWaitCycles = 1ll << 31;  // about a second
+constexpr int kTcGroup = 4;  // block pairs accumulated in D before it is folded into S
 
 template <int NP>
 struct TcLayout {
   static constexpr uint32_t kA = 128 * 128;            // one [128 x 32] FP32 tile
   static constexpr uint32_t kB = NP * 128;             // one [NP x 32] FP32 tile
-  static constexpr uint32_t kStage = 2 * kA + 4 * kB;  // A hi, A lo, Re B hi/lo, Im B hi/lo
+  static constexpr uint32_t kStage = 2 * kA + 4 * kB;  // A hi, A lo, B hi, B lo (B: Re rows, Im rows)
   static constexpr uint32_t kNodes = 2 * kStage;       // target node positions, float4 [NP]
   static constexpr uint32_t kBars = kNodes + 16 * NP;
   static constexpr uint32_t kBytes = kBars + 64;
@@ -84,13 +86,19 @@ __device__ __forceinline__ float2 ldg_pin(const float2 *p) {
   asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
   return v;
 }
+__device__ __forceinline__ int ldg_pin(const int *p) {
+  int v;
+  asm volatile("ld.global.nc.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
 
 }  // namespace
 
-// Warp w of the 16 stages, in every stage, the source nodes j = 32 c + 4 (w % 8) + 2 (w / 8) + e
-// (e < 2): lane l the fields l and l + 32 (A rows f and 64 + f) and the target nodes
-// n = l + 32 k (B rows).  Tensor memory: D1 [0, NP), D2 [NP, 2 NP) hold the block pair in
-// flight, S1 [2 NP, 3 NP), S2 [3 NP, 4 NP) the running sums over the far list.
+// Staging map of a stage: lane l of warp w covers the source nodes j = 32 c + 4 (w % 8) +
+// 2 ((l / 8) % 2) + e (e < 2) and the rows r = l % 8 + 8 (l / 16) + 16 (2 i + w / 8): fields
+// f = r (A rows f and 64 + f, i < 2) and target nodes n = r (B rows, i < NP / 32).  A
+// half-warp then writes 8 rows x 4 K-columns, 32 distinct banks.  Tensor memory: D1 [0, NP), D2 [NP, 2 NP) hold the group of block
+// pairs in flight, S1 [2 NP, 3 NP), S2 [3 NP, 4 NP) the running sums over the far list.
 template <int NP, int MODE>
 __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
     const int *__restrict__ targets, const int *__restrict__ fptr, const int *__restrict__ fsrc,
@@ -105,7 +113,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
   const uint32_t b_full = tc::smem_u32(&bars[0]), b_empty = tc::smem_u32(&bars[2]);
   const uint32_t b_tfull = tc::smem_u32(&bars[4]), b_tempty = tc::smem_u32(&bars[5]);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int jq = warp & 7, jh = warp >> 3;  // this warp's source nodes: 4 jq + 2 jh + {0, 1}
+  const int jq = warp & 7, jh = (lane >> 3) & 1;  // source nodes 4 jq + 2 jh + {0, 1}
+  const int rbase = (lane & 7) + 8 * (lane >> 4) + 16 * (warp >> 3);  // rows rbase + 32 i
   const int t = targets[blockIdx.x];
   const int f0 = blockIdx.y * kTcFields;
   const int k0 = fptr[t], nsrc = fptr[t + 1] - k0;
@@ -121,26 +130,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int i = tid; i < NP; i += kTcThreads) sXt[i] = i < nI ? nodeX4[(size_t)t * nI + i] : make_float4(0, 0, 0, 0);
-  // B rows n >= nI (padding up to NP) stay zero in both stages
-  for (int i = tid; i < 2 * 4 * (NP - nI) * 8; i += kTcThreads) {
+  // B rows of target nodes n >= nI (padding up to NP, in the Re and the Im half) stay zero
+  for (int i = tid; i < 2 * 2 * 2 * (NP - nI) * 8; i += kTcThreads) {
     const int kg = i & 7, n = nI + (i >> 3) % (NP - nI), tl = (i >> 3) / (NP - nI);
-    *reinterpret_cast<float4 *>(smem + (tl >> 2) * L::kStage + 2 * L::kA + (tl & 3) * L::kB +
-                                tc::tile_off(n, 4 * kg)) = make_float4(0.f, 0.f, 0.f, 0.f);
+    // tl: stage (bit 2), hi/lo tile (bit 1), Re/Im half (bit 0)
+    *reinterpret_cast<float4 *>(smem + (tl >> 2) * L::kStage + 2 * L::kA + ((tl >> 1) & 1) * 2 * L::kB +
+                                tc::tile_off((tl & 1) * NP + n, 4 * kg)) = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), L::kCols);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
-  const uint32_t idesc = tc::idesc_tf32(128, NP);
+  const uint32_t idesc = tc::idesc_tf32(128, 2 * NP);
   const int q = warp & 3, r4 = warp >> 2;  // lane quadrant and column quarter of the drain
   const uint32_t tq = tbase + ((uint32_t)(32 * q) << 16);
 
-  // S += D for block pair p (S = D for the first), then release D to the MMAs.  This thread
-  // covers lane 32 q + lane and the column blocks b = r4 + 4 i of D1/S1 and D2/S2.
-  auto drain = [&](int p) {
+  // S += D for group g of block pairs (S = D for the first), then release D to the MMAs.
+  // This thread covers lane 32 q + lane and the column blocks b = r4 + 4 i of D1/S1, D2/S2.
+  auto drain = [&](int g) {
     constexpr int NB = NP / 32;
-    if (!tc::mbar_wait(b_tfull, p & 1, kTcWaitCycles)) atomicOr(err, 1);
+    const int p = g;
+    if (!tc::mbar_wait(b_tfull, g & 1, kTcWaitCycles)) atomicOr(err, 1);
     tc::fence_after_sync();
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
@@ -172,7 +183,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
   float2 ca[2][2], na[2][2];
   float4 cg, ng = make_float4(0, 0, 0, 1);
   float2 cph, nph = make_float2(0, 0);
-  int s_next = nsrc > 0 ? fsrc[k0] : 0;
+  int s_next = nsrc > 0 ? ldg_pin(fsrc + k0) : 0;
   int lp = 0, lc = 0;  // (pair, chunk) that load_stage fetches next
   auto load_stage = [&]() {
     if (lp >= nsrc) return;
@@ -182,9 +193,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
       ++lp;
     }
     const int s2 = s_next;
-    if (lp < nsrc && lc == 0) s_next = fsrc[k0 + lp];
-    ng = pgeo[k0 + p2];
-    nph = pph[k0 + p2];
+    if (lp < nsrc && lc == 0) s_next = ldg_pin(fsrc + k0 + lp);
+    ng = ldg_pin(pgeo + k0 + p2);
+    nph = ldg_pin(pph + k0 + p2);
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int j = 32 * c2 + 4 * jq + 2 * jh + e;
@@ -192,7 +203,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
       nx[e] = jv ? ldg_pin(nodeX4 + (size_t)s2 * nI + j) : make_float4(0, 0, 0, 0);
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        const int f = lane + 32 * k;
+        const int f = rbase + 32 * k;
         na[k][e] = (jv && f0 + f < F) ? ldg_pin(src + ((size_t)s2 * nI + j) * ld + f0 + f) : make_float2(0.f, 0.f);
       }
     }
@@ -211,12 +222,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
     load_stage();
     if (it >= 2 && !tc::mbar_wait(b_empty + 8 * st, ((it >> 1) & 1) ^ 1, kTcWaitCycles)) atomicOr(err, 2);
     uint8_t *sAh = smem + st * L::kStage, *sAl = sAh + L::kA;
-    uint8_t *sBrh = sAh + 2 * L::kA, *sBrl = sBrh + L::kB, *sBih = sBrl + L::kB, *sBil = sBih + L::kB;
+    uint8_t *sBh = sAh + 2 * L::kA, *sBl = sBh + 2 * L::kB;  // rows [0, NP) Re, [NP, 2 NP) Im
     const uint32_t kcol = 4 * jq + 2 * jh;
     // A: fields on rows (Re 0-63, Im 64-127), this warp's 2 source nodes on K
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const int f = lane + 32 * k;
+      const int f = rbase + 32 * k;
       float rh[2], rl[2], ih[2], il[2];
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
@@ -232,7 +243,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
     const int jb = 32 * c + (int)kcol;
 #pragma unroll
     for (int k = 0; k < NP / 32; ++k) {
-      const int n = lane + 32 * k;
+      const int n = rbase + 32 * k;
       if (n >= nI) continue;  // padding rows, zero since the start
       const float4 xt = sXt[n];
       float rh[2], rl[2], ih[2], il[2];
@@ -242,40 +253,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
         tc::split_tf32(gv.x, rh[e], rl[e]);
         tc::split_tf32(gv.y, ih[e], il[e]);
       }
-      st2(sBrh, tc::tile_off(n, kcol), rh[0], rh[1]);
-      st2(sBrl, tc::tile_off(n, kcol), rl[0], rl[1]);
-      st2(sBih, tc::tile_off(n, kcol), ih[0], ih[1]);
-      st2(sBil, tc::tile_off(n, kcol), il[0], il[1]);
+      st2(sBh, tc::tile_off(n, kcol), rh[0], rh[1]);
+      st2(sBl, tc::tile_off(n, kcol), rl[0], rl[1]);
+      st2(sBh, tc::tile_off(NP + n, kcol), ih[0], ih[1]);
+      st2(sBl, tc::tile_off(NP + n, kcol), il[0], il[1]);
     }
     tc::fence_proxy_async();
     tc::mbar_arrive(b_full + 8 * st);
-    // the previous pair's MMAs are done by now: fold it into the running sums
-    if (c == 0 && p >= 1) drain(p - 1);
+    // the previous group's MMAs are done by now: fold it into the running sums
+    const bool gstart = c == 0 && p % kTcGroup == 0;
+    if (gstart && p >= 1) drain(p / kTcGroup - 1);
     if (warp == 0 && lane == 0) {
-      // MMAs of this stage: D1 (+)= A Re B^T and D2 (+)= A Im B^T, three split products each
-      if (c == 0 && p >= 1 && !tc::mbar_wait(b_tempty, (p - 1) & 1, kTcWaitCycles)) atomicOr(err, 4);
+      // MMAs of this stage: [D1 D2] (+)= A [Re B; Im B]^T, three split products
+      if (gstart && p >= 1 && !tc::mbar_wait(b_tempty, (p / kTcGroup - 1) & 1, kTcWaitCycles)) atomicOr(err, 4);
       if (!tc::mbar_wait(b_full + 8 * st, (it >> 1) & 1, kTcWaitCycles)) atomicOr(err, 8);
       tc::fence_after_sync();
       const int ksteps = min(4, (nI - 32 * c + 7) / 8);
       const uint32_t ah = tc::smem_u32(sAh), al = ah + L::kA;
-      const uint32_t brh = ah + 2 * L::kA, brl = brh + L::kB, bih = brl + L::kB, bil = bih + L::kB;
-      const uint32_t d1c = tbase, d2c = tbase + NP;
+      const uint32_t bh = ah + 2 * L::kA, bl = bh + 2 * L::kB;
       for (int ks = 0; ks < ksteps; ++ks) {
-        const uint32_t o = ks * tc::kKStepBytes, accum = (c > 0 || ks > 0) ? 1u : 0u;
-        const uint64_t dah = tc::smem_desc(ah + o), dal = tc::smem_desc(al + o);
-        tc::mma_tf32(d1c, dah, tc::smem_desc(brh + o), idesc, accum);
-        tc::mma_tf32(d1c, dah, tc::smem_desc(brl + o), idesc, 1u);
-        tc::mma_tf32(d1c, dal, tc::smem_desc(brh + o), idesc, 1u);
-        tc::mma_tf32(d2c, dah, tc::smem_desc(bih + o), idesc, accum);
-        tc::mma_tf32(d2c, dah, tc::smem_desc(bil + o), idesc, 1u);
-        tc::mma_tf32(d2c, dal, tc::smem_desc(bih + o), idesc, 1u);
+        const uint32_t o = ks * tc::kKStepBytes, accum = (gstart && ks == 0) ? 0u : 1u;
+        const uint64_t dah = tc::smem_desc(ah + o), dbh = tc::smem_desc(bh + o);
+        tc::mma_tf32(tbase, dah, dbh, idesc, accum);
+        tc::mma_tf32(tbase, dah, tc::smem_desc(bl + o), idesc, 1u);
+        tc::mma_tf32(tbase, tc::smem_desc(al + o), dbh, idesc, 1u);
       }
       tc::mma_commit(b_empty + 8 * st);
-      if (c == nchunk - 1) tc::mma_commit(b_tfull);
+      if (c == nchunk - 1 && (p % kTcGroup == kTcGroup - 1 || p == nsrc - 1)) tc::mma_commit(b_tfull);
     }
     __syncwarp();
   }
-  if (nsrc >= 1) drain(nsrc - 1);
+  if (nsrc >= 1) drain((nsrc - 1) / kTcGroup);
   // ------------------------------------------------------------------------- epilogue
   // every MMA is complete and drained: stage the sums as [128][NP + 1] in the stage memory
   __syncthreads();
