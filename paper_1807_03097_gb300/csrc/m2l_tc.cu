@@ -13,10 +13,11 @@
 // N = 2 NP against B = [Re G; Im G]), and the group's result is added to running sums S in
 // tensor memory with FP32 adds on the CUDA cores.
 //
-// A block has 16 warps.  All of them stage operands (A from the folded moments, B by
-// evaluating e^{i kappa |x - y|} / (4 pi |x - y|) with the same phase forms as the CUDA-core
-// kernels), fold D into S and write the result; warp 0 also allocates tensor memory, and its
-// lane 0 issues the MMAs of a stage once every warp has staged it.  Operands go through two
+// A block has 17 warps.  Warps 0-15 stage operands (A from the folded moments, B by evaluating
+// e^{i kappa |x - y|} / (4 pi |x - y|) with the same phase forms as the CUDA-core kernels),
+// fold D into S and write the result; warp 0 also allocates tensor memory.  Lane 0 of warp 16
+// issues the MMAs of a stage once every staging warp has written it: the issuing thread
+// stalls while the tensor pipe is busy, which a staging warp cannot afford.  Operands go through two
 // shared-memory stages of 32 source nodes each, handed over with mbarriers; every wait is
 // bounded and a wait that runs out sets an error flag for the host.
 #include "efie_internal.h"
@@ -27,8 +28,9 @@ namespace efie {
 namespace {
 
 constexpr int kTcFields = 64;      // fields per block (MMA rows = 2 x 64)
-constexpr int kTcWarps = 16;
-constexpr int kTcThreads = 32 * kTcWarps;
+constexpr int kTcWarps = 16;                    // staging warps
+constexpr int kTcProducers = 32 * kTcWarps;
+constexpr int kTcThreads = kTcProducers + 32;   // + the MMA-issue warp
 constexpr long long kTcWaitCycles = 1ll << 31;  // about a second
 constexpr int kTcGroup = 4;  // block pairs accumulated in D before it is folded into S
 
@@ -122,11 +124,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
 
   if (tid == 0) {
     for (int i = 0; i < 2; ++i) {
-      tc::mbar_init(b_full + 8 * i, kTcThreads);
+      tc::mbar_init(b_full + 8 * i, kTcProducers);
       tc::mbar_init(b_empty + 8 * i, 1);
     }
     tc::mbar_init(b_tfull, 1);
-    tc::mbar_init(b_tempty, kTcThreads);
+    tc::mbar_init(b_tempty, kTcProducers);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int i = tid; i < NP; i += kTcThreads) sXt[i] = i < nI ? nodeX4[(size_t)t * nI + i] : make_float4(0, 0, 0, 0);
@@ -146,6 +148,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
   const int q = warp & 3, r4 = warp >> 2;  // lane quadrant and column quarter of the drain
   const uint32_t tq = tbase + ((uint32_t)(32 * q) << 16);
 
+  if (warp < kTcWarps) {
   // S += D for group g of block pairs (S = D for the first), then release D to the MMAs.
   // This thread covers lane 32 q + lane and the column blocks b = r4 + 4 i of D1/S1, D2/S2.
   auto drain = [&](int g) {
@@ -263,33 +266,43 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
     // the previous group's MMAs are done by now: fold it into the running sums
     const bool gstart = c == 0 && p % kTcGroup == 0;
     if (gstart && p >= 1) drain(p / kTcGroup - 1);
-    if (warp == 0 && lane == 0) {
-      // MMAs of this stage: [D1 D2] (+)= A [Re B; Im B]^T, three split products
+  }
+  if (nsrc >= 1) drain((nsrc - 1) / kTcGroup);
+  } else if (lane == 0) {
+    // ------------------------------------------------------------------- MMA issue
+    // One thread, so that its waits on the tensor pipe stall no staging warp.  Descriptors are
+    // built once; the start address sits in the low bits, so stage st and K-step ks are
+    // reached by adding (st kStage + 256 ks) / 16 (shared addresses stay below 2^18 bytes).
+    const uint32_t a0 = tc::smem_u32(smem);
+    const uint64_t dah0 = tc::smem_desc(a0), dal0 = tc::smem_desc(a0 + L::kA);
+    const uint64_t dbh0 = tc::smem_desc(a0 + 2 * L::kA), dbl0 = tc::smem_desc(a0 + 2 * L::kA + 2 * L::kB);
+    for (int it = 0, p = 0, c = 0; it < T; ++it, c = (c + 1 == nchunk) ? 0 : c + 1, p += (c == 0)) {
+      const int st = it & 1;
+      const bool gstart = c == 0 && p % kTcGroup == 0;
+      // [D1 D2] (+)= A [Re B; Im B]^T, three split products per K-step
       if (gstart && p >= 1 && !tc::mbar_wait(b_tempty, (p / kTcGroup - 1) & 1, kTcWaitCycles)) atomicOr(err, 4);
       if (!tc::mbar_wait(b_full + 8 * st, (it >> 1) & 1, kTcWaitCycles)) atomicOr(err, 8);
       tc::fence_after_sync();
       const int ksteps = min(4, (nI - 32 * c + 7) / 8);
-      const uint32_t ah = tc::smem_u32(sAh), al = ah + L::kA;
-      const uint32_t bh = ah + 2 * L::kA, bl = bh + 2 * L::kB;
       for (int ks = 0; ks < ksteps; ++ks) {
-        const uint32_t o = ks * tc::kKStepBytes, accum = (gstart && ks == 0) ? 0u : 1u;
-        const uint64_t dah = tc::smem_desc(ah + o), dbh = tc::smem_desc(bh + o);
-        tc::mma_tf32(tbase, dah, dbh, idesc, accum);
-        tc::mma_tf32(tbase, dah, tc::smem_desc(bl + o), idesc, 1u);
-        tc::mma_tf32(tbase, tc::smem_desc(al + o), dbh, idesc, 1u);
+        const uint64_t o = (uint64_t)(st * (L::kStage >> 4) + 16 * ks);
+        tc::mma_tf32(tbase, dah0 + o, dbh0 + o, idesc, (gstart && ks == 0) ? 0u : 1u);
+        tc::mma_tf32(tbase, dah0 + o, dbl0 + o, idesc, 1u);
+        tc::mma_tf32(tbase, dal0 + o, dbh0 + o, idesc, 1u);
       }
       tc::mma_commit(b_empty + 8 * st);
       if (c == nchunk - 1 && (p % kTcGroup == kTcGroup - 1 || p == nsrc - 1)) tc::mma_commit(b_tfull);
     }
-    __syncwarp();
   }
-  if (nsrc >= 1) drain((nsrc - 1) / kTcGroup);
+  __syncwarp();
   // ------------------------------------------------------------------------- epilogue
   // every MMA is complete and drained: stage the sums as [128][NP + 1] in the stage memory
   __syncthreads();
   float *sS1 = reinterpret_cast<float *>(smem), *sS2 = sS1 + 128 * (NP + 1);
   const int m = 32 * q + lane;
-  if (nsrc >= 1) {
+  if (warp >= kTcWarps) {
+    // the MMA-issue warp takes no part in staging the sums
+  } else if (nsrc >= 1) {
     tc::fence_after_sync();
 #pragma unroll 1
     for (int b = r4; b < NP / 8; b += 4) {
