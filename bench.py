@@ -325,6 +325,106 @@ def run_gpu(args):
     return 0
 
 
+# ---------------------------------------------------------------------------- many right-hand sides
+MULTI = {
+    "workload": "torus16_nurbs_p3_n64_kappa20_q10_eta1.6_64rhs",
+    "geometry": "torus R=2, r=0.5, 16 rational biquadratic patches",
+    "p": 3, "elements_per_patch": "64x64", "level_m": 6, "kappa": 20.0, "q": 10, "eta": 1.6,
+    "rhs": 64, "directions": "plane waves, directions normalised Gaussian, polarisation random unit vector "
+                             "orthogonal to the direction, seed 1807",
+    "precision": "mixed: M2L split-TF32 on the tensor cores with FP32 accumulation, near field FP32 blocks "
+                 "from FP64 quadrature, geometry FP64",
+    "l2": "working set > L2 (near-field blocks 19 GB FP32, 64 x 2.1e6 superspace vectors)",
+}
+
+
+def run_multi(args):
+    """One step = one matrix-vector product of all 64 right-hand sides (a batched GMRES
+    iteration's product); value = right-hand-side products per second."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1807_03097_gb300 import Solver
+
+    w = MULTI
+    geo = G.torus(R=2.0, r=0.5)
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    s = Solver(geo, stream=stream.cuda_stream, p=w["p"], level_m=w["level_m"], kappa=w["kappa"], q=w["q"],
+               eta=w["eta"], precision=1, m2l_batch=0)
+    setup_s = time.time() - t0
+    N, R = s.ndof, w["rhs"]
+    d, pol = G.plane_waves(R, seed=1807)
+    b = s.rhs(d, pol)                                    # [R][N] right-hand sides (host)
+    x = torch.from_numpy(b).cuda()
+    y = torch.empty_like(x)
+    for _ in range(args.warmup):
+        s.matvec(x, out=y)
+    torch.cuda.synchronize()
+    clk = ClockSampler(0)
+    clk.start()
+    l0 = s.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    ph = []
+    for _ in range(args.steps):
+        s.matvec(x, out=y)
+        ph.append(s.last_timings())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    launches = s.launch_count() - l0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    mv = {k: statistics.median([p_[k] for p_ in ph]) for k in ph[0]}
+    # the batched tensor-core product against the single-vector FP32 product (CUDA cores)
+    # for two right-hand sides
+    y1 = torch.empty_like(x[0])
+    diffs = []
+    for i in (0, R - 1):
+        s.matvec(x[i], out=y1)
+        diffs.append(float(torch.linalg.norm(y[i] - y1) / torch.linalg.norm(y1)))
+    single_ms = s.last_timings()["total"]
+    # roofline of the tensor-core M2L (useful complex work; TF32 peak = measured BF16 peak x
+    # the nominal TF32/BF16 ratio 1.1/2.25)
+    pk = peaks()
+    nI = (w["q"] + 1) ** 2
+    useful = 8.0 * nI * nI * 4 * R * s.nfar
+    np_ = 64 if nI <= 64 else (96 if nI <= 96 else 128)
+    kp = 8 * sum(min(4, (nI - 32 * c + 7) // 8) for c in range((nI + 31) // 32))
+    executed = 3 * 2.0 * 128 * (2 * np_) * kp * ((4 * R + 63) // 64) * s.nfar
+    tf32_peak = pk.get("bf16_tflops", 1900.0) * 1.1 / 2.25
+    m2l_s = mv["m2l"] * 1e-3
+    roof = {"kernel": "k_m2l_tc", "bound": "tensor", "achieved": useful / m2l_s / 1e12, "peak": tf32_peak,
+            "unit": "TFLOP/s", "frac": useful / m2l_s / 1e12 / tf32_peak, "traffic": None,
+            "peak_note": "TF32 dense = measured BF16 burst peak x 1.1/2.25 (nominal ratio)",
+            "work": f"useful 8 n_I^2 x 4R x far pairs = {useful:.3e} real flop per product "
+                    f"(complex MACs of {4 * R} fields); executed on the tensor pipe (3 split-TF32 passes, "
+                    f"padded to N={2 * np_}, K={kp}) = {executed:.3e}",
+            "executed_tflops": executed / m2l_s / 1e12, "m2l_ms": mv["m2l"]}
+    # end to end with host buffers
+    yh = np.empty_like(b)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.e2e_steps)):
+        s.matvec(b, out=yh)
+    e2e_ms = (time.perf_counter() - t0) * 1000.0 / max(1, args.e2e_steps)
+    line = {"metric": "FMM-EFIE matvec/s (right-hand-side products per second, 64 right-hand sides per "
+                      "batched product), mixed precision",
+            "value": R * 1000.0 / ms, "unit": "matvec/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "tf32x3-m2l/f32/f64", "data": "synthetic", "config": MULTI, "ndof": int(N),
+            "far_pairs": int(s.nfar), "near_pairs": int(s.nnear), "setup_s": setup_s,
+            "matvec_ms_phases": mv, "single_rhs_matvec_ms": single_ms,
+            "tensor_vs_single_rhs_rel_diff": diffs, "roofline": roof, "cpu_baseline": None,
+            "cpu_baseline_note": "the FP64 oracle is timed on the default workload only",
+            "e2e": {"value": R * 1000.0 / e2e_ms, "unit": "matvec/s", "h2d_bytes_per_step": int(b.nbytes),
+                    "d2h_bytes_per_step": int(yh.nbytes)},
+            "gpu_launches": int(launches), "clocks": clocks}
+    print(json.dumps(line))
+    s.close()
+    return 0
+
+
 # ---------------------------------------------------------------------------- serving
 SERVING = {
     "workload": "serving_poisson50_mixed_1e-5",
@@ -407,7 +507,7 @@ def main():
     ap.add_argument("--ref-iterations", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-steps", action="store_true", help="time the steps only (for launch-list profiling)")
-    ap.add_argument("--workload", default="solve", choices=["solve", "serving"])
+    ap.add_argument("--workload", default="solve", choices=["solve", "serving", "multi"])
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--m2l-store", type=int, default=0, choices=[0, 1, 2],
                     help="M2L coupling matrices: 0 auto (kept in HBM when they fit), 1 evaluated, 2 kept")
@@ -416,6 +516,8 @@ def main():
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "multi":
+        return run_multi(args)
     return run_gpu(args)
 
 

@@ -355,6 +355,20 @@ efie_status efie_export_near_blocks(efie_ctx *ctx, double *blocks) {
   return EFIE_OK;
 }
 
+// device times of the phases of the last product (events recorded by dev_matvec and
+// dev_matvec_batch): total, gather, near field, moments + M2M, M2L, L2L + evaluation, scatter
+static void collect_timings(Ctx *c) {
+  float ms[7];
+  cudaEventElapsedTime(&ms[0], c->tm.ev[0], c->tm.ev[6]);
+  cudaEventElapsedTime(&ms[1], c->tm.ev[0], c->tm.ev[1]);
+  cudaEventElapsedTime(&ms[2], c->tm.ev[1], c->tm.ev[2]);
+  cudaEventElapsedTime(&ms[3], c->tm.ev[1], c->tm.ev[3]);
+  cudaEventElapsedTime(&ms[4], c->tm.ev[3], c->tm.ev[4]);
+  cudaEventElapsedTime(&ms[5], c->tm.ev[4], c->tm.ev[5]);
+  cudaEventElapsedTime(&ms[6], c->tm.ev[5], c->tm.ev[6]);
+  for (int i = 0; i < 7; ++i) c->last_ms[i] = ms[i];
+}
+
 efie_status efie_matvec(efie_ctx *ctx, int nrhs, const double *x, double *y, int ptr_kind) {
   Ctx *c = reinterpret_cast<Ctx *>(ctx);
   if (!c || nrhs < 0 || (nrhs > 0 && (!x || !y))) return EFIE_EINVAL;
@@ -388,6 +402,7 @@ efie_status efie_matvec(efie_ctx *ctx, int nrhs, const double *x, double *y, int
       }
     }
     EFIE_CUDA(cudaStreamSynchronize(c->stream));
+    collect_timings(c);  // phases of the last pass
     return m2l_tc_check(c);
   }
   for (int r = 0; r < nrhs; ++r) {
@@ -402,17 +417,7 @@ efie_status efie_matvec(efie_ctx *ctx, int nrhs, const double *x, double *y, int
     }
   }
   EFIE_CUDA(cudaStreamSynchronize(c->stream));
-  if (nrhs > 0) {
-    float ms[7];
-    cudaEventElapsedTime(&ms[0], c->tm.ev[0], c->tm.ev[6]);
-    cudaEventElapsedTime(&ms[1], c->tm.ev[0], c->tm.ev[1]);
-    cudaEventElapsedTime(&ms[2], c->tm.ev[1], c->tm.ev[2]);
-    cudaEventElapsedTime(&ms[3], c->tm.ev[1], c->tm.ev[3]);
-    cudaEventElapsedTime(&ms[4], c->tm.ev[3], c->tm.ev[4]);
-    cudaEventElapsedTime(&ms[5], c->tm.ev[4], c->tm.ev[5]);
-    cudaEventElapsedTime(&ms[6], c->tm.ev[5], c->tm.ev[6]);
-    for (int i = 0; i < 7; ++i) c->last_ms[i] = ms[i];
-  }
+  if (nrhs > 0) collect_timings(c);
   return EFIE_OK;
 }
 

@@ -1230,6 +1230,9 @@ efie_status dev_matvec_batch(Ctx *c, int R, const double2 *const *X, double2 *co
   }
   EFIE_TRY(dev_batch_alloc(c, R));
   cudaStream_t st = c->stream;
+  // phase events as in the single-vector product: 0 start, 1 gathered, 2 near done (second
+  // stream), 3 moments folded, 4 M2L done, 5 local expansions evaluated, 6 end
+  EFIE_CUDA(cudaEventRecord(c->tm.ev[0], st));
   const int nI = c->nI, q1 = c->q1, p1 = c->p1, m = c->m;
   const float h = (float)(1.0 / c->n);
   const size_t mstride = (size_t)c->ncl * 3 * nI;
@@ -1238,10 +1241,12 @@ efie_status dev_matvec_batch(Ctx *c, int R, const double2 *const *X, double2 *co
     k_gather<<<(c->nsup + 255) / 256, 256, 0, st>>>(c->nsup, c->d_tg_ptr, c->d_tg_col, c->d_tg_val,
                                                     X[r], xs); ++c->launches;
   }
+  EFIE_CUDA(cudaEventRecord(c->tm.ev[1], st));
   EFIE_CUDA(cudaEventRecord(c->fork, st));
   EFIE_CUDA(cudaStreamWaitEvent(c->stream2, c->fork, 0));
   for (int r = 0; r < R; ++r)
     EFIE_TRY(dev_near_apply(c, c->d_xsB + (size_t)r * c->nsup, c->d_ysnB + (size_t)r * c->nsup, c->stream2));
+  EFIE_CUDA(cudaEventRecord(c->tm.ev[2], c->stream2));
   EFIE_CUDA(cudaEventRecord(c->join, c->stream2));
   for (int r = 0; r < R; ++r) {
     float2 *mom = c->d_momB + r * mstride;
@@ -1257,6 +1262,7 @@ efie_status dev_matvec_batch(Ctx *c, int R, const double2 *const *X, double2 *co
   const unsigned gtot = (unsigned)((tot + 255) / 256);
   const int ld = 4 * c->batch_cap;
   k_fold_multi<<<gtot, 256, 0, st>>>(tot, nI, R, ld, mstride, c->d_nodeD, c->d_momB, c->d_srcB); ++c->launches;
+  EFIE_CUDA(cudaEventRecord(c->tm.ev[3], st));
   const bool use_tc = c->opt.m2l_batch != 1 && m2l_tc_supported(c);
   if (c->n_m2l_targets > 0 && use_tc) {
     EFIE_TRY(launch_m2l_tc(c, st, 4 * R, ld, c->d_srcB, c->d_accB));
@@ -1279,6 +1285,7 @@ efie_status dev_matvec_batch(Ctx *c, int R, const double2 *const *X, double2 *co
 #undef EFIE_MULTI
     ++c->launches;
   }
+  EFIE_CUDA(cudaEventRecord(c->tm.ev[4], st));
   k_unfold_multi<<<gtot, 256, 0, st>>>(tot, nI, R, ld, mstride, (float)(1.0 / (c->kappa * c->kappa)), c->d_nodeD,
                                        c->d_accB, c->d_locB); ++c->launches;
   for (int r = 0; r < R; ++r) {
@@ -1291,12 +1298,14 @@ efie_status dev_matvec_batch(Ctx *c, int R, const double2 *const *X, double2 *co
     k_leaf_eval<float><<<c->nE, 128, 0, st>>>(c->nE, c->lev_off[m], p1, q1, h, c->d_M, c->d_Md, loc,
                                               c->d_ysB + (size_t)r * c->nsup); ++c->launches;
   }
+  EFIE_CUDA(cudaEventRecord(c->tm.ev[5], st));
   EFIE_CUDA(cudaStreamWaitEvent(st, c->join, 0));
   for (int r = 0; r < R; ++r) {
     k_scatter<<<(c->ndof + 255) / 256, 256, 0, st>>>(c->ndof, c->d_ts_ptr, c->d_ts_col, c->d_ts_val,
                                                      c->d_ysB + (size_t)r * c->nsup, c->d_ysnB + (size_t)r * c->nsup,
                                                      Y[r]); ++c->launches;
   }
+  EFIE_CUDA(cudaEventRecord(c->tm.ev[6], st));
   EFIE_CUDA(cudaGetLastError());
   return EFIE_OK;
 }
