@@ -173,6 +173,7 @@ efie_status dev_far_field(Ctx *c, const double2 *w, int ndir, const double *dirs
 efie_status dev_gmres(Ctx *c, const double2 *b, double2 *x, int *its, double *res, int *conv);
 efie_status dev_alloc_work(Ctx *c);
 efie_status dev_near_blocks_f32(Ctx *c);
+efie_status dev_near_apply_batch(Ctx *c, int R, const double2 *xs, double2 *ysn, size_t vstride, cudaStream_t st);
 // Y[r] = A X[r] for r < R (host arrays of device pointers); one pass in the mixed form
 efie_status dev_matvec_batch(Ctx *c, int R, const double2 *const *X, double2 *const *Y);
 // R independent GMRES solves advanced in lockstep, one batched matvec per step

@@ -73,9 +73,12 @@ __global__ void k_add(int n, double2 *a, const double2 *b) {
 // nu(m)      = h sum_ab (Md[m1][a] M[m2][b] x*_{0,b,a} + M[m1][a] Md[m2][b] x*_{1,b,a})
 template <class R>
 __global__ void k_leaf_moments(int nE, int leaf_off, int p1, int q1, R h, const double *__restrict__ Mt,
-                               const double *__restrict__ Mdt, const double2 *__restrict__ xs, C2<R> *__restrict__ mom) {
+                               const double *__restrict__ Mdt, const double2 *__restrict__ xs, C2<R> *__restrict__ mom,
+                               size_t xstride = 0, size_t mstride = 0) {
   int e = blockIdx.x;
   if (e >= nE) return;
+  xs += blockIdx.y * xstride;  // right-hand side blockIdx.y of a batch
+  mom += blockIdx.y * mstride;
   int nI = q1 * q1;
   __shared__ R sM[kMaxQ1 * kMaxP1], sMd[kMaxQ1 * kMaxP1];
   __shared__ C2<R> sx[2 * kMaxP1 * kMaxP1];
@@ -126,9 +129,10 @@ __global__ void k_leaf_moments(int nE, int leaf_off, int p1, int q1, R h, const 
 // parent(f, m2, m1) = sum_c sum_{m2'} E[c2][m2][m2'] sum_{m1'} E[c1][m1][m1'] child_c(f, m2', m1')
 template <class R>
 __global__ void k_m2m(int nparent, int par_off, int ch_off, int q1, const double *__restrict__ Et,
-                      C2<R> *__restrict__ mom) {
+                      C2<R> *__restrict__ mom, size_t mstride = 0) {
   int pid = blockIdx.x;
   if (pid >= nparent) return;
+  mom += blockIdx.y * mstride;
   int nI = q1 * q1;
   extern __shared__ unsigned char smraw[];
   R *sE = (R *)smraw;                                      // [2][q1][q1]
@@ -638,9 +642,10 @@ __global__ void __launch_bounds__(128) k_m2l_f64_stored(const int *__restrict__ 
 // child_c(f, m2', m1') += sum_{m2} E[c2][m2][m2'] sum_{m1} E[c1][m1][m1'] parent(f, m2, m1)
 template <class R>
 __global__ void k_l2l(int nparent, int par_off, int ch_off, int q1, const double *__restrict__ Et,
-                      C2<R> *__restrict__ loc) {
+                      C2<R> *__restrict__ loc, size_t mstride = 0) {
   int pid = blockIdx.x;
   if (pid >= nparent) return;
+  loc += blockIdx.y * mstride;
   int nI = q1 * q1;
   extern __shared__ unsigned char smraw[];
   R *sE = (R *)smraw;
@@ -685,9 +690,12 @@ __global__ void k_l2l(int nparent, int par_off, int ch_off, int q1, const double
 // y*_{1,b,a} = h^2 sum_m M[m1][a] M[m2][b] l_1(m) + h sum_m M[m1][a] Md[m2][b] l_div(m)
 template <class R>
 __global__ void k_leaf_eval(int nE, int leaf_off, int p1, int q1, R h, const double *__restrict__ Mt,
-                            const double *__restrict__ Mdt, const C2<R> *__restrict__ loc, double2 *__restrict__ ys) {
+                            const double *__restrict__ Mdt, const C2<R> *__restrict__ loc, double2 *__restrict__ ys,
+                            size_t mstride = 0, size_t ystride = 0) {
   int e = blockIdx.x;
   if (e >= nE) return;
+  loc += blockIdx.y * mstride;  // right-hand side blockIdx.y of a batch
+  ys += blockIdx.y * ystride;
   int nI = q1 * q1;
   __shared__ R sM[kMaxQ1 * kMaxP1], sMd[kMaxQ1 * kMaxP1];
   __shared__ C2<R> R0[kMaxQ1 * kMaxP1], R1[kMaxQ1 * kMaxP1], R2[kMaxQ1 * kMaxP1], Rd[kMaxQ1 * kMaxP1];
@@ -1244,19 +1252,16 @@ efie_status dev_matvec_batch(Ctx *c, int R, const double2 *const *X, double2 *co
   EFIE_CUDA(cudaEventRecord(c->tm.ev[1], st));
   EFIE_CUDA(cudaEventRecord(c->fork, st));
   EFIE_CUDA(cudaStreamWaitEvent(c->stream2, c->fork, 0));
-  for (int r = 0; r < R; ++r)
-    EFIE_TRY(dev_near_apply(c, c->d_xsB + (size_t)r * c->nsup, c->d_ysnB + (size_t)r * c->nsup, c->stream2));
+  EFIE_TRY(dev_near_apply_batch(c, R, c->d_xsB, c->d_ysnB, (size_t)c->nsup, c->stream2));
   EFIE_CUDA(cudaEventRecord(c->tm.ev[2], c->stream2));
   EFIE_CUDA(cudaEventRecord(c->join, c->stream2));
-  for (int r = 0; r < R; ++r) {
-    float2 *mom = c->d_momB + r * mstride;
-    k_leaf_moments<float><<<c->nE, 128, 0, st>>>(c->nE, c->lev_off[m], p1, q1, h, c->d_M, c->d_Md,
-                                                 c->d_xsB + (size_t)r * c->nsup, mom); ++c->launches;
-    for (int l = m - 1; l >= 0; --l) {
-      int npar = c->np << (2 * l);
-      k_m2m<float><<<npar, 128, m2m_smem(q1, sizeof(float2)), st>>>(npar, c->lev_off[l], c->lev_off[l + 1], q1, c->d_E,
-                                                                    mom); ++c->launches;
-    }
+  // leaf moments and M2M of all right-hand sides: grid dimension y = right-hand side
+  k_leaf_moments<float><<<dim3(c->nE, R), 128, 0, st>>>(c->nE, c->lev_off[m], p1, q1, h, c->d_M, c->d_Md, c->d_xsB,
+                                                        c->d_momB, (size_t)c->nsup, mstride); ++c->launches;
+  for (int l = m - 1; l >= 0; --l) {
+    int npar = c->np << (2 * l);
+    k_m2m<float><<<dim3(npar, R), 128, m2m_smem(q1, sizeof(float2)), st>>>(npar, c->lev_off[l], c->lev_off[l + 1], q1,
+                                                                           c->d_E, c->d_momB, mstride); ++c->launches;
   }
   const long long tot = (long long)c->ncl * nI;
   const unsigned gtot = (unsigned)((tot + 255) / 256);
@@ -1288,16 +1293,13 @@ efie_status dev_matvec_batch(Ctx *c, int R, const double2 *const *X, double2 *co
   EFIE_CUDA(cudaEventRecord(c->tm.ev[4], st));
   k_unfold_multi<<<gtot, 256, 0, st>>>(tot, nI, R, ld, mstride, (float)(1.0 / (c->kappa * c->kappa)), c->d_nodeD,
                                        c->d_accB, c->d_locB); ++c->launches;
-  for (int r = 0; r < R; ++r) {
-    float2 *loc = c->d_locB + r * mstride;
-    for (int l = 0; l < m; ++l) {
-      int npar = c->np << (2 * l);
-      k_l2l<float><<<npar, 128, l2l_smem(q1, sizeof(float2)), st>>>(npar, c->lev_off[l], c->lev_off[l + 1], q1, c->d_E,
-                                                                    loc); ++c->launches;
-    }
-    k_leaf_eval<float><<<c->nE, 128, 0, st>>>(c->nE, c->lev_off[m], p1, q1, h, c->d_M, c->d_Md, loc,
-                                              c->d_ysB + (size_t)r * c->nsup); ++c->launches;
+  for (int l = 0; l < m; ++l) {
+    int npar = c->np << (2 * l);
+    k_l2l<float><<<dim3(npar, R), 128, l2l_smem(q1, sizeof(float2)), st>>>(npar, c->lev_off[l], c->lev_off[l + 1], q1,
+                                                                           c->d_E, c->d_locB, mstride); ++c->launches;
   }
+  k_leaf_eval<float><<<dim3(c->nE, R), 128, 0, st>>>(c->nE, c->lev_off[m], p1, q1, h, c->d_M, c->d_Md, c->d_locB,
+                                                     c->d_ysB, mstride, (size_t)c->nsup); ++c->launches;
   EFIE_CUDA(cudaEventRecord(c->tm.ev[5], st));
   EFIE_CUDA(cudaStreamWaitEvent(st, c->join, 0));
   for (int r = 0; r < R; ++r) {

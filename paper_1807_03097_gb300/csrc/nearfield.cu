@@ -404,6 +404,112 @@ __global__ void __launch_bounds__(32 * kApplyWarps) k_near_apply(int nE, const i
   }
 }
 
+// The same product for several right-hand sides (FP32 blocks, mixed form): each block is read
+// once for a group of up to RB right-hand sides (grid dimension y), which divides the HBM
+// traffic of the near field by RB.  Vectors of right-hand side r start at r * vstride.
+template <int NB, int RB>
+__global__ void __launch_bounds__(32 * kApplyWarps) k_near_apply_multi(int nE, int R, size_t vstride,
+                                                                       const int *__restrict__ ptr,
+                                                                       const int *__restrict__ src,
+                                                                       const float2 *__restrict__ blocks,
+                                                                       const double2 *__restrict__ xs,
+                                                                       double2 *__restrict__ ysn) {
+  constexpr int GS = NB <= 8 ? 8 : (NB <= 16 ? 16 : 32);
+  constexpr int NG = 32 / GS;
+  constexpr int RPL = (NB + GS - 1) / GS;
+  constexpr int XPL = (NB + GS - 1) / GS;
+  __shared__ float red[kApplyWarps * NG][NB][RB][2];
+  const int e = blockIdx.x;
+  if (e >= nE) return;
+  const int r0 = blockIdx.y * RB, nr = min(RB, R - r0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / GS, rl = lane % GS;
+  const int gid = warp * NG + g, ngroups = kApplyWarps * NG;
+  float ar[RPL][RB], ai[RPL][RB], cr[RPL][RB], ci[RPL][RB];
+#pragma unroll
+  for (int t = 0; t < RPL; ++t)
+#pragma unroll
+    for (int j = 0; j < RB; ++j) ar[t][j] = ai[t][j] = cr[t][j] = ci[t][j] = 0.f;
+  const int k0 = ptr[e], k1 = ptr[e + 1];
+  for (int kb = k0; kb < k1; kb += ngroups) {
+    const int k = kb + gid;
+    const bool act = k < k1;
+    const float2 *B = blocks + (size_t)(act ? k : k0) * NB * NB;
+    const size_t xo = (size_t)src[act ? k : k0] * NB;
+    float xr[RB][XPL], xi[RB][XPL];
+#pragma unroll
+    for (int j = 0; j < RB; ++j)
+#pragma unroll
+      for (int t = 0; t < XPL; ++t) {
+        const int cidx = rl + GS * t;
+        double2 v = (act && cidx < NB && j < nr) ? xs[(size_t)(r0 + j) * vstride + xo + cidx] : make_double2(0.0, 0.0);
+        xr[j][t] = (float)v.x;
+        xi[j][t] = (float)v.y;
+      }
+    float pr[RPL][RB], pim[RPL][RB];
+#pragma unroll
+    for (int t = 0; t < RPL; ++t)
+#pragma unroll
+      for (int j = 0; j < RB; ++j) pr[t][j] = pim[t][j] = 0.f;
+#pragma unroll
+    for (int tc = 0; tc < XPL; ++tc) {
+      const int ncol = (NB - GS * tc) < GS ? (NB - GS * tc) : GS;
+#pragma unroll 2
+      for (int c0 = 0; c0 < ncol; ++c0) {
+        const int cc = GS * tc + c0;
+        float2 b[RPL];
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+          const int rr = rl + GS * t;
+          b[t] = (act && rr < NB) ? B[cc * NB + rr] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < RB; ++j) {
+          const float vr = __shfl_sync(0xffffffffu, xr[j][tc], g * GS + c0);
+          const float vi = __shfl_sync(0xffffffffu, xi[j][tc], g * GS + c0);
+#pragma unroll
+          for (int t = 0; t < RPL; ++t) {
+            pr[t][j] += b[t].x * vr - b[t].y * vi;
+            pim[t][j] += b[t].x * vi + b[t].y * vr;
+          }
+        }
+      }
+    }
+    // per-source partial sums enter the running sums with two-sum compensation
+#pragma unroll
+    for (int t = 0; t < RPL; ++t)
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        const float sr = ar[t][j] + pr[t][j], si = ai[t][j] + pim[t][j];
+        const float br = sr - ar[t][j], bi = si - ai[t][j];
+        cr[t][j] += (ar[t][j] - (sr - br)) + (pr[t][j] - br);
+        ci[t][j] += (ai[t][j] - (si - bi)) + (pim[t][j] - bi);
+        ar[t][j] = sr;
+        ai[t][j] = si;
+      }
+  }
+#pragma unroll
+  for (int t = 0; t < RPL; ++t) {
+    const int rr = rl + GS * t;
+    if (rr < NB)
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        red[gid][rr][j][0] = ar[t][j] + cr[t][j];
+        red[gid][rr][j][1] = ai[t][j] + ci[t][j];
+      }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NB * nr; i += blockDim.x) {
+    const int rr = i % NB, j = i / NB;
+    double sr = 0.0, si = 0.0;
+    for (int q = 0; q < ngroups; ++q) {
+      sr += (double)red[q][rr][j][0];
+      si += (double)red[q][rr][j][1];
+    }
+    ysn[(size_t)(r0 + j) * vstride + (size_t)e * NB + rr] = make_double2(sr, si);
+  }
+}
+
 __global__ void k_blocks_to_f32(size_t n, const double2 *__restrict__ in, float2 *__restrict__ out) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
@@ -413,6 +519,37 @@ efie_status dev_near_blocks_f32(Ctx *c) {
   size_t n = (size_t)c->nnear * c->nb * c->nb;
   EFIE_TRY(dalloc(c, &c->d_nblkf, n));
   k_blocks_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, c->d_nblk, c->d_nblkf); ++c->launches;
+  EFIE_CUDA(cudaGetLastError());
+  return EFIE_OK;
+}
+
+efie_status dev_near_apply(Ctx *c, const double2 *xs, double2 *ysn, cudaStream_t st);
+
+// R right-hand sides, vector r at xs + r vstride (FP32 blocks of the mixed form)
+efie_status dev_near_apply_batch(Ctx *c, int R, const double2 *xs, double2 *ysn, size_t vstride, cudaStream_t st) {
+  constexpr int RB = 8;
+  if (!c->d_nblkf) {
+    for (int r = 0; r < R; ++r) EFIE_TRY(dev_near_apply(c, xs + r * vstride, ysn + r * vstride, st));
+    return EFIE_OK;
+  }
+  const dim3 grid(c->nE, (R + RB - 1) / RB);
+  const int threads = 32 * kApplyWarps;
+  switch (c->nb) {
+#define EFIE_APPLYB_CASE(NBV)                                                                                \
+  case NBV:                                                                                                  \
+    k_near_apply_multi<NBV, RB><<<grid, threads, 0, st>>>(c->nE, R, vstride, c->d_near_ptr, c->d_near_src,   \
+                                                          c->d_nblkf, xs, ysn);                              \
+    break;
+    EFIE_APPLYB_CASE(8)
+    EFIE_APPLYB_CASE(18)
+    EFIE_APPLYB_CASE(32)
+    EFIE_APPLYB_CASE(50)
+#undef EFIE_APPLYB_CASE
+    default:
+      c->err = "unsupported block size";
+      return EFIE_EINVAL;
+  }
+  ++c->launches;
   EFIE_CUDA(cudaGetLastError());
   return EFIE_OK;
 }
