@@ -1,6 +1,7 @@
 """Run a few matrix-vector products of one configurable case (for profiling a kernel on a
 case smaller than the benchmark's).  Example:
     python -m paper_1807_03097_gb300.profile_case --p 2 --m 4 --kappa 10 --q 8 --precision mixed --matvecs 3
+--nrhs R > 1 applies each product to R random right-hand sides at once (batched product).
 """
 import argparse
 import os
@@ -21,6 +22,8 @@ def main():
     ap.add_argument("--eta", type=float, default=1.6)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--matvecs", type=int, default=3)
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--m2l-batch", type=int, default=0, choices=[0, 1, 2])
     a = ap.parse_args()
     from paper_1807_03097_gb300 import Solver
     from workloads import geometry as G
@@ -29,17 +32,19 @@ def main():
     import time
 
     t0 = time.perf_counter()
-    s = Solver(geo, p=a.p, level_m=a.m, kappa=a.kappa, q=a.q, eta=a.eta, precision=1 if a.precision == "mixed" else 0)
+    s = Solver(geo, p=a.p, level_m=a.m, kappa=a.kappa, q=a.q, eta=a.eta, precision=1 if a.precision == "mixed" else 0,
+               m2l_batch=a.m2l_batch)
     t_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
     s.setup()
     t_setup2 = time.perf_counter() - t0
     rng = np.random.default_rng(0)
-    x = rng.standard_normal(s.ndof) + 1j * rng.standard_normal(s.ndof)
+    shape = (a.nrhs, s.ndof) if a.nrhs > 1 else (s.ndof,)
+    x = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
     for _ in range(a.matvecs):
         y = s.matvec(x)
     t = s.last_timings()
-    print(f"ndof {s.ndof} far {s.nfar} near {s.nnear} setup s {t_setup:.3f} (again {t_setup2:.3f}) matvec ms "
+    print(f"nrhs {a.nrhs} ndof {s.ndof} far {s.nfar} near {s.nnear} setup s {t_setup:.3f} (again {t_setup2:.3f}) matvec ms "
           + " ".join(f"{k}={v:.3f}" for k, v in t.items()))
     s.close()
 
