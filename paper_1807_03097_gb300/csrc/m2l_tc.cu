@@ -46,16 +46,18 @@ struct TcLayout {
   static_assert(2 * 128 * (NP + 1) * 4 <= 2 * kStage, "epilogue staging must fit in the stages");
 };
 
+// ut = g + xt (pair offset plus target node), used by the direct form (MODE 0) only
 template <int MODE>
-__device__ __forceinline__ float2 kernel_entry(float4 g, float2 ph, float kappa, float4 xt, float4 xs) {
+__device__ __forceinline__ float2 kernel_entry(float4 g, float2 ph, float kappa, float4 xt, float4 ut, float4 xs) {
   const float inv2pi = 0.15915494309189535f, c1 = 6.28318548202514648f, c2 = -1.7484555e-7f;
-  float ex = xt.x - xs.x, ey = xt.y - xs.y, ez = xt.z - xs.z, rinv, phs;
+  float rinv, phs;
   if (MODE == 0) {
-    float vx = g.x + ex, vy = g.y + ey, vz = g.z + ez;
+    float vx = ut.x - xs.x, vy = ut.y - xs.y, vz = ut.z - xs.z;
     float r2 = vx * vx + vy * vy + vz * vz;
     rinv = rsqrtf(r2);
     phs = fmaf(kappa, r2 * rinv, -kappa * g.w);
   } else {
+    float ex = xt.x - xs.x, ey = xt.y - xs.y, ez = xt.z - xs.z;
     float num = fmaf(2.f, g.x * ex + g.y * ey + g.z * ez, ex * ex + ey * ey + ez * ez);
     float r2 = g.w * g.w + num;
     rinv = rsqrtf(r2);
@@ -249,10 +251,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
       const int n = rbase + 32 * k;
       if (n >= nI) continue;  // padding rows, zero since the start
       const float4 xt = sXt[n];
+      const float4 ut = make_float4(cg.x + xt.x, cg.y + xt.y, cg.z + xt.z, 0.f);
       float rh[2], rl[2], ih[2], il[2];
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
-        const float2 gv = jb + e < nI ? kernel_entry<MODE>(cg, cph, kappa, xt, cx[e]) : make_float2(0.f, 0.f);
+        const float2 gv = jb + e < nI ? kernel_entry<MODE>(cg, cph, kappa, xt, ut, cx[e]) : make_float2(0.f, 0.f);
         tc::split_tf32(gv.x, rh[e], rl[e]);
         tc::split_tf32(gv.y, ih[e], il[e]);
       }

@@ -38,6 +38,9 @@ MATVEC_CASES = {
     "sphere_p1_m1_q10_r17": (G.sphere, 1, 1, 2.0, 10, 17),
     "sphere_p1_m1_q11_r9": (G.sphere, 1, 1, 2.0, 11, 9),
     "sphere_p1_m1_q12_r2": (G.sphere, 1, 1, 2.0, 12, 2),
+    # p = 3 and p = 4: near-field blocks of 32 x 32 and 50 x 50 in the batched near field
+    "cube_p3_m1_q5_r9": (G.cube, 3, 1, 1.5, 5, 9),
+    "sphere_p4_m1_q4_r5": (G.sphere, 4, 1, 1.0, 4, 5),
 }
 # m2l_batch: 1 CUDA cores, 2 tensor cores (q <= 10)
 MATVEC_PARAMS = [(c, b) for c in MATVEC_CASES for b in (1, 2) if b == 1 or MATVEC_CASES[c][4] <= 10]
