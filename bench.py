@@ -384,6 +384,22 @@ def run_multi(args):
         s.matvec(x[i], out=y1)
         diffs.append(float(torch.linalg.norm(y[i] - y1) / torch.linalg.norm(y1)))
     single_ms = s.last_timings()["total"]
+    fp64 = None
+    if getattr(args, "check_fp64", False):
+        # both mixed products against the FP64 form (coupling matrices evaluated) for the same
+        # two right-hand sides; outside the timed region
+        s64 = Solver(geo, stream=stream.cuda_stream, p=w["p"], level_m=w["level_m"], kappa=w["kappa"], q=w["q"],
+                     eta=w["eta"], precision=0, m2l_store=1)
+        y64 = torch.empty_like(x[0])
+        fp64 = {"tensor_batched": [], "single_fp32": []}
+        for i in (0, R - 1):
+            s64.matvec(x[i], out=y64)
+            s.matvec(x[i], out=y1)
+            n64 = torch.linalg.norm(y64)
+            fp64["tensor_batched"].append(float(torch.linalg.norm(y[i] - y64) / n64))
+            fp64["single_fp32"].append(float(torch.linalg.norm(y1 - y64) / n64))
+        fp64["fp64_matvec_ms"] = s64.last_timings()["total"]
+        s64.close()
     # roofline of the tensor-core M2L (useful complex work; TF32 peak = measured BF16 peak x
     # the nominal TF32/BF16 ratio 1.1/2.25)
     pk = peaks()
@@ -415,7 +431,7 @@ def run_multi(args):
             "dtype": "tf32x3-m2l/f32/f64", "data": "synthetic", "config": MULTI, "ndof": int(N),
             "far_pairs": int(s.nfar), "near_pairs": int(s.nnear), "setup_s": setup_s,
             "matvec_ms_phases": mv, "single_rhs_matvec_ms": single_ms,
-            "tensor_vs_single_rhs_rel_diff": diffs, "roofline": roof, "cpu_baseline": None,
+            "tensor_vs_single_rhs_rel_diff": diffs, "rel_err_vs_fp64": fp64, "roofline": roof, "cpu_baseline": None,
             "cpu_baseline_note": "the FP64 oracle is timed on the default workload only",
             "e2e": {"value": R * 1000.0 / e2e_ms, "unit": "matvec/s", "h2d_bytes_per_step": int(b.nbytes),
                     "d2h_bytes_per_step": int(yh.nbytes)},
@@ -509,6 +525,8 @@ def main():
     ap.add_argument("--only-steps", action="store_true", help="time the steps only (for launch-list profiling)")
     ap.add_argument("--workload", default="solve", choices=["solve", "serving", "multi"])
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--check-fp64", action="store_true",
+                    help="multi workload: also compare two right-hand sides with the FP64 form (slow)")
     ap.add_argument("--m2l-store", type=int, default=0, choices=[0, 1, 2],
                     help="M2L coupling matrices: 0 auto (kept in HBM when they fit), 1 evaluated, 2 kept")
     args = ap.parse_args()
