@@ -97,6 +97,24 @@ def far_dirs(n=64):
     return np.stack([r * np.cos(ph), r * np.sin(ph), z], axis=1)
 
 
+def max_over_ranks(ms, device="cpu"):
+    """Slowest rank's time: every replica runs the same workload, the job is done when the
+    last one is (no data-path collective; this is the only exchange)."""
+    import torch
+    import torch.distributed as dist
+
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world, ms):
+    """Whole-job solves/s of `world` replicas that each finish one solve per `ms`."""
+    return world * 1000.0 / ms
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -227,11 +245,8 @@ def run_gpu(args):
     clocks = clk.stop()
     launches = s.launch_count() - l0
     ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * 1000.0 / ms
+    ms = max_over_ranks(ms, "cuda")
+    value = replica_value(world, ms)
     if args.only_steps:
         if rank == 0:
             print(json.dumps({"metric": "steps only", "value": value, "unit": "solves/s", "ms_per_step": ms,
