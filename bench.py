@@ -502,7 +502,7 @@ def run_serving(args):
 
     torch.cuda.set_device(0)
     reqs = serving_requests(SERVING["requests"])
-    srv = Server(hbm_budget_bytes=64 << 30, max_slots=args.slots)
+    srv = Server(hbm_budget_bytes=int(args.budget_gib) << 30, max_slots=args.slots)
     t0 = time.perf_counter()
     tickets = []
     for r in reqs:
@@ -520,7 +520,7 @@ def run_serving(args):
             "value": nsolve / makespan, "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
             "requests": len(reqs), "requests_converged": ok, "plane_wave_solves": nsolve,
             "makespan_s": makespan, "latency_ms_p50": float(np.percentile(lat, 50)),
-            "latency_ms_p99": float(np.percentile(lat, 99)), "slots": args.slots,
+            "latency_ms_p99": float(np.percentile(lat, 99)), "slots": args.slots, "budget_gib": args.budget_gib,
             "dofs": [int(x[0].ndof) for x in res], "data": "synthetic", "config": SERVING}
     print(json.dumps(line))
     return 0
@@ -540,6 +540,7 @@ def main():
     ap.add_argument("--only-steps", action="store_true", help="time the steps only (for launch-list profiling)")
     ap.add_argument("--workload", default="solve", choices=["solve", "serving", "multi"])
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--budget-gib", type=int, default=192, help="serving: device-memory budget of the admission")
     ap.add_argument("--check-fp64", action="store_true",
                     help="multi workload: also compare two right-hand sides with the FP64 form (slow)")
     ap.add_argument("--m2l-store", type=int, default=0, choices=[0, 1, 2],

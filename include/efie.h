@@ -249,6 +249,13 @@ efie_status efie_server_poll(efie_server *srv, uint64_t ticket, efie_result *res
 /* Waits for every queued and running request, then stops the workers. */
 efie_status efie_server_destroy(efie_server *srv);
 
+/* Failure-detection check of the device-side waits (the mbarrier waits of the tensor-core M2L,
+ * which give up after about 2^31 clock cycles and report EFIE_ETIMEOUT for the product).  Runs
+ * one such wait, limited to `cycles` clocks (1 .. 2^32), on a barrier that nothing completes, so
+ * the expected result is EFIE_ETIMEOUT with the detail in efie_last_error; the context stays
+ * usable.  EFIE_EINVAL for a NULL ctx or cycles out of range.  The paper has no counterpart. */
+efie_status efie_check_device_waits(efie_ctx *ctx, long long cycles);
+
 /* Static description of a status code. */
 const char *efie_status_string(efie_status s);
 /* Detail of the last failed call on ctx (the failing CUDA call and its error string, or the

@@ -70,6 +70,13 @@ efie_status check_options(const efie_options *o) {
 
 extern "C" {
 
+efie_status efie_check_device_waits(efie_ctx *ctx, long long cycles) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c || cycles < 1 || cycles > (1ll << 32)) return EFIE_EINVAL;
+  if (cudaSetDevice(c->device) != cudaSuccess) return EFIE_ECUDA;
+  return dev_wait_selftest(c, cycles);
+}
+
 const char *efie_last_error(const efie_ctx *ctx) {
   const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
   return c ? c->err.c_str() : "";

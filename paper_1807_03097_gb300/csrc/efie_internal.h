@@ -183,6 +183,7 @@ bool m2l_tc_supported(const Ctx *c);
 efie_status m2l_tc_prepare(Ctx *c);
 efie_status launch_m2l_tc(Ctx *c, cudaStream_t st, int F, int ld, const float2 *src, float2 *acc);
 efie_status m2l_tc_check(Ctx *c);
+efie_status dev_wait_selftest(Ctx *c, long long cycles);
 efie_status dev_gmres_batch(Ctx *c, int R, const double2 *const *b, double2 *const *x, int *its, double *res,
                             int *conv);
 

@@ -390,6 +390,26 @@ efie_status launch_m2l_tc(Ctx *c, cudaStream_t st, int F, int ld, const float2 *
   return EFIE_OK;
 }
 
+// One bounded wait on an mbarrier that nothing ever completes (the situation of a stalled
+// pipeline stage): the wait gives up after `cycles` clocks and sets the same error flag as the
+// tensor-core M2L.  The barrier lives in shared memory and is abandoned when the block exits.
+__global__ void k_wait_selftest(long long cycles, int *err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(tc::smem_u32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!tc::mbar_wait(tc::smem_u32(&bar), 0, cycles)) atomicOr(err, 16);
+  }
+}
+
+efie_status dev_wait_selftest(Ctx *c, long long cycles) {
+  EFIE_TRY(m2l_tc_prepare(c));
+  k_wait_selftest<<<1, 32, 0, c->stream>>>(cycles, c->d_tc_err);
+  ++c->launches;
+  EFIE_CUDA(cudaGetLastError());
+  return m2l_tc_check(c);
+}
+
 efie_status m2l_tc_check(Ctx *c) {
   if (!c->d_tc_err) return EFIE_OK;
   int e = 0;

@@ -27,7 +27,7 @@ ABI_SYMBOLS = (
     "efie_default_options", "efie_create", "efie_set_geometry", "efie_setup", "efie_num_dofs",
     "efie_matvec", "efie_rhs_plane_waves", "efie_solve", "efie_solve_plane_waves", "efie_far_field",
     "efie_block_counts", "efie_export_blocks", "efie_export_near_blocks", "efie_matvec_superspace",
-    "efie_last_timings", "efie_launch_count", "efie_destroy", "efie_status_string", "efie_last_error",
+    "efie_last_timings", "efie_launch_count", "efie_destroy", "efie_status_string", "efie_last_error", "efie_check_device_waits",
     "efie_far_field_noalloc",
     "efie_server_create", "efie_server_submit", "efie_server_poll", "efie_server_destroy",
 )
@@ -106,6 +106,7 @@ def load(path: str = LIB_PATH):
         "efie_destroy": (c_int, [P]),
         "efie_status_string": (ctypes.c_char_p, [c_int]),
         "efie_last_error": (ctypes.c_char_p, [P]),
+        "efie_check_device_waits": (c_int, [P, ctypes.c_longlong]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -283,6 +284,12 @@ class Solver:
 
     def launch_count(self):
         return int(self._L.efie_launch_count(self.h))
+
+    def check_device_waits(self, cycles=1 << 20):
+        """Run one bounded device wait that cannot complete; returns the status (expected
+        EFIE_ETIMEOUT = -6) and efie_last_error's detail, without raising."""
+        st = self._L.efie_check_device_waits(self.h, int(cycles))
+        return st, self._L.efie_last_error(self.h).decode()
 
     def last_timings(self):
         out = np.zeros(7)

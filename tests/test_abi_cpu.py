@@ -59,6 +59,11 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     assert lib.efie_destroy(None) == 0
     assert lib.efie_setup(None) == -1
     assert lib.efie_matvec(None, 1, None, None, 0) == -1
+    assert lib.efie_check_device_waits(None, 1000) == -1
+    assert lib.efie_last_error(None) == b""
+    for bad in (dict(m2l_store=3), dict(m2l_batch=3), dict(m2l_batch=2, q=11)):
+        o = efie.options(**bad)
+        assert lib.efie_create(ctypes.byref(h), ctypes.byref(o), None) == -1, bad
 
 
 def test_package_fails_loudly_without_library(tmp_path):

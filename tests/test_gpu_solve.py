@@ -55,6 +55,25 @@ def test_not_converged_reports_last_iterate():
     s.close()
 
 
+def test_device_wait_timeout_is_reported_and_context_stays_usable():
+    """Failure detection of the device-side waits: a bounded wait on a barrier that nothing
+    completes reports EFIE_ETIMEOUT through the same flag as the tensor-core M2L, and the
+    context keeps working (single and batched tensor-core products afterwards)."""
+    from paper_1807_03097_gb300 import Solver
+
+    geo = G.sphere()
+    s = Solver(geo, p=1, level_m=2, kappa=1.0, q=4, eta=1.6, precision=1)
+    rng = np.random.default_rng(40)
+    x = rng.standard_normal((17, s.ndof)) + 1j * rng.standard_normal((17, s.ndof))
+    y0 = s.matvec(x[0])
+    yb0 = s.matvec(x)
+    st, msg = s.check_device_waits(1 << 20)
+    assert st == -6 and "ran out" in msg
+    assert np.array_equal(s.matvec(x[0]), y0)
+    assert np.array_equal(s.matvec(x), yb0)
+    s.close()
+
+
 def test_geometry_errors():
     from paper_1807_03097_gb300 import Solver
     from paper_1807_03097_gb300.efie import EfieError
