@@ -498,6 +498,67 @@ def serving_requests(n, seed=1809):
     return reqs
 
 
+BATCH = {
+    "workload": "batch256_mixed_1e-5",
+    "solves": 256, "seed": 1808,
+    "geometries": "6-patch sphere (radius U[0.5,2]), 6-patch bilinear cube (side 2), 16-patch torus (R=2, r=0.5)",
+    "elements_per_patch": "4x4, 8x8, 16x16 or 32x32", "p": "U{1,2}", "kappa": "U[1,15]", "q": 6, "eta": 1.6,
+    "incident": "one seeded plane wave per solve", "gmres_tol": 1e-5, "gmres_maxit": 1500, "precision": "mixed",
+    "execution": "all 256 submitted at once to the serving loop (independent contexts, 16 slots); the "
+                 "persistent fused launch across solves is not built",
+}
+
+
+def batch_requests(n, seed=1808):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        kind = int(rng.integers(0, 3))
+        if kind == 0:
+            geo = G.sphere(radius=float(rng.uniform(0.5, 2.0)))
+        elif kind == 1:
+            geo = G.cube()
+        else:
+            geo = G.torus()
+        m = int(rng.integers(2, 6))
+        p = int(rng.integers(1, 3))
+        kappa = float(rng.uniform(1.0, 15.0))
+        d, pol = G.plane_waves(1, seed=seed * 1000 + i)
+        reqs.append(dict(t=0.0, geo=geo, dirs=d, pols=pol,
+                         opt=dict(p=p, level_m=m, kappa=kappa, q=6, eta=1.6, precision=1, gmres_tol=1e-5,
+                                  gmres_maxit=1500)))
+    return reqs
+
+
+def run_batch(args):
+    import torch
+    from paper_1807_03097_gb300.efie import Server
+
+    torch.cuda.set_device(0)
+    reqs = batch_requests(BATCH["solves"], BATCH["seed"])
+    clk = ClockSampler(0)
+    clk.start()
+    srv = Server(hbm_budget_bytes=int(args.budget_gib) << 30, max_slots=16)
+    t0 = time.perf_counter()
+    tickets = [srv.submit(r["geo"], r["dirs"], r["pols"], None, **r["opt"]) for r in reqs]
+    res = [srv.wait(t) for t in tickets]
+    makespan = time.perf_counter() - t0
+    srv.close()
+    clocks = clk.stop()
+    lat = np.array([x[0].latency_ms for x in res])
+    its = [int(x[0].iterations) for x in res]
+    ok = sum(1 for x in res if x[0].status == 0)
+    line = {"metric": "batch of independent solves: solves/s (mixed precision, GMRES 1e-5)",
+            "value": len(reqs) / makespan, "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
+            "solves": len(reqs), "converged": ok, "makespan_s": makespan,
+            "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+            "gmres_iterations_median": int(np.median(its)), "gmres_iterations_max": int(max(its)),
+            "total_dofs": int(sum(int(x[0].ndof) for x in res)), "data": "synthetic", "config": BATCH,
+            "clocks": clocks}
+    print(json.dumps(line))
+    return 0
+
+
 def run_serving(args):
     import torch
     from paper_1807_03097_gb300.efie import Server
@@ -540,7 +601,7 @@ def main():
     ap.add_argument("--ref-iterations", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-steps", action="store_true", help="time the steps only (for launch-list profiling)")
-    ap.add_argument("--workload", default="solve", choices=["solve", "serving", "multi"])
+    ap.add_argument("--workload", default="solve", choices=["solve", "serving", "multi", "batch"])
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--budget-gib", type=int, default=192, help="serving: device-memory budget of the admission")
     ap.add_argument("--check-fp64", action="store_true",
@@ -554,6 +615,8 @@ def main():
         return run_serving(args)
     if args.workload == "multi":
         return run_multi(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_gpu(args)
 
 

@@ -203,10 +203,12 @@ efie_status efie_destroy(efie_ctx *ctx);
 
 /* ---------------------------------------------------------------------------------------
  * Serving: a request loop that admits scattering solves of different geometries, sizes and
- * wavenumbers while others run.  Requests wait in a queue; whenever a slot is free, the
- * oldest queued request whose estimated device-memory footprint (near-field blocks, Krylov
- * basis, cluster data) fits the remaining budget is admitted (so small requests may pass a
- * large one that does not fit yet; a request larger than the whole budget runs alone).
+ * wavenumbers while others run.  Requests wait in a queue; whenever a slot is free, among the
+ * 8 oldest queued requests whose estimated device-memory footprint (near-field blocks, Krylov
+ * bases, cluster data) fits the remaining budget, the one with the least estimated work
+ * (directions x DOFs x local basis size x interpolation nodes) is admitted; so small requests
+ * may pass larger ones, the oldest request goes first once 8 admissions have passed it, and a
+ * request larger than the whole budget runs alone.
  * Each admitted request runs the ordinary per-context path (efie_create, set_geometry,
  * setup, solve_plane_waves, far_field) on its own worker thread and CUDA stream, so the
  * work of several requests overlaps on the GPU.  Results do not depend on what else runs:

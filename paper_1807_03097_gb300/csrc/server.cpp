@@ -1,6 +1,7 @@
 // Serving loop of the library (efie_server_*): scattering requests of different geometries,
-// sizes and wavenumbers are admitted into slots as slots and device memory free up, and
-// run concurrently on the GPU, each in its own context and CUDA stream.  Host-side
+// sizes and wavenumbers are admitted into slots as slots and device memory free up (least
+// estimated work first among the 8 oldest that fit), and run concurrently on the GPU, each in
+// its own context and CUDA stream.  Host-side
 // scheduling only; every numerical step is the ordinary per-context path.
 #include <algorithm>
 #include <atomic>
@@ -34,6 +35,8 @@ struct Job {
   std::vector<double> dir, pol, ffdirs;
   double *w_out = nullptr, *e_inf_out = nullptr;  // caller-owned
   size_t footprint = 0;
+  double cost = 0.0;  // relative work estimate, for the admission order
+  int passed = 0;     // admissions that went to a request behind this one
   int64_t ndof = 0;
   // progress
   Clock::time_point t_submit, t_start, t_done;
@@ -114,14 +117,24 @@ void worker(Server *S) {
       std::unique_lock<std::mutex> lk(S->mu);
       for (;;) {
         if (S->stop) return;
-        // admit the oldest queued request whose footprint fits the remaining budget
+        // among the kLookahead oldest queued requests whose footprint fits the remaining
+        // budget, admit the one with the least estimated work; the oldest request goes first
+        // once kLookahead admissions have passed it while it was the oldest
         const size_t left = S->budget > S->in_use ? S->budget - S->in_use : 0;
-        for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
-          if ((*it)->footprint <= left || S->busy == 0) {
-            job = *it;
-            S->queue.erase(it);
-            break;
-          }
+        constexpr int kLookahead = 8;
+        auto fits = [&](const std::shared_ptr<Job> &q) { return q->footprint <= left || S->busy == 0; };
+        auto best = S->queue.end();
+        if (!S->queue.empty() && S->queue.front()->passed >= kLookahead && fits(S->queue.front())) {
+          best = S->queue.begin();
+        } else {
+          int seen = 0;
+          for (auto it = S->queue.begin(); it != S->queue.end() && seen < kLookahead; ++it, ++seen)
+            if (fits(*it) && (best == S->queue.end() || (*it)->cost < (*best)->cost)) best = it;
+        }
+        if (best != S->queue.end()) {
+          if (best != S->queue.begin()) ++S->queue.front()->passed;
+          job = *best;
+          S->queue.erase(best);
         }
         if (job) break;
         S->cv_work.wait(lk);
@@ -193,6 +206,9 @@ efie_status efie_server_submit(efie_server *srv, const efie_request *q, uint64_t
   const int64_t n = int64_t(1) << q->opt.level_m;
   j->ndof = 2 * int64_t(q->n_patches) * (n + q->opt.p - 1) * (n + q->opt.p - 1);
   j->footprint = estimate_footprint(*j);
+  // work ~ directions x DOFs x (basis functions per element) x interpolation nodes
+  j->cost = double(j->nrhs) * double(j->ndof) * double((q->opt.p + 1) * (q->opt.p + 1)) *
+            double((q->opt.q + 1) * (q->opt.q + 1));
   j->t_submit = Clock::now();
   std::lock_guard<std::mutex> lk(S->mu);
   if (S->stop) return EFIE_ESTATE;
