@@ -67,6 +67,9 @@ def _load():
         "orc_area": (c_double, [P]),
         "orc_mie_l2": (None, [P, D, c_double, D]),
         "orc_mie_field": (None, [c_double, c_double, c_int, c_int, D, D]),
+        "orc_dipole_field": (None, [c_double, D, D, c_int, D, D]),
+        "orc_rhs_dipole": (None, [P, D, D, D]),
+        "orc_exterior_field": (None, [P, D, c_int, D, D]),
         "orc_gauss01": (None, [c_int, D, D]),
         "orc_cheb01": (None, [c_int, D]),
     }
@@ -111,6 +114,17 @@ def mie_field(kappa, radius, which, pts):
     pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
     out = np.zeros((pts.shape[0], 3), dtype=np.complex128)
     L.orc_mie_field(kappa, radius, which, pts.shape[0], _d(pts), _d(out.view(np.float64)))
+    return out
+
+
+def dipole_field(kappa, x0, p0, pts):
+    """Hertz dipole DP_{x0,p0} (Sec. 5.2) at points [n][3] -> [n][3] complex."""
+    L = _load()
+    x0 = np.ascontiguousarray(x0, float)
+    p0 = np.ascontiguousarray(p0, float)
+    pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros((pts.shape[0], 3), dtype=np.complex128)
+    L.orc_dipole_field(kappa, _d(x0), _d(p0), pts.shape[0], _d(pts), _d(out.view(np.float64)))
     return out
 
 
@@ -252,6 +266,20 @@ class Problem:
         dirs = np.ascontiguousarray(dirs, float).reshape(-1, 3)
         out = np.zeros((dirs.shape[0], 3), np.complex128)
         self._L.orc_far_field(self.h, _d(coef.view(np.float64)), dirs.shape[0], _d(dirs), _d(out.view(np.float64)))
+        return out
+
+    def rhs_dipole(self, x0, p0):
+        x0 = np.ascontiguousarray(x0, float)
+        p0 = np.ascontiguousarray(p0, float)
+        g = np.zeros(self.ndof, np.complex128)
+        self._L.orc_rhs_dipole(self.h, _d(x0), _d(p0), _d(g.view(np.float64)))
+        return g
+
+    def exterior_field(self, coef, pts):
+        coef = _cz(coef)
+        pts = np.ascontiguousarray(pts, float).reshape(-1, 3)
+        out = np.zeros((pts.shape[0], 3), np.complex128)
+        self._L.orc_exterior_field(self.h, _d(coef.view(np.float64)), pts.shape[0], _d(pts), _d(out.view(np.float64)))
         return out
 
     def div_integral(self, coef):

@@ -1369,6 +1369,100 @@ void orc_far_field(const orc_problem *P, const double *coef, int ndir, const dou
   free(xs);
 }
 
+/* Hertz dipole at x0 with moment p0 (Sec. 5.2, "The Electric Field as a Quantity of
+ * Interest", after Jackson (9.18) without the 1/(4 pi eps0) factor):
+ *   E(x) = e^{i kappa r} ( kappa^2/r (n x p0) x n + (1/r^3 - i kappa/r^2)(3 n (n.p0) - p0) ),
+ * r = |x - x0|, n = (x - x0)/r.  It solves curl curl E - kappa^2 E = 0 away from x0. */
+static void dipole_at(double kappa, const double *x0, const double *p0, const double *x, cplx *E) {
+  double d[3] = {x[0] - x0[0], x[1] - x0[1], x[2] - x0[2]};
+  double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  double n[3] = {d[0] / r, d[1] / r, d[2] / r};
+  double np = n[0] * p0[0] + n[1] * p0[1] + n[2] * p0[2];
+  /* (n x p0) x n = p0 - n (n.p0) */
+  cplx ph = cexp(I * kappa * r);
+  cplx a = kappa * kappa / r, b = 1.0 / (r * r * r) - I * kappa / (r * r);
+  for (int c = 0; c < 3; ++c) E[c] = ph * (a * (p0[c] - n[c] * np) + b * (3.0 * n[c] * np - p0[c]));
+}
+
+void orc_dipole_field(double kappa, const double *x0, const double *p0, int npts, const double *x, double *out) {
+  cplx *o = (cplx *)out;
+  for (int k = 0; k < npts; ++k) dipole_at(kappa, x0, p0, x + 3 * k, o + 3 * k);
+}
+
+/* Right-hand side for the incident field e_i = -DP_{x0,p0}: g = -T^T int e_i . phi, i.e.
+ * +T^T int DP . phi, so that the scattered field outside is the dipole field itself (the
+ * manufactured solution of Sec. 5.2; the dipole sits inside the scatterer). */
+void orc_rhs_dipole(const orc_problem *P, const double *x0, const double *p0, double *g) {
+  int p = P->p, np1 = p + 1, gq = P->greg;
+  double gx[64], gw[64], h2 = 1.0 / ((double)P->n * P->n);
+  orc_gauss01(gq, gx, gw);
+  cplx *gs = calloc(P->nsup, sizeof(cplx));
+  for (int e = 0; e < P->nE; ++e)
+    for (int u = 0; u < gq; ++u)
+      for (int v = 0; v < gq; ++v) {
+        double sig[2] = {gx[u], gx[v]}, X[3], D[2][3];
+        cplx E[3];
+        elem_geo(P, e, sig, X, D[0], D[1]);
+        dipole_at(P->kappa, x0, p0, X, E);
+        for (int alpha = 0; alpha < 2; ++alpha) {
+          cplx ed = E[0] * D[alpha][0] + E[1] * D[alpha][1] + E[2] * D[alpha][2];
+          for (int b = 0; b < np1; ++b)
+            for (int a = 0; a < np1; ++a)
+              gs[((size_t)(e * 2 + alpha) * np1 + b) * np1 + a] +=
+                  gw[u] * gw[v] * h2 * ed * bern(p, a, sig[0]) * bern(p, b, sig[1]);
+        }
+      }
+  apply_Tt(P, gs, (cplx *)g);
+  free(gs);
+}
+
+/* Electric single-layer potential (eq. ESLP) at points off the surface:
+ *   E(x) = int G(x-y) w(y) dsigma_y + kappa^-2 grad_x int G(x-y) div_Gamma w(y) dsigma_y,
+ * G of eq. HelmholtzGreen, grad_x G(x-y) = G(x-y) (i kappa - 1/R) (x-y)/R, R = |x-y|.  On a
+ * patch w dsigma = dF w_hat ds and div_Gamma w dsigma = div w_hat ds (Piola transforms);
+ * tensor Gauss with quad_regular points per element direction (the points are assumed well
+ * separated from the surface).  out [npts][3] complex. */
+void orc_exterior_field(const orc_problem *P, const double *coef, int npts, const double *xp, double *out) {
+  int p = P->p, np1 = p + 1, gq = P->greg;
+  double gx[64], gw[64], h = 1.0 / P->n, h2 = h * h;
+  orc_gauss01(gq, gx, gw);
+  cplx *xs = malloc(sizeof(cplx) * P->nsup);
+  apply_T(P, (const cplx *)coef, xs);
+  cplx *o = (cplx *)out;
+  double k2 = P->kappa * P->kappa;
+  for (int k = 0; k < npts; ++k) {
+    const double *x = xp + 3 * k;
+    cplx Ev[3] = {0, 0, 0}, Ed[3] = {0, 0, 0};
+    for (int e = 0; e < P->nE; ++e)
+      for (int u = 0; u < gq; ++u)
+        for (int v = 0; v < gq; ++v) {
+          double sig[2] = {gx[u], gx[v]}, X[3], D[2][3];
+          elem_geo(P, e, sig, X, D[0], D[1]);
+          double d[3] = {x[0] - X[0], x[1] - X[1], x[2] - X[2]};
+          double R = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+          cplx G = cexp(I * P->kappa * R) / (4.0 * M_PI * R);
+          cplx w[2] = {0, 0}, dv = 0;
+          for (int alpha = 0; alpha < 2; ++alpha)
+            for (int b = 0; b < np1; ++b)
+              for (int a = 0; a < np1; ++a) {
+                cplx c = xs[((size_t)(e * 2 + alpha) * np1 + b) * np1 + a];
+                w[alpha] += c * bern(p, a, sig[0]) * bern(p, b, sig[1]);
+                dv += c * (alpha == 0 ? bern_d(p, a, sig[0]) * bern(p, b, sig[1])
+                                      : bern(p, a, sig[0]) * bern_d(p, b, sig[1]));
+              }
+          /* vector part: h^2 ds weight; divergence part: div in patch coordinates is (1/h)
+           * times the element-local derivative, times h^2 */
+          cplx gv = gw[u] * gw[v] * h2 * G, gd = gw[u] * gw[v] * h * G * (I * P->kappa - 1.0 / R) / R;
+          for (int c = 0; c < 3; ++c) {
+            Ev[c] += gv * (D[0][c] * w[0] + D[1][c] * w[1]);
+            Ed[c] += gd * d[c] * dv;
+          }
+        }
+    for (int c = 0; c < 3; ++c) o[3 * k + c] = Ev[c] + Ed[c] / k2;
+  }
+  free(xs);
+}
+
 /* int_Gamma div_Gamma w dsigma = sum_e int_e div w_hat ds (iota_2 cancels tau). */
 void orc_div_integral(const orc_problem *P, const double *coef, double *out2) {
   int p = P->p, np1 = p + 1, gq = P->greg;

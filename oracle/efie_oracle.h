@@ -86,6 +86,13 @@ int orc_gmres(orc_problem *P, int use_fmm, const double *b, double *x, int resta
 /* far field E_inf(d) = (1/4pi) (d x W) x d for ndir directions: out [ndir][3] complex */
 void orc_far_field(const orc_problem *P, const double *coef, int ndir, const double *dirs,
                    double *out);
+/* Hertz dipole field DP_{x0,p0} (Sec. 5.2) at npts points: out [npts][3] complex */
+void orc_dipole_field(double kappa, const double *x0, const double *p0, int npts, const double *x, double *out);
+/* right-hand side for e_i = -DP_{x0,p0} (scattered field = DP outside; manufactured solution) */
+void orc_rhs_dipole(const orc_problem *P, const double *x0, const double *p0, double *g);
+/* electric single-layer potential (eq. ESLP) of the field with global coefficients coef at
+ * npts points off the surface: out [npts][3] complex */
+void orc_exterior_field(const orc_problem *P, const double *coef, int npts, const double *x, double *out);
 /* integral of the surface divergence of the field with global coefficients coef */
 void orc_div_integral(const orc_problem *P, const double *coef, double *out2);
 /* surface area (integral of tau) */
