@@ -138,9 +138,10 @@ efie_status efie_matvec(efie_ctx *ctx, int nrhs, const double *x, double *y, int
 efie_status efie_rhs_plane_waves(efie_ctx *ctx, int nrhs, const double *dir, const double *pol,
                                  double *g, int ptr_kind);
 
-/* Solves A x = b by restarted GMRES (zero initial guess) for nrhs right-hand sides, one
- * after the other.  Returns EFIE_NOT_CONVERGED (with the last iterate in x) if some
- * right-hand side reached gmres_maxit.  info may be NULL. */
+/* Solves A x = b by restarted GMRES (zero initial guess) for nrhs right-hand sides: one after
+ * the other in the FP64 form; in the mixed form (nrhs > 1) in lockstep, with one batched
+ * product of all unfinished systems per iteration.  Returns EFIE_NOT_CONVERGED (with the last
+ * iterate in x) if some right-hand side reached gmres_maxit.  info may be NULL. */
 efie_status efie_solve(efie_ctx *ctx, int nrhs, const double *b, double *x, int ptr_kind,
                        efie_solve_info *info);
 
@@ -154,6 +155,21 @@ efie_status efie_solve_plane_waves(efie_ctx *ctx, int nrhs, const double *dir, c
  * unit vectors (host), e_inf: [nrhs][ndir][3] complex; w and e_inf in ptr_kind memory. */
 efie_status efie_far_field(efie_ctx *ctx, int nrhs, const double *w, int ndir, const double *dirs,
                            double *e_inf, int ptr_kind);
+
+/* Scattered electric field at points off the surface by the electric single-layer potential
+ * (eq. ESLP): E(x) = int G w dsigma + kappa^-2 grad_x int G div_Gamma w dsigma.  w: [nrhs][ndof]
+ * complex; pts: [npts][3] host array (1 <= npts <= 65535), points well separated from the
+ * surface (tensor Gauss rule of quad_regular points per element direction, not adapted to near
+ * points); e_out: [nrhs][npts][3] complex; w and e_out in ptr_kind memory. */
+efie_status efie_exterior_field(efie_ctx *ctx, int nrhs, const double *w, int npts, const double *pts,
+                                double *e_out, int ptr_kind);
+
+/* Right-hand side of the manufactured solution of Sec. 5.2: incident field e_i = -DP, DP the
+ * Hertz dipole at x0 with moment p0 (x0 inside the scatterer), so that the scattered field
+ * outside is DP itself: g_j = +int_Gamma DP . phi_j dsigma.  x0, p0: [nrhs][3] host arrays;
+ * g [nrhs][ndof] complex in ptr_kind memory. */
+efie_status efie_rhs_dipole(efie_ctx *ctx, int nrhs, const double *x0, const double *p0, double *g,
+                            int ptr_kind);
 
 /* Introspection for verification.
  * efie_block_counts: far blocks, near element pairs, clusters, superspace size.

@@ -627,6 +627,49 @@ efie_status efie_far_field(efie_ctx *ctx, int nrhs, const double *w, int ndir, c
   return EFIE_OK;
 }
 
+efie_status efie_exterior_field(efie_ctx *ctx, int nrhs, const double *w, int npts, const double *pts,
+                                double *e_out, int ptr_kind) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c || nrhs < 0 || npts < 0 || npts > 65535 || (nrhs > 0 && npts > 0 && (!w || !pts || !e_out)))
+    return EFIE_EINVAL;
+  if (ptr_kind != EFIE_PTR_HOST && ptr_kind != EFIE_PTR_DEVICE) return EFIE_EINVAL;
+  if (!c->setup_done) return EFIE_ESTATE;
+  if (npts == 0 || nrhs == 0) return EFIE_OK;
+  cudaSetDevice(c->device);
+  const size_t N = c->ndof;
+  double2 *d_out = nullptr;
+  EFIE_TRY(dalloc(c, &d_out, 3 * (size_t)npts));
+  for (int r = 0; r < nrhs; ++r) {
+    const double2 *wr = reinterpret_cast<const double2 *>(w) + r * N;
+    double2 *er = reinterpret_cast<double2 *>(e_out) + (size_t)r * npts * 3;
+    const double2 *src = wr;
+    if (ptr_kind == EFIE_PTR_HOST) {
+      EFIE_CUDA(cudaMemcpyAsync(c->d_x, wr, 16 * N, cudaMemcpyHostToDevice, c->stream));
+      src = c->d_x;
+    }
+    EFIE_TRY(dev_exterior_field(c, src, npts, pts, ptr_kind == EFIE_PTR_HOST ? d_out : er));
+    if (ptr_kind == EFIE_PTR_HOST) EFIE_CUDA(cudaMemcpy(er, d_out, 48 * (size_t)npts, cudaMemcpyDeviceToHost));
+  }
+  cudaFree(d_out);
+  return EFIE_OK;
+}
+
+efie_status efie_rhs_dipole(efie_ctx *ctx, int nrhs, const double *x0, const double *p0, double *g, int ptr_kind) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c || nrhs < 0 || (nrhs > 0 && (!x0 || !p0 || !g))) return EFIE_EINVAL;
+  if (ptr_kind != EFIE_PTR_HOST && ptr_kind != EFIE_PTR_DEVICE) return EFIE_EINVAL;
+  if (!c->setup_done) return EFIE_ESTATE;
+  cudaSetDevice(c->device);
+  const size_t N = c->ndof;
+  for (int r = 0; r < nrhs; ++r) {
+    double2 *gr = reinterpret_cast<double2 *>(g) + r * N;
+    double2 *dst = ptr_kind == EFIE_PTR_HOST ? c->d_y : gr;
+    EFIE_TRY(dev_rhs_dipole(c, x0 + 3 * r, p0 + 3 * r, dst));
+    if (ptr_kind == EFIE_PTR_HOST) EFIE_CUDA(cudaMemcpy(gr, c->d_y, 16 * N, cudaMemcpyDeviceToHost));
+  }
+  return EFIE_OK;
+}
+
 int64_t efie_launch_count(const efie_ctx *ctx) {
   const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
   return c ? (int64_t)c->launches : -1;

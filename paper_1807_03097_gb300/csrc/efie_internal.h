@@ -184,6 +184,9 @@ efie_status m2l_tc_prepare(Ctx *c);
 efie_status launch_m2l_tc(Ctx *c, cudaStream_t st, int F, int ld, const float2 *src, float2 *acc);
 efie_status m2l_tc_check(Ctx *c);
 efie_status dev_wait_selftest(Ctx *c, long long cycles);
+// exterior field and the dipole right-hand side (exterior.cu)
+efie_status dev_exterior_field(Ctx *c, const double2 *w, int npts, const double *pts, double2 *out);
+efie_status dev_rhs_dipole(Ctx *c, const double *x0, const double *p0, double2 *g);
 efie_status dev_gmres_batch(Ctx *c, int R, const double2 *const *b, double2 *const *x, int *its, double *res,
                             int *conv);
 

@@ -27,7 +27,8 @@ ABI_SYMBOLS = (
     "efie_default_options", "efie_create", "efie_set_geometry", "efie_setup", "efie_num_dofs",
     "efie_matvec", "efie_rhs_plane_waves", "efie_solve", "efie_solve_plane_waves", "efie_far_field",
     "efie_block_counts", "efie_export_blocks", "efie_export_near_blocks", "efie_matvec_superspace",
-    "efie_last_timings", "efie_launch_count", "efie_destroy", "efie_status_string", "efie_last_error", "efie_check_device_waits",
+    "efie_last_timings", "efie_launch_count", "efie_destroy", "efie_status_string", "efie_last_error", "efie_check_device_waits", "efie_exterior_field",
+    "efie_rhs_dipole",
     "efie_far_field_noalloc",
     "efie_server_create", "efie_server_submit", "efie_server_poll", "efie_server_destroy",
 )
@@ -107,6 +108,8 @@ def load(path: str = LIB_PATH):
         "efie_status_string": (ctypes.c_char_p, [c_int]),
         "efie_last_error": (ctypes.c_char_p, [P]),
         "efie_check_device_waits": (c_int, [P, ctypes.c_longlong]),
+        "efie_exterior_field": (c_int, [P, c_int, P, c_int, P, P, c_int]),
+        "efie_rhs_dipole": (c_int, [P, c_int, P, P, P, c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -257,6 +260,29 @@ class Solver:
         pw, kw = _ptr(w)
         po, _ = _ptr(out)
         self._check(self._L.efie_far_field(self.h, nrhs, pw, dirs.shape[0], _d(dirs), po, kw), "efie_far_field")
+        return out
+
+    def exterior_field(self, w, pts, out=None):
+        """Scattered field (eq. ESLP) at points [npts][3] well away from the surface."""
+        pts = np.ascontiguousarray(pts, float).reshape(-1, 3)
+        nrhs = 1 if w.ndim == 1 else w.shape[0]
+        if out is None:
+            out = np.zeros((nrhs, pts.shape[0], 3), np.complex128) if isinstance(w, np.ndarray) else \
+                w.new_zeros((nrhs, pts.shape[0], 3))
+        pw, kw = _ptr(w)
+        po, _ = _ptr(out)
+        self._check(self._L.efie_exterior_field(self.h, nrhs, pw, pts.shape[0], _d(pts), po, kw),
+                    "efie_exterior_field")
+        return out
+
+    def rhs_dipole(self, x0, p0, out=None):
+        """Right-hand side for the incident field -DP_{x0,p0} (scattered field = the dipole)."""
+        x0 = np.ascontiguousarray(x0, float).reshape(-1, 3)
+        p0 = np.ascontiguousarray(p0, float).reshape(-1, 3)
+        if out is None:
+            out = np.zeros((x0.shape[0], self.ndof), np.complex128)
+        po, k = _ptr(out)
+        self._check(self._L.efie_rhs_dipole(self.h, x0.shape[0], _d(x0), _d(p0), po, k), "efie_rhs_dipole")
         return out
 
     def far_field_noalloc(self, w, dirs, out):
