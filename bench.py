@@ -184,7 +184,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC,
             "value": val, "unit": "solves/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 / val, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic", "config": WORKLOAD,
+            "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, precision=args.precision, parallelism="single"),
             "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": det["sample"]},
             "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "details": det}
