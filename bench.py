@@ -129,44 +129,54 @@ def dist_env():
 
 # ---------------------------------------------------------------------------- CPU oracle
 def oracle_sample(seconds_hint=15.0, its=None):
-    """Oracle cost of one solve of the workload, from a bounded sample: FMM rows of a few
-    elements (near blocks integrated on demand + far field) timed at two sample sizes, which
-    separates the per-element cost from the global moment cost; near-block integration of
-    the sampled pairs timed on its own.  Returns (solves/s, details)."""
+    """Oracle cost of one solve of the workload (serial, one core), from a bounded sample:
+    * setup = problem creation + (near pairs) x (time of one near block, timed on the near
+      pairs of 3 sampled elements);
+    * product = direct moments (timed) + (far blocks) x (time of one far block), the latter
+      timed on the far-field part of 48 sampled rows: a far pair whose target cluster is on
+      level l is applied once for each of the 4^(m-l) elements under it, which gives the
+      number of far blocks the sampled rows process on average;
+    the near-field apply with the stored blocks (< 0.5 % of the product) is not counted.
+    Returns (solves/s, details)."""
     import oracle as O
 
     geo = G.sphere()
     w = WORKLOAD
-    t0 = time.time()
+    t0 = time.perf_counter()
     r = O.Problem(geo, p=w["p"], m=w["level_m"], kappa=w["kappa"], q=w["q"], eta=w["eta"])
-    t_create = time.time() - t0
+    t_create = time.perf_counter() - t0
     rng = np.random.default_rng(5)
     xs = rng.standard_normal(r.nsup) + 1j * rng.standard_normal(r.nsup)
-    near = r.near_pairs()
     nE = r.nE
     e_all = rng.permutation(nE)
-    n1, n2 = 2, 6
-    t = time.time()
-    r.fmm_rows(xs, e_all[:n1])
-    t1 = time.time() - t
-    t = time.time()
-    r.fmm_rows(xs, e_all[n1:n1 + n2])
-    t2 = time.time() - t
-    per_row = max(t2 - t1, 1e-9) / (n2 - n1)
-    fixed = max(t1 - n1 * per_row, 0.0)
-    # near-block integration (setup) share of a row
-    sel = [k for k, (a, _) in enumerate(near) if a in set(e_all[:3].tolist())]
-    t = time.time()
+    t = time.perf_counter()
+    r.fmm_rows_far(xs, e_all[:0])
+    t_mom = time.perf_counter() - t
+    nrow = 48
+    t = time.perf_counter()
+    r.fmm_rows_far(xs, e_all[:nrow])
+    t_rows = max(time.perf_counter() - t - t_mom, 1e-9)
+    far = np.asarray(r.far_pairs())
+    m = w["level_m"]
+    blocks_per_row = float(np.sum(4.0 ** (m - far[:, 0]))) / nE
+    t_block = t_rows / (nrow * blocks_per_row)
+    apply_ = t_mom + len(far) * t_block
+    near = r.near_pairs()
+    pick = set(e_all[:3].tolist())
+    sel = [k for k, (a, _) in enumerate(near) if a in pick]
+    t = time.perf_counter()
     for k in sel:
         r.pair_block(int(near[k][0]), int(near[k][1]))
-    t_quad_row = (time.time() - t) / 3
-    setup = t_create + nE * t_quad_row
-    apply_ = fixed + nE * max(per_row - t_quad_row, 0.0)
+    t_pair = (time.perf_counter() - t) / max(len(sel), 1)
+    setup = t_create + len(near) * t_pair
     its = its or 1
     solve = setup + its * apply_
     return 1.0 / solve, {"oracle_setup_s_est": setup, "oracle_matvec_s_est": apply_, "iterations": its,
-                         "sample": f"oracle FMM rows of {n1}+{n2} of {nE} elements and near blocks of 3 elements, "
-                                   f"scaled to the full operator; solve = setup + {its} x matvec"}
+                         "far_block_us": t_block * 1e6, "near_block_ms": t_pair * 1e3,
+                         "sample": f"oracle far field of {nrow} of {nE} element rows (far blocks per row from the "
+                                   f"block tree), direct moments, and near blocks of {len(sel)} pairs; scaled to "
+                                   f"{len(far)} far blocks and {len(near)} near pairs; solve = setup + {its} x "
+                                   f"product; serial, one core"}
 
 
 def run_reference(args):

@@ -60,6 +60,7 @@ def _load():
         "orc_fmm_matvec": (None, [P, c_int, D, D]),
         "orc_fmm_matvec_superspace": (None, [P, D, D]),
         "orc_fmm_rows": (None, [P, D, c_int, I, D]),
+        "orc_fmm_rows_far": (None, [P, D, c_int, I, D]),
         "orc_rhs": (None, [P, D, D, D]),
         "orc_gmres": (c_int, [P, c_int, D, D, c_int, c_double, c_int, I, D]),
         "orc_far_field": (None, [P, D, c_int, D, D]),
@@ -243,6 +244,14 @@ class Problem:
         elems = np.ascontiguousarray(elems, np.int32)
         out = np.zeros((len(elems), self.nb), np.complex128)
         self._L.orc_fmm_rows(self.h, _d(xs.view(np.float64)), len(elems), _i(elems), _d(out.view(np.float64)))
+        return out
+
+    def fmm_rows_far(self, xs, elems):
+        """Far-field part of fmm_rows (no near blocks)."""
+        xs = _cz(xs).reshape(self.nsup)
+        elems = np.ascontiguousarray(elems, np.int32)
+        out = np.zeros((len(elems), self.nb), np.complex128)
+        self._L.orc_fmm_rows_far(self.h, _d(xs.view(np.float64)), len(elems), _i(elems), _d(out.view(np.float64)))
         return out
 
     def rhs(self, d, pol):

@@ -1124,9 +1124,10 @@ static void fmm_superspace(orc_problem *P, const cplx *xs, cplx *ys) {
   free(loc);
 }
 
-/* rows of y* = (N + F) x* for selected elements only: near blocks integrated on demand,
- * far field restricted to the blocks whose target cluster contains the element */
-void orc_fmm_rows(orc_problem *P, const double *xsd, int nrows, const int *elems, double *out) {
+/* rows of y* = (N + F) x* for selected elements only: near blocks integrated on demand
+ * (with_near = 1, else the near part is left out), far field restricted to the blocks whose
+ * target cluster contains the element */
+static void fmm_rows(orc_problem *P, const double *xsd, int nrows, const int *elems, double *out, int with_near) {
   const cplx *xs = (const cplx *)xsd;
   int nb = nb_of(P), nI = P->nI;
   cplx *o = (cplx *)out;
@@ -1138,7 +1139,7 @@ void orc_fmm_rows(orc_problem *P, const double *xsd, int nrows, const int *elems
     int e = elems[r];
     cplx *ye = o + (size_t)r * nb;
     for (int i = 0; i < nb; ++i) ye[i] = 0;
-    for (int k = 0; k < P->nnear; ++k) {
+    for (int k = 0; with_near && k < P->nnear; ++k) {
       if (P->near[2 * k] != e) continue;
       int e2 = P->near[2 * k + 1];
       pair_block(P, e, e2, P->greg, P->gsing, blk);
@@ -1161,6 +1162,14 @@ void orc_fmm_rows(orc_problem *P, const double *xsd, int nrows, const int *elems
   free(blk);
   free(mom);
   free(loc);
+}
+
+void orc_fmm_rows(orc_problem *P, const double *xs, int nrows, const int *elems, double *out) {
+  fmm_rows(P, xs, nrows, elems, out, 1);
+}
+
+void orc_fmm_rows_far(orc_problem *P, const double *xs, int nrows, const int *elems, double *out) {
+  fmm_rows(P, xs, nrows, elems, out, 0);
 }
 
 void orc_fmm_matvec_superspace(orc_problem *P, const double *xs, double *ys) {

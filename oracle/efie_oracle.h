@@ -76,6 +76,8 @@ void orc_fmm_matvec_superspace(orc_problem *P, const double *xs, double *ys);
 /* the rows of y* = (N + F) x* belonging to the listed elements, out [nrows][2(p+1)^2]
  * (near blocks integrated on demand; for sampled checks and timing at large sizes) */
 void orc_fmm_rows(orc_problem *P, const double *xs, int nrows, const int *elems, double *out);
+/* the far-field part of those rows only (no near blocks): for timing the far field */
+void orc_fmm_rows_far(orc_problem *P, const double *xs, int nrows, const int *elems, double *out);
 
 /* right-hand side g = -T^T int e_i . phi for e_i = pol exp(i kappa d.x) */
 void orc_rhs(const orc_problem *P, const double *dir, const double *pol, double *g);
