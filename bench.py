@@ -14,6 +14,15 @@ phase-split M2L, FP64 near field, geometry and GMRES) is the timed form; its
 matrix-vector product is checked against the FP64 form in the same run.
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+
+Other workloads (--workload):
+  multi    64 plane waves on the torus (16 patches, p = 3, 64x64 elements per patch, 139 392
+           DOFs, kappa = 20, q = 10): matvec/s of the batched product on the tensor cores
+           (--check-fp64 adds the error of two right-hand sides against the FP64 form);
+  serving  32 Poisson-arriving scattering requests through the serving loop: solves/s and
+           p50/p99 latency;
+  batch    256 independent solves of a seeded mix of spheres, cubes and tori through the
+           serving loop: solves/s.
 """
 from __future__ import annotations
 
