@@ -60,6 +60,17 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     assert lib.efie_setup(None) == -1
     assert lib.efie_matvec(None, 1, None, None, 0) == -1
     assert lib.efie_check_device_waits(None, 1000) == -1
+    assert lib.efie_exterior_field(None, 1, None, 1, None, None, 0) == -1
+    assert lib.efie_rhs_dipole(None, 1, None, None, None, 0) == -1
+    assert lib.efie_far_field_noalloc(None, None, 1, None, None) == -1
+    assert lib.efie_solve(None, 1, None, None, 0, None) == -1
+    assert lib.efie_solve_plane_waves(None, 1, None, None, None, 0, None) == -1
+    assert lib.efie_rhs_plane_waves(None, 1, None, None, None, 0) == -1
+    assert lib.efie_far_field(None, 1, None, 1, None, None, 0) == -1
+    assert lib.efie_server_submit(None, None, None) == -1
+    assert lib.efie_server_poll(None, 0, None) == -1
+    assert lib.efie_server_destroy(None) == 0
+    assert lib.efie_launch_count(None) == -1
     assert lib.efie_last_error(None) == b""
     for bad in (dict(m2l_store=3), dict(m2l_batch=3), dict(m2l_batch=2, q=11)):
         o = efie.options(**bad)
