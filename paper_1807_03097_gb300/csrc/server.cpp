@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/efie.h"
+#include "admission.h"
 
 namespace {
 
@@ -122,19 +123,19 @@ void worker(Server *S) {
         // once kLookahead admissions have passed it while it was the oldest
         const size_t left = S->budget > S->in_use ? S->budget - S->in_use : 0;
         constexpr int kLookahead = 8;
-        auto fits = [&](const std::shared_ptr<Job> &q) { return q->footprint <= left || S->busy == 0; };
-        auto best = S->queue.end();
-        if (!S->queue.empty() && S->queue.front()->passed >= kLookahead && fits(S->queue.front())) {
-          best = S->queue.begin();
-        } else {
-          int seen = 0;
-          for (auto it = S->queue.begin(); it != S->queue.end() && seen < kLookahead; ++it, ++seen)
-            if (fits(*it) && (best == S->queue.end() || (*it)->cost < (*best)->cost)) best = it;
+        size_t fp[kLookahead];
+        double cost[kLookahead];
+        const int nq = (int)std::min<size_t>(S->queue.size(), kLookahead);
+        for (int i = 0; i < nq; ++i) {
+          fp[i] = S->queue[i]->footprint;
+          cost[i] = S->queue[i]->cost;
         }
-        if (best != S->queue.end()) {
-          if (best != S->queue.begin()) ++S->queue.front()->passed;
-          job = *best;
-          S->queue.erase(best);
+        const int pick = efie::pick_admission(nq, fp, cost, nq ? S->queue.front()->passed : 0, left, S->busy == 0,
+                                              kLookahead);
+        if (pick >= 0) {
+          if (pick > 0) ++S->queue.front()->passed;
+          job = S->queue[pick];
+          S->queue.erase(S->queue.begin() + pick);
         }
         if (job) break;
         S->cv_work.wait(lk);

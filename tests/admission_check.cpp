@@ -1,0 +1,81 @@
+// Host-only checks of the serving loop's admission decision (compiled and run by
+// test_admission_cpu.py with the system C++ compiler).
+#include <cstdio>
+#include <deque>
+#include <vector>
+
+#include "../paper_1807_03097_gb300/csrc/admission.h"
+
+static int failures = 0;
+#define CHECK(cond)                                           \
+  do {                                                        \
+    if (!(cond)) {                                            \
+      std::printf("FAILED line %d: %s\n", __LINE__, #cond);   \
+      ++failures;                                             \
+    }                                                         \
+  } while (0)
+
+int main() {
+  using efie::pick_admission;
+  {
+    CHECK(pick_admission(0, nullptr, nullptr, 0, 100, false, 8) == -1);
+  }
+  {  // least work among those that fit
+    size_t fp[3] = {10, 10, 10};
+    double c[3] = {5, 3, 9};
+    CHECK(pick_admission(3, fp, c, 0, 50, false, 8) == 1);
+  }
+  {  // only the oldest fits the budget
+    size_t fp[2] = {10, 100};
+    double c[2] = {9, 1};
+    CHECK(pick_admission(2, fp, c, 0, 50, false, 8) == 0);
+  }
+  {  // nothing fits: only when nothing runs may a request exceed the budget
+    size_t fp[3] = {100, 200, 300};
+    double c[3] = {5, 3, 9};
+    CHECK(pick_admission(3, fp, c, 0, 50, false, 8) == -1);
+    CHECK(pick_admission(3, fp, c, 0, 50, true, 8) == 1);
+  }
+  {  // the window: requests behind the 8 oldest are not considered
+    size_t fp[10];
+    double c[10];
+    for (int i = 0; i < 10; ++i) {
+      fp[i] = 1;
+      c[i] = 10.0 - i;  // cheapest at index 9
+    }
+    CHECK(pick_admission(10, fp, c, 0, 50, false, 8) == 7);
+  }
+  {  // the oldest goes first after 8 passes, if it fits
+    size_t fp[3] = {10, 10, 10};
+    double c[3] = {9, 1, 2};
+    CHECK(pick_admission(3, fp, c, 8, 50, false, 8) == 0);
+    CHECK(pick_admission(3, fp, c, 7, 50, false, 8) == 1);
+    size_t fp2[3] = {100, 10, 10};
+    CHECK(pick_admission(3, fp2, c, 8, 50, false, 8) == 1);
+  }
+  {  // a large request at the head of a stream of small ones is passed exactly 8 times
+    std::deque<std::pair<size_t, double>> q;
+    q.push_back({10, 1000.0});
+    for (int i = 0; i < 30; ++i) q.push_back({10, 1.0 + 0.01 * i});
+    int passed = 0, admitted_before = 0;
+    for (;;) {
+      size_t fp[8];
+      double c[8];
+      const int n = (int)std::min<size_t>(q.size(), 8);
+      for (int i = 0; i < n; ++i) {
+        fp[i] = q[i].first;
+        c[i] = q[i].second;
+      }
+      const int k = pick_admission(n, fp, c, passed, 50, false, 8);
+      CHECK(k >= 0);
+      if (k < 0) break;
+      if (k == 0) break;  // the large request
+      ++passed;
+      ++admitted_before;
+      q.erase(q.begin() + k);
+    }
+    CHECK(admitted_before == 8);
+  }
+  if (failures == 0) std::printf("ok\n");
+  return failures == 0 ? 0 : 1;
+}
