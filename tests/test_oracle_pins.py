@@ -366,3 +366,22 @@ def test_dipole_error_rate_matches_table1(exterior_runs):
     assert abs(rate / tab_rate - 1) < 0.25, (rate, tab_rate)
     for m, t in ((1, t1), (2, t2)):
         assert t / 10 < e[m] < t, (m, e[m], t)
+
+
+def test_far_only_rows_plus_near_blocks_give_the_rows():
+    """orc_fmm_rows_far (used to time the far field) is the far-field part of orc_fmm_rows:
+    the difference of the two is the near blocks applied to the source coefficients."""
+    r = O.Problem(G.sphere(), p=1, m=1, kappa=2.0, q=4, eta=1.6)
+    rng = np.random.default_rng(60)
+    xs = rng.standard_normal(r.nsup) + 1j * rng.standard_normal(r.nsup)
+    elems = np.array([0, 5, 17, r.nE - 1])
+    full, far = r.fmm_rows(xs, elems), r.fmm_rows_far(xs, elems)
+    near = r.near_pairs()
+    nb = r.nb
+    X = xs.reshape(r.nE, nb)
+    for i, e in enumerate(elems):
+        ref = np.zeros(nb, complex)
+        for a, b in near:
+            if a == e:
+                ref += r.pair_block(int(a), int(b)) @ X[b]
+        assert np.abs(full[i] - far[i] - ref).max() < 1e-12 * np.abs(full[i]).max()
