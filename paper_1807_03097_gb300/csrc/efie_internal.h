@@ -221,6 +221,31 @@ inline efie_status dalloc(Ctx *c, T **p, size_t count) {
   return EFIE_OK;
 }
 
+// Temporary device buffers of one call, freed when the owner goes out of scope (also on the
+// early returns of EFIE_TRY / EFIE_CUDA).  cudaFree waits for work in flight on the device.
+struct DevTemp {
+  std::vector<void *> p;
+  DevTemp() = default;
+  DevTemp(const DevTemp &) = delete;
+  DevTemp &operator=(const DevTemp &) = delete;
+  ~DevTemp() {
+    for (void *q : p) cudaFree(q);
+  }
+  template <class T>
+  efie_status get(Ctx *c, T **out, size_t n) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, (n ? n : 1) * sizeof(T));
+    if (e != cudaSuccess) {
+      c->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+      *out = nullptr;
+      return EFIE_ENOMEM;
+    }
+    p.push_back(q);
+    *out = static_cast<T *>(q);
+    return EFIE_OK;
+  }
+};
+
 inline int morton2(int i1, int i2) {
   int k = 0;
   for (int b = 0; b < 15; ++b) k |= (((i1 >> b) & 1) << (2 * b)) | (((i2 >> b) & 1) << (2 * b + 1));

@@ -184,12 +184,12 @@ __global__ void k_ext_final(int nE, const double2 *part, double2 *out) {
     for (int k = 0; k < 3; ++k) out[3 * pt + k] = red[0][k];
 }
 
-static efie_status upload_rule(Ctx *c, double **d_rule) {
+static efie_status upload_rule(Ctx *c, DevTemp &tmp, double **d_rule) {
   if (c->gr * c->gr > 256) {
     c->err = "quad_regular must be <= 16";
     return EFIE_EINVAL;
   }
-  EFIE_TRY(dalloc(c, d_rule, 2 * (size_t)c->gr));
+  EFIE_TRY(tmp.get(c, d_rule, 2 * (size_t)c->gr));
   EFIE_CUDA(cudaMemcpyAsync(*d_rule, c->tab.gx.data(), 8 * (size_t)c->gr, cudaMemcpyHostToDevice, c->stream));
   EFIE_CUDA(cudaMemcpyAsync(*d_rule + c->gr, c->tab.gw.data(), 8 * (size_t)c->gr, cudaMemcpyHostToDevice, c->stream));
   return EFIE_OK;
@@ -197,9 +197,10 @@ static efie_status upload_rule(Ctx *c, double **d_rule) {
 
 // g (device, ndof) for the incident field -DP_{x0,p0}; x0, p0 host arrays of 3
 efie_status dev_rhs_dipole(Ctx *c, const double *x0, const double *p0, double2 *g) {
+  DevTemp tmp;
   double *d_rule = nullptr, *d_xp = nullptr;
-  EFIE_TRY(upload_rule(c, &d_rule));
-  EFIE_TRY(dalloc(c, &d_xp, 6));
+  EFIE_TRY(upload_rule(c, tmp, &d_rule));
+  EFIE_TRY(tmp.get(c, &d_xp, 6));
   double xp[6] = {x0[0], x0[1], x0[2], p0[0], p0[1], p0[2]};
   EFIE_CUDA(cudaMemcpyAsync(d_xp, xp, sizeof(xp), cudaMemcpyHostToDevice, c->stream));
   k_rhs_dipole<<<c->nE, 256, 0, c->stream>>>(c->d_patches, c->d_knots, c->d_cpw, c->n, c->p, c->gr, d_rule,
@@ -207,18 +208,17 @@ efie_status dev_rhs_dipole(Ctx *c, const double *x0, const double *p0, double2 *
   EFIE_CUDA(cudaGetLastError());
   EFIE_TRY(dev_scatter(c, c->d_ys, g));
   EFIE_CUDA(cudaStreamSynchronize(c->stream));
-  cudaFree(d_rule);
-  cudaFree(d_xp);
   return EFIE_OK;
 }
 
 // out (device, [npts][3] complex) = eq. ESLP of the DOF vector w (device) at pts (host)
 efie_status dev_exterior_field(Ctx *c, const double2 *w, int npts, const double *pts, double2 *out) {
+  DevTemp tmp;
   double *d_rule = nullptr, *d_pts = nullptr;
   double2 *d_part = nullptr;
-  EFIE_TRY(upload_rule(c, &d_rule));
-  EFIE_TRY(dalloc(c, &d_pts, 3 * (size_t)npts));
-  EFIE_TRY(dalloc(c, &d_part, 3 * (size_t)npts * c->nE));
+  EFIE_TRY(upload_rule(c, tmp, &d_rule));
+  EFIE_TRY(tmp.get(c, &d_pts, 3 * (size_t)npts));
+  EFIE_TRY(tmp.get(c, &d_part, 3 * (size_t)npts * c->nE));
   EFIE_CUDA(cudaMemcpyAsync(d_pts, pts, 24 * (size_t)npts, cudaMemcpyHostToDevice, c->stream));
   EFIE_TRY(dev_gather(c, w, c->d_xs));
   dim3 grid(c->nE, npts);
@@ -227,9 +227,6 @@ efie_status dev_exterior_field(Ctx *c, const double2 *w, int npts, const double 
   k_ext_final<<<npts, 256, 0, c->stream>>>(c->nE, d_part, out); ++c->launches;
   EFIE_CUDA(cudaGetLastError());
   EFIE_CUDA(cudaStreamSynchronize(c->stream));
-  cudaFree(d_rule);
-  cudaFree(d_pts);
-  cudaFree(d_part);
   return EFIE_OK;
 }
 

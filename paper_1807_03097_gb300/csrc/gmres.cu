@@ -341,24 +341,6 @@ struct GSys {
   bool r_ready = false;  // r holds b (first cycle) or b - A x (after a failed check)
 };
 
-struct DevBlock {
-  std::vector<void *> p;
-  ~DevBlock() {
-    for (void *q : p) cudaFree(q);
-  }
-  template <class T>
-  efie_status get(Ctx *c, T **out, size_t n) {
-    void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
-    if (e != cudaSuccess) {
-      c->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
-      return EFIE_ENOMEM;
-    }
-    p.push_back(q);
-    *out = static_cast<T *>(q);
-    return EFIE_OK;
-  }
-};
 }  // namespace
 
 size_t gmres_batch_bytes_per_system(const Ctx *c) {
@@ -373,7 +355,7 @@ efie_status dev_gmres_batch(Ctx *c, int R, const double2 *const *b, double2 *con
   const int maxit = c->opt.gmres_maxit;
   cudaStream_t st = c->stream;
   const int blk = 256, grid = (N + blk - 1) / blk;
-  DevBlock mem;
+  DevTemp mem;
   std::vector<GSys> S(R);
   for (int i = 0; i < R; ++i) {
     GSys &s = S[i];

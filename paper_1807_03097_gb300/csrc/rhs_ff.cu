@@ -76,8 +76,9 @@ efie_status dev_rhs(Ctx *c, const double *dir, const double *pol, double2 *g) {
     c->err = "quad_regular must be <= 16";
     return EFIE_EINVAL;
   }
+  DevTemp tmp;
   double *d_rule = nullptr;
-  EFIE_TRY(dalloc(c, &d_rule, 2 * (size_t)c->gr));
+  EFIE_TRY(tmp.get(c, &d_rule, 2 * (size_t)c->gr));
   EFIE_CUDA(cudaMemcpyAsync(d_rule, c->tab.gx.data(), 8 * (size_t)c->gr, cudaMemcpyHostToDevice, c->stream));
   EFIE_CUDA(cudaMemcpyAsync(d_rule + c->gr, c->tab.gw.data(), 8 * (size_t)c->gr, cudaMemcpyHostToDevice, c->stream));
   k_rhs<<<c->nE, 256, 0, c->stream>>>(c->d_patches, c->d_knots, c->d_cpw, c->n, c->p, c->gr, d_rule, d_rule + c->gr,
@@ -85,7 +86,6 @@ efie_status dev_rhs(Ctx *c, const double *dir, const double *pol, double2 *g) {
   EFIE_CUDA(cudaGetLastError());
   EFIE_TRY(dev_scatter(c, c->d_ys, g));
   EFIE_CUDA(cudaStreamSynchronize(c->stream));
-  cudaFree(d_rule);
   return EFIE_OK;
 }
 
@@ -176,11 +176,12 @@ efie_status dev_far_field(Ctx *c, const double2 *w, int ndir, const double *dirs
     c->err = "quad_regular must be <= 16";
     return EFIE_EINVAL;
   }
+  DevTemp tmp;
   double *d_rule = nullptr, *d_dirs = nullptr;
   double2 *d_part = nullptr;
-  EFIE_TRY(dalloc(c, &d_rule, 2 * (size_t)c->gr));
-  EFIE_TRY(dalloc(c, &d_dirs, 3 * (size_t)ndir));
-  EFIE_TRY(dalloc(c, &d_part, 3 * (size_t)ndir * c->nE));
+  EFIE_TRY(tmp.get(c, &d_rule, 2 * (size_t)c->gr));
+  EFIE_TRY(tmp.get(c, &d_dirs, 3 * (size_t)ndir));
+  EFIE_TRY(tmp.get(c, &d_part, 3 * (size_t)ndir * c->nE));
   EFIE_CUDA(cudaMemcpyAsync(d_rule, c->tab.gx.data(), 8 * (size_t)c->gr, cudaMemcpyHostToDevice, c->stream));
   EFIE_CUDA(cudaMemcpyAsync(d_rule + c->gr, c->tab.gw.data(), 8 * (size_t)c->gr, cudaMemcpyHostToDevice, c->stream));
   EFIE_CUDA(cudaMemcpyAsync(d_dirs, dirs, 24 * (size_t)ndir, cudaMemcpyHostToDevice, c->stream));
@@ -191,9 +192,6 @@ efie_status dev_far_field(Ctx *c, const double2 *w, int ndir, const double *dirs
   k_ff_final<<<ndir, 256, 0, c->stream>>>(c->nE, d_dirs, d_part, out); ++c->launches;
   EFIE_CUDA(cudaGetLastError());
   EFIE_CUDA(cudaStreamSynchronize(c->stream));
-  cudaFree(d_rule);
-  cudaFree(d_dirs);
-  cudaFree(d_part);
   return EFIE_OK;
 }
 
