@@ -1,12 +1,35 @@
-// Admission decision of the serving loop (host only, no CUDA): which queued request to start
-// when a slot is free.  Among the `lookahead` oldest queued requests whose estimated device
+// Admission of the serving loop (host only, no CUDA): the device-memory estimate of a request
+// and the decision which queued request to start when a slot is free.  Among the `lookahead` oldest queued requests whose estimated device
 // footprint fits the remaining budget (any request fits when nothing runs), the one with the
 // least estimated work is chosen; the oldest is chosen once `passes` admissions have gone to
 // requests behind it.  Returns the queue index (0 = oldest) or -1 when none fits.
 #pragma once
+#include <algorithm>
 #include <cstddef>
 
 namespace efie {
+
+// Device memory of one scattering request, estimated from the discretisation before anything
+// is built: near-field blocks (about 30 neighbours per element, FP64 plus an FP32 copy in the
+// mixed form), the Krylov bases, cluster data and work vectors.  In the mixed form the
+// directions of a request are solved in lockstep (up to 64 at a time), each with its own
+// Krylov basis, and the batched product holds per-direction superspace vectors and cluster
+// fields.  np patches, 2^level_m elements per patch direction, degree p, interpolation degree q.
+inline size_t request_footprint(int np, int level_m, int p, int q, int gmres_restart, int gmres_maxit, bool mixed,
+                                int nrhs) {
+  const size_t n = size_t(1) << level_m, nE = size_t(np) * n * n;
+  const size_t p1 = p + 1, nb = 2 * p1 * p1, nI = size_t(q + 1) * (q + 1);
+  const size_t ndof = 2 * size_t(np) * (n + p - 1) * (n + p - 1);
+  const size_t near = 30 * nE * nb * nb * (mixed ? 24 : 16);
+  const size_t kr = (size_t)std::min(gmres_restart, gmres_maxit) + 1;
+  const size_t lockstep = (mixed && nrhs > 1) ? (size_t)std::min(nrhs, 64) : 1;
+  const size_t krylov = lockstep * (kr * ndof * 16 + kr * kr * 16);
+  const size_t ncl = nE * 4 / 3 + np;
+  const size_t clusters = ncl * nI * (72 + 14 * 16);
+  const size_t vecs = nE * nb * 16 * 6 + ndof * 16 * 8;
+  const size_t batch = lockstep > 1 ? lockstep * (5 * nE * nb * 16 + 14 * ncl * nI * 8 + 4 * ndof * 16) : 0;
+  return near + krylov + clusters + vecs + batch + (size_t(64) << 20);
+}
 
 inline int pick_admission(int nqueued, const size_t *footprint, const double *cost, int oldest_passed, size_t left,
                           bool idle, int lookahead) {

@@ -58,25 +58,9 @@ struct Server {
   bool stop = false;
 };
 
-// Device memory of one request, estimated from the discretisation before anything is built:
-// near-field blocks (about 30 neighbours per element, FP64 plus an FP32 copy in the mixed
-// form), the Krylov bases, cluster data and work vectors.  In the mixed form the directions of
-// a request are solved in lockstep (up to 64 at a time), each with its own Krylov basis, and
-// the batched product holds per-direction superspace vectors and cluster fields.
 size_t estimate_footprint(const Job &j) {
-  const efie_options &o = j.opt;
-  const size_t n = size_t(1) << o.level_m, nE = size_t(j.np) * n * n;
-  const size_t p1 = o.p + 1, nb = 2 * p1 * p1, nI = size_t(o.q + 1) * (o.q + 1);
-  const size_t ndof = 2 * size_t(j.np) * (n + o.p - 1) * (n + o.p - 1);
-  const size_t near = 30 * nE * nb * nb * (o.precision == EFIE_MIXED_FP32 ? 24 : 16);
-  const size_t kr = (size_t)std::min(o.gmres_restart, o.gmres_maxit) + 1;
-  const size_t lockstep = (o.precision == EFIE_MIXED_FP32 && j.nrhs > 1) ? (size_t)std::min(j.nrhs, 64) : 1;
-  const size_t krylov = lockstep * (kr * ndof * 16 + kr * kr * 16);
-  const size_t ncl = nE * 4 / 3 + j.np;
-  const size_t clusters = ncl * nI * (72 + 14 * 16);
-  const size_t vecs = nE * nb * 16 * 6 + ndof * 16 * 8;
-  const size_t batch = lockstep > 1 ? lockstep * (5 * nE * nb * 16 + 14 * ncl * nI * 8 + 4 * ndof * 16) : 0;
-  return near + krylov + clusters + vecs + batch + (size_t(64) << 20);
+  return efie::request_footprint(j.np, j.opt.level_m, j.opt.p, j.opt.q, j.opt.gmres_restart, j.opt.gmres_maxit,
+                                 j.opt.precision == EFIE_MIXED_FP32, j.nrhs);
 }
 
 void run_job(Server *S, Job &j) {

@@ -76,6 +76,20 @@ int main() {
     }
     CHECK(admitted_before == 8);
   }
+  {  // footprint estimate: the mixed form stores an FP32 copy of the near blocks; directions
+     // solved in lockstep each hold a Krylov basis (at most 64); FP64 solves are sequential
+    using efie::request_footprint;
+    const size_t f64 = request_footprint(6, 5, 2, 8, 1500, 3000, false, 1);
+    const size_t f32 = request_footprint(6, 5, 2, 8, 1500, 3000, true, 1);
+    CHECK(f32 > f64);
+    const size_t ndof = 2 * 6 * 33 * 33, krylov1 = 1501 * ndof * 16;
+    const size_t f32x16 = request_footprint(6, 5, 2, 8, 1500, 3000, true, 16);
+    CHECK(f32x16 >= f32 + 15 * krylov1);
+    CHECK(request_footprint(6, 5, 2, 8, 1500, 3000, true, 100) == request_footprint(6, 5, 2, 8, 1500, 3000, true, 64));
+    CHECK(request_footprint(6, 5, 2, 8, 1500, 3000, false, 16) == f64);
+    CHECK(request_footprint(6, 6, 2, 8, 1500, 3000, true, 1) > f32);
+    CHECK(request_footprint(6, 5, 2, 8, 20, 3000, true, 1) < f32);  // shorter restart, smaller basis
+  }
   if (failures == 0) std::printf("ok\n");
   return failures == 0 ? 0 : 1;
 }

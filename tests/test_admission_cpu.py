@@ -1,6 +1,7 @@
-"""Serving loop admission decision (host logic): least estimated work first within a window
-of the 8 oldest requests, budget fit, oversize requests only on an idle device, and the oldest
-admitted after 8 passes.  Compiles tests/admission_check.cpp with the system C++ compiler."""
+"""Serving loop admission (host logic): least estimated work first within a window of the 8
+oldest requests, budget fit, oversize requests only on an idle device, the oldest admitted
+after 8 passes, and the properties of the device-memory estimate.  Compiles
+tests/admission_check.cpp with the system C++ compiler."""
 import os
 import shutil
 import subprocess
