@@ -10,8 +10,16 @@ One step = one pass of the whole hot path: device setup from the device-resident
 (geometry at the interpolation nodes, Sauter-Schwab near field, trees), right-hand side,
 device GMRES solve (FMM matrix-vector products) and the far field in 64 directions.
 value = solves per second (steps per second, whole job).  The mixed-precision form (FP32
-phase-split M2L, FP64 near field, geometry and GMRES) is the timed form; its
-matrix-vector product is checked against the FP64 form in the same run.
+phase-split M2L, near field integrated in FP64 and applied from FP32 blocks, geometry and
+GMRES in FP64) is the timed form.  After the timed steps, the same line carries: the
+matrix-vector products of the mixed and FP64 forms and their difference; one plain FP64 solve
+(solves/s) with the mixed form's far-field and current errors against it; the rooflines of the
+M2L (FP32 ALU), the near-field apply (HBM) and the near-field quadrature (FP64 ALU) against
+compute peaks measured on the GPU by microbench/ and the HBM copy bandwidth of
+MEASURED_PEAKS.json; the end-to-end rate with host buffers; the 64-right-hand-side torus
+leg (matvec/s, tensor roofline) and the serving leg (p50/p99 latency) unless --no-extras; and
+the oracle's CPU baseline (an estimate from a bounded sample, one core and all cores, plus a
+timed oracle solve of the 192-DOF sphere).
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
 
@@ -137,8 +145,40 @@ def dist_env():
 
 
 # ---------------------------------------------------------------------------- CPU oracle
-def oracle_sample(seconds_hint=15.0, its=None):
-    """Oracle cost of one solve of the workload (serial, one core), from a bounded sample:
+def host_cpu():
+    """(model name, logical cores) of the host, from lscpu when available."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return model, os.cpu_count() or 1
+
+
+def _far_rows_worker(args):
+    """Process-pool worker (spawned): time the oracle's far-field part of a share of element
+    rows of the workload."""
+    rows, seed = args
+    import oracle as O
+
+    w = WORKLOAD
+    r = O.Problem(G.sphere(), p=w["p"], m=w["level_m"], kappa=w["kappa"], q=w["q"], eta=w["eta"])
+    rng = np.random.default_rng(seed)
+    xs = rng.standard_normal(r.nsup) + 1j * rng.standard_normal(r.nsup)
+    t = time.perf_counter()
+    r.fmm_rows_far(xs, np.asarray(rows[:0], np.int32))  # direct moments alone
+    t_mom = time.perf_counter() - t
+    t = time.perf_counter()
+    r.fmm_rows_far(xs, np.asarray(rows, np.int32))
+    return max(time.perf_counter() - t - t_mom, 1e-9)
+
+
+def oracle_sample(its=None, all_cores=True):
+    """Estimate of the oracle's cost of one solve of the workload, from a bounded sample:
     * setup = problem creation + (near pairs) x (time of one near block, timed on the near
       pairs of 3 sampled elements);
     * product = direct moments (timed) + (far blocks) x (time of one far block), the latter
@@ -146,7 +186,9 @@ def oracle_sample(seconds_hint=15.0, its=None):
       level l is applied once for each of the 4^(m-l) elements under it, which gives the
       number of far blocks the sampled rows process on average;
     the near-field apply with the stored blocks (< 0.5 % of the product) is not counted.
-    Returns (solves/s, details)."""
+    Serial (one core) and, with all_cores, the far-field rows split over one spawned process
+    per core (the oracle's near-block loop uses OpenMP over pairs).
+    Returns (solves/s on one core, details)."""
     import oracle as O
 
     geo = G.sphere()
@@ -180,12 +222,48 @@ def oracle_sample(seconds_hint=15.0, its=None):
     setup = t_create + len(near) * t_pair
     its = its or 1
     solve = setup + its * apply_
-    return 1.0 / solve, {"oracle_setup_s_est": setup, "oracle_matvec_s_est": apply_, "iterations": its,
-                         "far_block_us": t_block * 1e6, "near_block_ms": t_pair * 1e3,
-                         "sample": f"oracle far field of {nrow} of {nE} element rows (far blocks per row from the "
-                                   f"block tree), direct moments, and near blocks of {len(sel)} pairs; scaled to "
-                                   f"{len(far)} far blocks and {len(near)} near pairs; solve = setup + {its} x "
-                                   f"product; serial, one core"}
+    model, ncores = host_cpu()
+    det = {"kind": "estimate", "oracle_setup_s_est": setup, "oracle_matvec_s_est": apply_, "iterations": its,
+           "far_block_us": t_block * 1e6, "near_block_ms": t_pair * 1e3, "cpu_model": model, "cpu_cores": ncores,
+           "sample": f"estimate, not a timed solve: oracle far field of {nrow} of {nE} element rows (far blocks per "
+                     f"row from the block tree), direct moments, and near blocks of {len(sel)} pairs; scaled to "
+                     f"{len(far)} far blocks and {len(near)} near pairs; solve = setup + {its} x product; serial, "
+                     f"one core"}
+    if all_cores and ncores > 1:
+        import multiprocessing as mp
+
+        rows_per = 24
+        shares = [(e_all[nrow + i * rows_per: nrow + (i + 1) * rows_per].tolist(), 100 + i) for i in range(ncores)]
+        ctx = mp.get_context("spawn")
+        t = time.perf_counter()
+        with ctx.Pool(ncores) as pool:
+            times = pool.map(_far_rows_worker, shares)
+        wall = max(times)
+        t_block_all = wall / (rows_per * ncores * blocks_per_row)
+        apply_all = t_mom + len(far) * t_block_all
+        setup_all = t_create + len(near) * t_pair / ncores
+        det.update({"all_cores": ncores, "far_block_us_all_cores": t_block_all * 1e6,
+                    "oracle_matvec_s_est_all_cores": apply_all,
+                    "solves_per_s_all_cores": 1.0 / (setup_all + its * apply_all),
+                    "all_cores_sample": f"far field of {rows_per} rows per process on {ncores} spawned processes "
+                                        f"(slowest process's time), near blocks scaled by 1/{ncores}, direct "
+                                        f"moments serial; pool wall {time.perf_counter() - t:.1f} s"})
+    return 1.0 / solve, det
+
+
+def oracle_timed_small_solve():
+    """A really timed oracle solve on the host: the 192-DOF sphere (6 patches, p = 1, 4 x 4
+    elements per patch, kappa = 1, q = 4, eta = 1.6), one plane wave along +z polarised in x,
+    FMM operator, GMRES to 1e-8 (serial except the near-block loop)."""
+    import oracle as O
+
+    t0 = time.perf_counter()
+    r = O.Problem(G.sphere(), p=1, m=2, kappa=1.0, q=4, eta=1.6)
+    b = r.rhs(np.array([0, 0, 1.0]), np.array([1.0, 0, 0]))
+    x, its = r.gmres(b, use_fmm=True, tol=1e-8)[:2]
+    dt = time.perf_counter() - t0
+    return {"workload": "sphere6_p1_n4_kappa1_q4 (192 DOFs), GMRES 1e-8", "seconds": dt, "solves_per_s": 1.0 / dt,
+            "gmres_iterations": int(its)}
 
 
 def run_reference(args):
@@ -196,7 +274,7 @@ def run_reference(args):
     vals = []
     det = None
     for _ in range(args.warmup + args.steps):
-        v, det = oracle_sample(its=its)
+        v, det = oracle_sample(its=its, all_cores=False)
         vals.append(v)
     vals = vals[args.warmup:]
     val = statistics.median(vals)
@@ -207,9 +285,23 @@ def run_reference(args):
             "config": dict(WORKLOAD, precision=args.precision, parallelism="single"),
             "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": det["sample"]},
             "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "note": "each step is a bounded oracle sample (about 20 s) from which the cost of one solve is "
+                    "estimated; ms_per_step is that estimated solve time, not the sample's wall time",
             "details": det}
     print(json.dumps(line))
     return 0
+
+
+# ---------------------------------------------------------------------------- measured peaks
+def measured_peaks():
+    """Compute peaks measured on this GPU by microbench/ (FFMA, FFMA2, DFMA, MUFU, tcgen05), or
+    None with the reason."""
+    try:
+        import microbench
+
+        return microbench.measure(), None
+    except Exception as e:  # noqa: BLE001
+        return None, f"peak microbenchmark unavailable: {e}"
 
 
 # ---------------------------------------------------------------------------- GPU
@@ -231,6 +323,7 @@ def run_gpu(args):
     kw = dict(p=w["p"], level_m=w["level_m"], kappa=w["kappa"], q=w["q"], eta=w["eta"], gmres_tol=w["gmres_tol"],
               gmres_restart=w["gmres_restart"], gmres_maxit=args.maxit, m2l_store=args.m2l_store)
     prec = 1 if args.precision == "mixed" else 0
+    pk_alu, pk_err = measured_peaks() if not args.only_steps else (None, "skipped")
     s = Solver(geo, stream=stream.cuda_stream, precision=prec, **kw)
     N = s.ndof
     dirs = far_dirs(64)
@@ -258,12 +351,12 @@ def run_gpu(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record(stream)
-    its = []
-    conv = []
+    its, conv, setups = [], [], []
     for _ in range(args.steps):
         info, st = step()
         its.append(info.iterations)
         conv.append(bool(info.converged))
+        setups.append(s.setup_timings())
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -278,6 +371,8 @@ def run_gpu(args):
                               "gmres_iterations": int(np.median(its)), "gpu_launches": int(launches)}))
         s.close()
         return 0
+    e_mixed = edev[0].cpu().numpy().copy()
+    w_mixed = wdev[0].cpu().numpy().copy()
 
     # matrix-vector products: mixed vs FP64 form, per-phase device times (CUDA events on
     # the library's stream), roofline of the dominant kernel
@@ -300,7 +395,27 @@ def run_gpu(args):
             ph64.append(s64.last_timings())
     mv64 = {k: statistics.median([p[k] for p in ph64]) for k in ph64[0]}
     err_vs_fp64 = float(torch.linalg.norm(y_mixed - y64) / torch.linalg.norm(y64))
-    # far-field error of the mixed solution vs the FP64 operator applied in the same solve
+
+    fp64 = None
+    if not args.no_fp64_solve:
+        # the plain FP64 form: one whole step (setup, solve, far field) timed on the host clock
+        # around synchronous calls, and the per-result errors of the mixed form against it
+        w64 = torch.zeros((1, N), dtype=torch.complex128, device="cuda")
+        e64 = torch.zeros((1, 64, 3), dtype=torch.complex128, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s64.setup()
+        _, info64, _ = s64.solve_plane_waves(d_inc, p_inc, out=w64)
+        s64.far_field(w64[0], dirs, out=e64)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        E64, W64 = e64[0].cpu().numpy(), w64[0].cpu().numpy()
+        fp64 = {"solves_per_s": 1.0 / t64, "ms_per_solve": t64 * 1e3, "gmres_iterations": int(info64.iterations),
+                "converged": bool(info64.converged), "m2l": "stored FP64 coupling matrices",
+                "far_field_rel_err_mixed_vs_fp64": float(np.abs(e_mixed - E64).max() / np.abs(E64).max()),
+                "current_rel_err_mixed_vs_fp64": float(np.linalg.norm(w_mixed - W64) / np.linalg.norm(W64)),
+                "note": "far-field error = max over 64 directions and 3 components of |E_mixed - E_fp64|, "
+                        "relative to max |E_fp64|; both solves to GMRES 1e-6"}
     pk = peaks()
     n_eval = s.nfar * (w["q"] + 1) ** 4
     # 4 complex MACs on the folded fields (32) + kernel generation counted as 16: distance 9,
@@ -308,36 +423,75 @@ def run_gpu(args):
     flops_per_eval = 48.0
     m2l_ms = mv["m2l"]
     achieved = n_eval * flops_per_eval / (m2l_ms * 1e-3) / 1e12
-    fp32_peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    if pk_alu:
+        fp32_peak = max(pk_alu["ffma_flops"], pk_alu["ffma2_flops"]) / 1e12
+        peak_note = ("FP32: measured on this GPU (microbench/peaks.cu), max of scalar FFMA "
+                     f"{pk_alu['ffma_flops'] / 1e12:.1f} and packed FFMA2 {pk_alu['ffma2_flops'] / 1e12:.1f} TFLOP/s")
+    else:
+        fp32_peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        peak_note = f"FP32 derived (152 SMs x 128 lanes x 2 flop x max clock), not measured: {pk_err}"
     roof = {"kernel": "k_m2l_f32w", "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak, "traffic": None,
-            "peak_note": "FP32 SIMT: 152 SMs x 128 lanes x 2 flop x max SM clock (derived, not measured)",
+            "frac": achieved / fp32_peak, "traffic": None, "peak_note": peak_note,
             "work": f"{n_eval:.3e} kernel entries x {flops_per_eval:.0f} flop per matvec", "m2l_ms": m2l_ms}
+    if pk_alu:
+        # time each pipe needs for the entries at its measured rate (per entry: 8 packed FMAs on
+        # the FMA pipe and 3 MUFU operations in the direct-phase form)
+        mufu_rate = min(pk_alu["rsqrt_per_s"], pk_alu["sin_per_s"], pk_alu["cos_per_s"])
+        roof["pipe_bound_ms"] = {"fma_32flop_per_entry": n_eval * 32 / pk_alu["ffma2_flops"] * 1e3,
+                                 "mufu_3_per_entry": n_eval * 3 / mufu_rate * 1e3}
     near_bytes = s.nnear * s.nb * s.nb * (8 if prec else 16) + 2 * s.nsup * 16
     near_roof = {"kernel": "k_near_apply", "bound": "hbm", "achieved": near_bytes / (mv["near"] * 1e-3) / 1e9,
-                 "peak": pk.get("hbm_gbs"), "unit": "GB/s", "near_ms": mv["near"], "bytes": near_bytes}
+                 "peak": pk.get("hbm_gbs"), "unit": "GB/s", "near_ms": mv["near"], "bytes": near_bytes,
+                 "peak_note": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
     near_roof["frac"] = near_roof["achieved"] / near_roof["peak"]
+    st_ = {k: statistics.median([x_[k] for x_ in setups]) for k in setups[0]}
+    # k_near_quad: per quadrature point and block entry, the integrand of eq. Vkh is a real
+    # combination of two products (geometry term and div-div term: 2 FMA) scaled by the complex
+    # kernel value (2 FMA): 8 FP64 flop per entry and point
+    quad_flop = st_["near_quad_points"] * s.nb * s.nb * 8.0
+    roof_setup = {"kernel": "k_near_quad", "bound": "alu (FP64)", "unit": "TFLOP/s",
+                  "achieved": quad_flop / (st_["near_quad_ms"] * 1e-3) / 1e12, "near_quad_ms": st_["near_quad_ms"],
+                  "setup_ms": st_["setup_ms"], "work": f"{st_['near_quad_points']:.3e} quadrature points x "
+                                                        f"{s.nb}^2 entries x 8 flop",
+                  "pairs_integrated": int(st_["near_quad_pairs"])}
+    if pk_alu:
+        roof_setup["peak"] = pk_alu["dfma_flops"] / 1e12
+        roof_setup["frac"] = roof_setup["achieved"] / roof_setup["peak"]
+        roof_setup["peak_note"] = "FP64 DFMA measured on this GPU (microbench/peaks.cu)"
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     deg, ncp, knots, cp, wgt = flatten(geo)
     h2d = sum(a.nbytes for a in (deg, ncp, knots, cp, wgt, d_inc, p_inc, dirs))
     d2h = N * 16 + 64 * 3 * 16
     s_e2e = Solver(None, stream=stream.cuda_stream, precision=prec, **kw)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    e2e_ms = []
     for _ in range(max(1, args.e2e_steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         s_e2e.set_geometry(geo)
         s_e2e.setup()
         wh, _, _ = s_e2e.solve_plane_waves(d_inc, p_inc)
         s_e2e.far_field(wh[0], dirs)
-    torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1000.0 / max(1, args.e2e_steps)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1000.0)
+    s.close()
+    s64.close()
+    s_e2e.close()
+
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        extra["multi"] = multi_leg(args, steps=args.multi_steps, pk_alu=pk_alu)
+        extra["serving"] = serving_leg(args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, det = oracle_sample(its=int(np.median(its)))
-        cpu = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": det["sample"],
-               "oracle_matvec_s_est": det["oracle_matvec_s_est"], "oracle_setup_s_est": det["oracle_setup_s_est"]}
+        cpu = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": det["sample"]}
+        cpu.update({k: det[k] for k in det if k not in ("sample",)})
+        try:
+            cpu["timed_solve_small"] = oracle_timed_small_solve()
+        except Exception as e:  # noqa: BLE001
+            cpu["timed_solve_small"] = f"failed: {e}"
 
     if rank == 0:
         line = {
@@ -347,20 +501,23 @@ def run_gpu(args):
             "dtype": "f32-m2l/f64" if prec else "f64", "data": "synthetic",
             "config": dict(WORKLOAD, precision=args.precision, parallelism="replicas" if world > 1 else "single"),
             "gmres_iterations": int(np.median(its)), "converged": all(conv),
+            "setup_ms": st_["setup_ms"],
             "matvec_per_s": 1000.0 / mv["total"], "matvec_ms_phases": mv,
             "matvec_per_s_fp64": 1000.0 / mv64["total"], "matvec_ms_phases_fp64": mv64,
             "matvec_rel_err_vs_fp64": err_vs_fp64,
-            "roofline": roof, "roofline_near": near_roof,
+            "fp64_solve": fp64,
+            "roofline": roof, "roofline_near": near_roof, "roofline_setup": roof_setup,
+            "peaks_measured": pk_alu, "peaks_hbm_bf16": {k: pk.get(k) for k in ("hbm_gbs", "bf16_tflops",
+                                                                               "bf16_tflops_sustained")},
             "cpu_baseline": cpu,
-            "e2e": {"value": 1000.0 / e2e_ms, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h)},
+            "e2e": {"value": 1000.0 / statistics.median(e2e_ms), "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "steps": len(e2e_ms), "ms_min": min(e2e_ms),
+                    "ms_median": statistics.median(e2e_ms), "ms_max": max(e2e_ms)},
             "gpu_launches": int(launches),
             "clocks": clocks,
         }
+        line.update(extra)
         print(json.dumps(line))
-    s.close()
-    s64.close()
-    s_e2e.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -379,9 +536,9 @@ MULTI = {
 }
 
 
-def run_multi(args):
+def multi_leg(args, steps=None, pk_alu=None):
     """One step = one matrix-vector product of all 64 right-hand sides (a batched GMRES
-    iteration's product); value = right-hand-side products per second."""
+    iteration's product); value = right-hand-side products per second.  Returns the line."""
     import torch
 
     torch.cuda.set_device(0)
@@ -399,7 +556,8 @@ def run_multi(args):
     b = s.rhs(d, pol)                                    # [R][N] right-hand sides (host)
     x = torch.from_numpy(b).cuda()
     y = torch.empty_like(x)
-    for _ in range(args.warmup):
+    steps = steps or args.steps
+    for _ in range(max(3, min(args.warmup, steps))):
         s.matvec(x, out=y)
     torch.cuda.synchronize()
     clk = ClockSampler(0)
@@ -408,14 +566,14 @@ def run_multi(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     ph = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         s.matvec(x, out=y)
         ph.append(s.last_timings())
     ev1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
     launches = s.launch_count() - l0
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = ev0.elapsed_time(ev1) / steps
     mv = {k: statistics.median([p_[k] for p_ in ph]) for k in ph[0]}
     # the batched tensor-core product against the single-vector FP32 product (CUDA cores)
     # for two right-hand sides
@@ -458,6 +616,11 @@ def run_multi(args):
                     f"(complex MACs of {4 * R} fields); executed on the tensor pipe (3 split-TF32 passes, "
                     f"padded to N={2 * np_}, K={kp}) = {executed:.3e}",
             "executed_tflops": executed / m2l_s / 1e12, "m2l_ms": mv["m2l"]}
+    if pk_alu and pk_alu.get("tcgen05_tf32_flops", 0) > 0:
+        tf = pk_alu["tcgen05_tf32_flops"] / 1e12
+        roof["peak_measured_tcgen05_tf32"] = tf
+        roof["frac_of_measured_tcgen05_tf32"] = useful / m2l_s / 1e12 / tf
+        roof["executed_frac_of_measured_tcgen05_tf32"] = executed / m2l_s / 1e12 / tf
     # end to end with host buffers
     yh = np.empty_like(b)
     torch.cuda.synchronize()
@@ -467,7 +630,7 @@ def run_multi(args):
     e2e_ms = (time.perf_counter() - t0) * 1000.0 / max(1, args.e2e_steps)
     line = {"metric": "FMM-EFIE matvec/s (right-hand-side products per second, 64 right-hand sides per "
                       "batched product), mixed precision",
-            "value": R * 1000.0 / ms, "unit": "matvec/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "value": R * 1000.0 / ms, "unit": "matvec/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "tf32x3-m2l/f32/f64", "data": "synthetic", "config": MULTI, "ndof": int(N),
             "far_pairs": int(s.nfar), "near_pairs": int(s.nnear), "setup_s": setup_s,
@@ -477,8 +640,13 @@ def run_multi(args):
             "e2e": {"value": R * 1000.0 / e2e_ms, "unit": "matvec/s", "h2d_bytes_per_step": int(b.nbytes),
                     "d2h_bytes_per_step": int(yh.nbytes)},
             "gpu_launches": int(launches), "clocks": clocks}
-    print(json.dumps(line))
     s.close()
+    return line
+
+
+def run_multi(args):
+    pk_alu, _ = measured_peaks()
+    print(json.dumps(multi_leg(args, pk_alu=pk_alu)))
     return 0
 
 
@@ -583,7 +751,8 @@ def run_batch(args):
     return 0
 
 
-def run_serving(args):
+def serving_leg(args):
+    """The serving stream: Poisson arrivals through the serving loop; returns the line."""
     import torch
     from paper_1807_03097_gb300.efie import Server
 
@@ -608,8 +777,14 @@ def run_serving(args):
             "requests": len(reqs), "requests_converged": ok, "plane_wave_solves": nsolve,
             "makespan_s": makespan, "latency_ms_p50": float(np.percentile(lat, 50)),
             "latency_ms_p99": float(np.percentile(lat, 99)), "slots": args.slots, "budget_gib": args.budget_gib,
-            "dofs": [int(x[0].ndof) for x in res], "data": "synthetic", "config": SERVING}
-    print(json.dumps(line))
+            "dofs": [int(x[0].ndof) for x in res], "data": "synthetic", "config": SERVING,
+            "footprint_over_device_peak_min": float(min(x[0].footprint_bytes / max(x[0].device_peak_bytes, 1)
+                                                        for x in res))}
+    return line
+
+
+def run_serving(args):
+    print(json.dumps(serving_leg(args)))
     return 0
 
 
@@ -621,7 +796,11 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--maxit", type=int, default=MAXIT)
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload only: skip the 64-right-hand-side torus and serving legs")
+    ap.add_argument("--no-fp64-solve", action="store_true", help="skip the plain FP64 solve of the workload")
+    ap.add_argument("--multi-steps", type=int, default=3, help="timed batched products of the torus leg")
     ap.add_argument("--ref-iterations", type=int, default=WORKLOAD_ITERATIONS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-steps", action="store_true", help="time the steps only (for launch-list profiling)")

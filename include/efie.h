@@ -53,7 +53,9 @@ typedef int efie_status;
 
 #define EFIE_FP64 0           /* every step in FP64 */
 #define EFIE_MIXED_FP32 1     /* moments, M2M, M2L, L2L in FP32 (phase split, FP64 per-pair
-                                 phase); geometry, near field and GMRES in FP64 */
+                                 phase); the near-field blocks are integrated in FP64 and
+                                 applied from an FP32 copy with compensated FP32 sums;
+                                 geometry, right-hand side, far field and GMRES in FP64 */
 
 #define EFIE_PTR_HOST 0
 #define EFIE_PTR_DEVICE 1
@@ -62,7 +64,7 @@ typedef struct efie_ctx efie_ctx;
 
 /* Discretisation and solver parameters (the paper's problem statement, Sec. 4.1, 4.2, 5). */
 typedef struct {
-  int p;             /* degree of S^0; S^1 uses (p, p-1) x (p-1, p), 1 <= p <= 6 (Sec. 3.2) */
+  int p;             /* degree of S^0; S^1 uses (p, p-1) x (p-1, p), 1 <= p <= 4 (Sec. 3.2) */
   int level_m;       /* refinement level: 2^m equidistant elements per patch direction,
                         0 <= m <= 10 (Sec. 4.1) */
   double kappa;      /* wavenumber, > 0 (eq. HelmholtzGreen) */
@@ -185,12 +187,24 @@ efie_status efie_block_counts(const efie_ctx *ctx, int64_t *nfar, int64_t *nnear
 efie_status efie_export_blocks(const efie_ctx *ctx, int *far, int *near);
 efie_status efie_export_near_blocks(efie_ctx *ctx, double *blocks);
 efie_status efie_matvec_superspace(efie_ctx *ctx, const double *xs, double *ys, int ptr_kind);
+/* ys[r] = (N + F) xs[r] for nrhs superspace vectors, [nrhs][nE][2][p+1][p+1] complex in
+ * ptr_kind memory: the product of several right-hand sides (eq. FMMlr) without the T gather
+ * and scatter, in one batched pass per 64 vectors in the mixed form (the M2L chosen by
+ * m2l_batch), one vector after the other in the FP64 form. */
+efie_status efie_matvec_superspace_batch(efie_ctx *ctx, int nrhs, const double *xs, double *ys, int ptr_kind);
 
 /* Device time in milliseconds of the named phases of the most recent efie_matvec
  * (CUDA events on the context stream): out[0] total, [1] gather, [2] near apply,
  * [3] moments + M2M, [4] M2L, [5] L2L + evaluation, [6] scatter.  Returns the number of
  * values written (<= n). */
 int efie_last_timings(const efie_ctx *ctx, double *out, int n);
+
+/* Figures of the last efie_setup: out[0] wall time of the setup (ms), [1] device time of the
+ * near-field quadrature kernel (ms, CUDA events on the context stream), [2] quadrature points
+ * it evaluated (Duffy parts x g^4, summed over the pairs integrated), [3] element pairs it
+ * integrated (the others are mirrored, B(e', e) = B(e, e')^T).  Returns the number of values
+ * written (<= n). */
+int efie_setup_timings(const efie_ctx *ctx, double *out, int n);
 
 /* Far field like efie_far_field, for callers that must not allocate device memory during
  * the call (a process running under a fixed device-memory budget owned by another
@@ -201,8 +215,8 @@ int efie_last_timings(const efie_ctx *ctx, double *out, int n);
  *  e_inf_dev  [ndir][3] complex output, device memory
  * Nothing is allocated: the T gather is fused into the kernel and the partial sums use one
  * file-scope device array of 2^18 complex doubles (4 MiB) that every GPU loading the library
- * holds until the process exits.  Limit: 3 * ndir * ceil(elements / 16) <= 2^18, else
- * EFIE_EINVAL.  The first call on a device looks up the array's device address
+ * holds until the process exits.  Limits: 3 * ndir * ceil(elements / 16) <= 2^18 and
+ * ndir <= 65535, else EFIE_EINVAL.  The caller's current CUDA device is unchanged on return.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before any stream
  * capture.  All calls on a device share the array and each call rewrites the part it uses
  * in full; calls that overlap on the GPU (other streams or other contexts on the same
@@ -213,6 +227,13 @@ efie_status efie_far_field_noalloc(efie_ctx *ctx, const double *w_dev, int ndir,
 /* Number of CUDA kernels this context has launched since efie_create (all phases);
  * -1 for a NULL context. */
 int64_t efie_launch_count(const efie_ctx *ctx);
+
+/* Device memory of the context: *live = bytes held now, *peak = the most held at any time
+ * since efie_create (both may be NULL).  Device buffers come from one stream-ordered memory
+ * pool per device (allocated and freed on the context's stream, so that no call of one
+ * context synchronises the device or waits for another context).  The paper has no
+ * counterpart; this is for admission control and tests.  EFIE_EINVAL for a NULL ctx. */
+efie_status efie_device_bytes(const efie_ctx *ctx, int64_t *live, int64_t *peak);
 
 /* Releases all device and host memory of the context (NULL is accepted). */
 efie_status efie_destroy(efie_ctx *ctx);
@@ -253,6 +274,8 @@ typedef struct {
   double queue_ms;         /* submit -> admitted */
   double latency_ms;       /* submit -> result in the caller's buffers */
   double setup_ms, solve_ms;
+  int64_t footprint_bytes;   /* the admission's device-memory estimate of the request */
+  int64_t device_peak_bytes; /* device memory the request's context held at its peak */
 } efie_result;
 
 /* Starts max_slots worker threads on the current CUDA device with a device-memory budget in

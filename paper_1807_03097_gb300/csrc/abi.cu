@@ -20,31 +20,26 @@ efie_status dev_norms(Ctx *c, int N, const double2 *v, double *out);
 
 namespace {
 
-template <class T>
-void dfree(T *&p) {
-  if (p) cudaFree(p);
-  p = nullptr;
-}
-
+// Returns every device buffer of the context to the pool (in stream order on c->stream;
+// callers make sure that no work on the second stream still reads them).
 void release_device(Ctx *c) {
-  dfree(c->d_patches); dfree(c->d_knots); dfree(c->d_cpw);
-  dfree(c->d_tg_ptr); dfree(c->d_tg_col); dfree(c->d_tg_val);
-  dfree(c->d_ts_ptr); dfree(c->d_ts_col); dfree(c->d_ts_val);
-  dfree(c->d_nodeX); dfree(c->d_nodeD); dfree(c->d_nodeXf); dfree(c->d_center);
-  dfree(c->d_far_ptr); dfree(c->d_far_src); dfree(c->d_m2l_targets);
-  dfree(c->d_near_ptr); dfree(c->d_near_src); dfree(c->d_nblk); dfree(c->d_nblkf);
-  dfree(c->d_M); dfree(c->d_Md); dfree(c->d_E); dfree(c->d_Mf); dfree(c->d_Mdf); dfree(c->d_Ef);
-  dfree(c->d_x); dfree(c->d_y); dfree(c->d_xs); dfree(c->d_ys); dfree(c->d_ysn);
-  dfree(c->d_mom); dfree(c->d_src); dfree(c->d_acc); dfree(c->d_loc);
-  dfree(c->d_momf); dfree(c->d_srcf); dfree(c->d_locf); dfree(c->d_accm); dfree(c->d_accf);
-  dfree(c->d_nodeX4); dfree(c->d_pgeo); dfree(c->d_pph); dfree(c->d_far_tgt);
-  if (c->d_K) cudaFree(c->d_K);
-  c->d_K = nullptr;
+  dfree(c, c->d_patches); dfree(c, c->d_knots); dfree(c, c->d_cpw);
+  dfree(c, c->d_tg_ptr); dfree(c, c->d_tg_col); dfree(c, c->d_tg_val);
+  dfree(c, c->d_ts_ptr); dfree(c, c->d_ts_col); dfree(c, c->d_ts_val);
+  dfree(c, c->d_nodeX); dfree(c, c->d_nodeD); dfree(c, c->d_nodeXf); dfree(c, c->d_center);
+  dfree(c, c->d_far_ptr); dfree(c, c->d_far_src); dfree(c, c->d_m2l_targets);
+  dfree(c, c->d_near_ptr); dfree(c, c->d_near_src); dfree(c, c->d_nblk); dfree(c, c->d_nblkf);
+  dfree(c, c->d_M); dfree(c, c->d_Md); dfree(c, c->d_E); dfree(c, c->d_Mf); dfree(c, c->d_Mdf); dfree(c, c->d_Ef);
+  dfree(c, c->d_x); dfree(c, c->d_y); dfree(c, c->d_xs); dfree(c, c->d_ys); dfree(c, c->d_ysn);
+  dfree(c, c->d_mom); dfree(c, c->d_src); dfree(c, c->d_acc); dfree(c, c->d_loc);
+  dfree(c, c->d_momf); dfree(c, c->d_srcf); dfree(c, c->d_locf); dfree(c, c->d_accm); dfree(c, c->d_accf);
+  dfree(c, c->d_nodeX4); dfree(c, c->d_pgeo); dfree(c, c->d_pph); dfree(c, c->d_far_tgt);
+  dfree(c, c->d_K);
   c->k_stored = false;
-  dfree(c->d_V); dfree(c->d_H); dfree(c->d_h); dfree(c->d_h2); dfree(c->d_part); dfree(c->d_gs);
-  dfree(c->d_w); dfree(c->d_r); dfree(c->d_b); dfree(c->d_sol);
-  dfree(c->d_xB); dfree(c->d_yB); dfree(c->d_xsB); dfree(c->d_ysB); dfree(c->d_ysnB);
-  dfree(c->d_momB); dfree(c->d_srcB); dfree(c->d_accB); dfree(c->d_locB); dfree(c->d_tc_err);
+  dfree(c, c->d_V); dfree(c, c->d_H); dfree(c, c->d_h); dfree(c, c->d_h2); dfree(c, c->d_part); dfree(c, c->d_gs);
+  dfree(c, c->d_w); dfree(c, c->d_r); dfree(c, c->d_b); dfree(c, c->d_sol);
+  dfree(c, c->d_xB); dfree(c, c->d_yB); dfree(c, c->d_xsB); dfree(c, c->d_ysB); dfree(c, c->d_ysnB);
+  dfree(c, c->d_momB); dfree(c, c->d_srcB); dfree(c, c->d_accB); dfree(c, c->d_locB); dfree(c, c->d_tc_err);
   c->batch_cap = 0;
   c->kr = 0;
   c->part_cap = 0;
@@ -140,6 +135,11 @@ efie_status efie_create(efie_ctx **out, const efie_options *opt, void *cuda_stre
   }
   for (int i = 0; i < 8; ++i) cudaEventCreate(&c->tm.ev[i]);
   c->tm.made = true;
+  if (pool_ref(c->device) != EFIE_OK) {
+    efie_destroy(reinterpret_cast<efie_ctx *>(c));
+    return EFIE_ECUDA;
+  }
+  c->pool_held = true;
   *out = reinterpret_cast<efie_ctx *>(c);
   return EFIE_OK;
 }
@@ -151,10 +151,13 @@ efie_status efie_destroy(efie_ctx *ctx) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->stream2) cudaStreamSynchronize(c->stream2);
   release_device(c);
-  if (c->h_res) cudaFreeHost(c->h_res);
-  if (c->h_resB) cudaFreeHost(c->h_resB);
+  if (c->stream) cudaStreamSynchronize(c->stream);  // the stream-ordered frees are done
+  pinned_put(c->h_res);
+  pinned_put(c->h_resB);
+  c->h_res = nullptr;
   c->h_resB = nullptr;
   c->h_resB_cap = 0;
+  if (c->pool_held) pool_unref(c->device);
   if (c->tm.made)
     for (int i = 0; i < 8; ++i) cudaEventDestroy(c->tm.ev[i]);
   if (c->fork) cudaEventDestroy(c->fork);
@@ -212,10 +215,11 @@ efie_status efie_set_geometry(efie_ctx *ctx, int n_patches, const int *deg, cons
   EFIE_TRY(dalloc(c, &c->d_patches, P.size()));
   EFIE_TRY(dalloc(c, &c->d_knots, kn.size()));
   EFIE_TRY(dalloc(c, &c->d_cpw, hw.size() / 4));
-  EFIE_CUDA(cudaMemcpy(c->d_patches, P.data(), sizeof(PatchDesc) * P.size(), cudaMemcpyHostToDevice));
-  EFIE_CUDA(cudaMemcpy(c->d_knots, kn.data(), 8 * kn.size(), cudaMemcpyHostToDevice));
-  EFIE_CUDA(cudaMemcpy(c->d_cpw, hw.data(), 8 * hw.size(), cudaMemcpyHostToDevice));
-  EFIE_CUDA(cudaDeviceSynchronize());
+  EFIE_CUDA(cudaMemcpyAsync(c->d_patches, P.data(), sizeof(PatchDesc) * P.size(), cudaMemcpyHostToDevice,
+                            c->stream));
+  EFIE_CUDA(cudaMemcpyAsync(c->d_knots, kn.data(), 8 * kn.size(), cudaMemcpyHostToDevice, c->stream));
+  EFIE_CUDA(cudaMemcpyAsync(c->d_cpw, hw.data(), 8 * hw.size(), cudaMemcpyHostToDevice, c->stream));
+  EFIE_CUDA(cudaStreamSynchronize(c->stream));
   c->have_geometry = true;
   return EFIE_OK;
 }
@@ -352,7 +356,8 @@ efie_status efie_export_near_blocks(efie_ctx *ctx, double *blocks) {
   cudaSetDevice(c->device);
   const size_t nb2 = (size_t)c->nb * c->nb;
   std::vector<double2> tmp(nb2 * c->nnear);
-  EFIE_CUDA(cudaMemcpy(tmp.data(), c->d_nblk, 16 * tmp.size(), cudaMemcpyDeviceToHost));
+  EFIE_CUDA(cudaMemcpyAsync(tmp.data(), c->d_nblk, 16 * tmp.size(), cudaMemcpyDeviceToHost, c->stream));
+  EFIE_CUDA(cudaStreamSynchronize(c->stream));
   double2 *out = reinterpret_cast<double2 *>(blocks);
   for (int at = 0; at < c->nnear; ++at) {
     int k = c->near_perm[at];
@@ -437,9 +442,10 @@ efie_status efie_matvec_superspace(efie_ctx *ctx, const double *xs, double *ys, 
   const size_t S = c->nsup;
   double2 *in = c->d_xs, *out = c->d_ys;
   double2 *tmp_in = nullptr, *tmp_out = nullptr;
+  DevTemp tmp;
   if (ptr_kind == EFIE_PTR_HOST) {
-    EFIE_TRY(dalloc(c, &tmp_in, S));
-    EFIE_TRY(dalloc(c, &tmp_out, S));
+    EFIE_TRY(tmp.get(c, &tmp_in, S));
+    EFIE_TRY(tmp.get(c, &tmp_out, S));
     EFIE_CUDA(cudaMemcpyAsync(tmp_in, xs, 16 * S, cudaMemcpyHostToDevice, c->stream));
     in = tmp_in;
     out = tmp_out;
@@ -450,9 +456,43 @@ efie_status efie_matvec_superspace(efie_ctx *ctx, const double *xs, double *ys, 
   EFIE_TRY(dev_matvec_super(c, in, out));
   if (ptr_kind == EFIE_PTR_HOST) EFIE_CUDA(cudaMemcpyAsync(ys, out, 16 * S, cudaMemcpyDeviceToHost, c->stream));
   EFIE_CUDA(cudaStreamSynchronize(c->stream));
-  if (tmp_in) cudaFree(tmp_in);
-  if (tmp_out) cudaFree(tmp_out);
   return EFIE_OK;
+}
+
+efie_status efie_matvec_superspace_batch(efie_ctx *ctx, int nrhs, const double *xs, double *ys, int ptr_kind) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c || nrhs < 0 || (nrhs > 0 && (!xs || !ys))) return EFIE_EINVAL;
+  if (ptr_kind != EFIE_PTR_HOST && ptr_kind != EFIE_PTR_DEVICE) return EFIE_EINVAL;
+  if (!c->setup_done) return EFIE_ESTATE;
+  if (nrhs == 0) return EFIE_OK;
+  cudaSetDevice(c->device);
+  const size_t S = c->nsup;
+  const int chunk = std::min(64, nrhs);
+  DevTemp tmp;
+  double2 *din = nullptr, *dout = nullptr;
+  if (ptr_kind == EFIE_PTR_HOST) {
+    EFIE_TRY(tmp.get(c, &din, (size_t)chunk * S));
+    EFIE_TRY(tmp.get(c, &dout, (size_t)chunk * S));
+  }
+  for (int r0 = 0; r0 < nrhs; r0 += chunk) {
+    const int R = std::min(chunk, nrhs - r0);
+    const double2 *xr = reinterpret_cast<const double2 *>(xs) + r0 * S;
+    double2 *yr = reinterpret_cast<double2 *>(ys) + r0 * S;
+    const double2 *xp[64];
+    double2 *yp[64];
+    if (ptr_kind == EFIE_PTR_HOST)
+      EFIE_CUDA(cudaMemcpyAsync(din, xr, 16 * S * R, cudaMemcpyHostToDevice, c->stream));
+    for (int r = 0; r < R; ++r) {
+      xp[r] = ptr_kind == EFIE_PTR_HOST ? din + r * S : xr + r * S;
+      yp[r] = ptr_kind == EFIE_PTR_HOST ? dout + r * S : yr + r * S;
+    }
+    EFIE_TRY(dev_matvec_batch(c, R, xp, yp, true));
+    if (ptr_kind == EFIE_PTR_HOST)
+      EFIE_CUDA(cudaMemcpyAsync(yr, dout, 16 * S * R, cudaMemcpyDeviceToHost, c->stream));
+  }
+  EFIE_CUDA(cudaStreamSynchronize(c->stream));
+  collect_timings(c);
+  return m2l_tc_check(c);
 }
 
 efie_status efie_rhs_plane_waves(efie_ctx *ctx, int nrhs, const double *dir, const double *pol, double *g,
@@ -467,7 +507,10 @@ efie_status efie_rhs_plane_waves(efie_ctx *ctx, int nrhs, const double *dir, con
     double2 *gr = reinterpret_cast<double2 *>(g) + r * N;
     double2 *dst = ptr_kind == EFIE_PTR_HOST ? c->d_y : gr;
     EFIE_TRY(dev_rhs(c, dir + 3 * r, pol + 3 * r, dst));
-    if (ptr_kind == EFIE_PTR_HOST) EFIE_CUDA(cudaMemcpy(gr, c->d_y, 16 * N, cudaMemcpyDeviceToHost));
+    if (ptr_kind == EFIE_PTR_HOST) {
+      EFIE_CUDA(cudaMemcpyAsync(gr, c->d_y, 16 * N, cudaMemcpyDeviceToHost, c->stream));
+      EFIE_CUDA(cudaStreamSynchronize(c->stream));
+    }
   }
   return EFIE_OK;
 }
@@ -489,15 +532,9 @@ static efie_status solve_batched(Ctx *c, int nrhs, const double *b, double *x, i
   chunk = std::min(chunk, nrhs);
   EFIE_TRY(dev_batch_alloc(c, chunk));
   double2 *d_bb = nullptr, *d_xx = nullptr;
-  struct Guard {
-    double2 **a, **b;
-    ~Guard() {
-      if (*a) cudaFree(*a);
-      if (*b) cudaFree(*b);
-    }
-  } guard{&d_bb, &d_xx};
-  EFIE_TRY(dalloc(c, &d_bb, (size_t)chunk * N));
-  if (ptr_kind == EFIE_PTR_HOST) EFIE_TRY(dalloc(c, &d_xx, (size_t)chunk * N));
+  DevTemp tmp;
+  EFIE_TRY(tmp.get(c, &d_bb, (size_t)chunk * N));
+  if (ptr_kind == EFIE_PTR_HOST) EFIE_TRY(tmp.get(c, &d_xx, (size_t)chunk * N));
   std::vector<const double2 *> bp(chunk);
   std::vector<double2 *> xp(chunk);
   std::vector<int> its(chunk), conv(chunk);
@@ -611,7 +648,8 @@ efie_status efie_far_field(efie_ctx *ctx, int nrhs, const double *w, int ndir, c
   cudaSetDevice(c->device);
   const size_t N = c->ndof;
   double2 *d_out = nullptr;
-  EFIE_TRY(dalloc(c, &d_out, 3 * (size_t)ndir));
+  DevTemp tmp;
+  EFIE_TRY(tmp.get(c, &d_out, 3 * (size_t)ndir));
   for (int r = 0; r < nrhs; ++r) {
     const double2 *wr = reinterpret_cast<const double2 *>(w) + r * N;
     double2 *er = reinterpret_cast<double2 *>(e_inf) + (size_t)r * ndir * 3;
@@ -621,9 +659,11 @@ efie_status efie_far_field(efie_ctx *ctx, int nrhs, const double *w, int ndir, c
       src = c->d_x;
     }
     EFIE_TRY(dev_far_field(c, src, ndir, dirs, ptr_kind == EFIE_PTR_HOST ? d_out : er));
-    if (ptr_kind == EFIE_PTR_HOST) EFIE_CUDA(cudaMemcpy(er, d_out, 48 * (size_t)ndir, cudaMemcpyDeviceToHost));
+    if (ptr_kind == EFIE_PTR_HOST) {
+      EFIE_CUDA(cudaMemcpyAsync(er, d_out, 48 * (size_t)ndir, cudaMemcpyDeviceToHost, c->stream));
+      EFIE_CUDA(cudaStreamSynchronize(c->stream));
+    }
   }
-  cudaFree(d_out);
   return EFIE_OK;
 }
 
@@ -638,7 +678,8 @@ efie_status efie_exterior_field(efie_ctx *ctx, int nrhs, const double *w, int np
   cudaSetDevice(c->device);
   const size_t N = c->ndof;
   double2 *d_out = nullptr;
-  EFIE_TRY(dalloc(c, &d_out, 3 * (size_t)npts));
+  DevTemp tmp;
+  EFIE_TRY(tmp.get(c, &d_out, 3 * (size_t)npts));
   for (int r = 0; r < nrhs; ++r) {
     const double2 *wr = reinterpret_cast<const double2 *>(w) + r * N;
     double2 *er = reinterpret_cast<double2 *>(e_out) + (size_t)r * npts * 3;
@@ -648,9 +689,11 @@ efie_status efie_exterior_field(efie_ctx *ctx, int nrhs, const double *w, int np
       src = c->d_x;
     }
     EFIE_TRY(dev_exterior_field(c, src, npts, pts, ptr_kind == EFIE_PTR_HOST ? d_out : er));
-    if (ptr_kind == EFIE_PTR_HOST) EFIE_CUDA(cudaMemcpy(er, d_out, 48 * (size_t)npts, cudaMemcpyDeviceToHost));
+    if (ptr_kind == EFIE_PTR_HOST) {
+      EFIE_CUDA(cudaMemcpyAsync(er, d_out, 48 * (size_t)npts, cudaMemcpyDeviceToHost, c->stream));
+      EFIE_CUDA(cudaStreamSynchronize(c->stream));
+    }
   }
-  cudaFree(d_out);
   return EFIE_OK;
 }
 
@@ -665,8 +708,29 @@ efie_status efie_rhs_dipole(efie_ctx *ctx, int nrhs, const double *x0, const dou
     double2 *gr = reinterpret_cast<double2 *>(g) + r * N;
     double2 *dst = ptr_kind == EFIE_PTR_HOST ? c->d_y : gr;
     EFIE_TRY(dev_rhs_dipole(c, x0 + 3 * r, p0 + 3 * r, dst));
-    if (ptr_kind == EFIE_PTR_HOST) EFIE_CUDA(cudaMemcpy(gr, c->d_y, 16 * N, cudaMemcpyDeviceToHost));
+    if (ptr_kind == EFIE_PTR_HOST) {
+      EFIE_CUDA(cudaMemcpyAsync(gr, c->d_y, 16 * N, cudaMemcpyDeviceToHost, c->stream));
+      EFIE_CUDA(cudaStreamSynchronize(c->stream));
+    }
   }
+  return EFIE_OK;
+}
+
+int efie_setup_timings(const efie_ctx *ctx, double *out, int n) {
+  const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+  if (!c || !out) return 0;
+  const double v[4] = {c->setup_ms, (double)c->near_quad_ms, (double)c->near_quad_points, (double)c->near_quad_pairs};
+  int k = n < 4 ? n : 4;
+  for (int i = 0; i < k; ++i) out[i] = v[i];
+  return k;
+}
+
+efie_status efie_device_bytes(const efie_ctx *ctx, int64_t *live, int64_t *peak) {
+  Ctx *c = reinterpret_cast<Ctx *>(const_cast<efie_ctx *>(ctx));
+  if (!c) return EFIE_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mem_mu);
+  if (live) *live = (int64_t)c->live_bytes;
+  if (peak) *peak = (int64_t)c->peak_bytes;
   return EFIE_OK;
 }
 

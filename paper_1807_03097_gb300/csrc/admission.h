@@ -1,8 +1,10 @@
 // Admission of the serving loop (host only, no CUDA): the device-memory estimate of a request
-// and the decision which queued request to start when a slot is free.  Among the `lookahead` oldest queued requests whose estimated device
-// footprint fits the remaining budget (any request fits when nothing runs), the one with the
-// least estimated work is chosen; the oldest is chosen once `passes` admissions have gone to
-// requests behind it.  Returns the queue index (0 = oldest) or -1 when none fits.
+// and the decision which queued request to start when a slot is free.  Among the `lookahead`
+// oldest queued requests whose estimated device footprint fits the remaining budget (any
+// request fits when nothing runs), the one with the least estimated work is chosen.  Once
+// `lookahead` admissions have gone to requests behind the oldest, the oldest is next: nothing
+// else is admitted until it fits, so that memory released by finishing requests is held for it
+// and its wait is bounded.  Returns the queue index (0 = oldest) or -1 when none may start.
 #pragma once
 #include <algorithm>
 #include <cstddef>
@@ -11,12 +13,14 @@ namespace efie {
 
 // Device memory of one scattering request, estimated from the discretisation before anything
 // is built: near-field blocks (about 30 neighbours per element, FP64 plus an FP32 copy in the
-// mixed form), the Krylov bases, cluster data and work vectors.  In the mixed form the
-// directions of a request are solved in lockstep (up to 64 at a time), each with its own
-// Krylov basis, and the batched product holds per-direction superspace vectors and cluster
-// fields.  np patches, 2^level_m elements per patch direction, degree p, interpolation degree q.
+// mixed form), the Krylov bases, cluster data and work vectors, and the far-field scratch of
+// ndir directions (3 complex values per element and direction, plus the output).  In the
+// mixed form the directions of a request are solved in lockstep (up to 64 at a time), each
+// with its own Krylov basis, and the batched product holds per-direction superspace vectors
+// and cluster fields.  np patches, 2^level_m elements per patch direction, degree p,
+// interpolation degree q.
 inline size_t request_footprint(int np, int level_m, int p, int q, int gmres_restart, int gmres_maxit, bool mixed,
-                                int nrhs) {
+                                int nrhs, int ndir = 0) {
   const size_t n = size_t(1) << level_m, nE = size_t(np) * n * n;
   const size_t p1 = p + 1, nb = 2 * p1 * p1, nI = size_t(q + 1) * (q + 1);
   const size_t ndof = 2 * size_t(np) * (n + p - 1) * (n + p - 1);
@@ -28,14 +32,15 @@ inline size_t request_footprint(int np, int level_m, int p, int q, int gmres_res
   const size_t clusters = ncl * nI * (72 + 14 * 16);
   const size_t vecs = nE * nb * 16 * 6 + ndof * 16 * 8;
   const size_t batch = lockstep > 1 ? lockstep * (5 * nE * nb * 16 + 14 * ncl * nI * 8 + 4 * ndof * 16) : 0;
-  return near + krylov + clusters + vecs + batch + (size_t(64) << 20);
+  const size_t farfield = ndir > 0 ? 48 * size_t(ndir) * nE + 48 * size_t(ndir) + 24 * size_t(ndir) : 0;
+  return near + krylov + clusters + vecs + batch + farfield + (size_t(64) << 20);
 }
 
 inline int pick_admission(int nqueued, const size_t *footprint, const double *cost, int oldest_passed, size_t left,
                           bool idle, int lookahead) {
   auto fits = [&](int i) { return footprint[i] <= left || idle; };
   if (nqueued <= 0) return -1;
-  if (oldest_passed >= lookahead && fits(0)) return 0;
+  if (oldest_passed >= lookahead) return fits(0) ? 0 : -1;
   int best = -1;
   for (int i = 0; i < nqueued && i < lookahead; ++i)
     if (fits(i) && (best < 0 || cost[i] < cost[best])) best = i;

@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/efie.h"
@@ -144,11 +146,22 @@ struct Ctx {
   double *h_res = nullptr;    // pinned host mirror of the residual estimate
   int part_cap = 0;
 
+  // device memory of this context (stream-ordered pool allocations, devmem.cpp)
+  std::mutex mem_mu;
+  std::unordered_map<void *, size_t> live;
+  size_t live_bytes = 0, peak_bytes = 0;
+  bool pool_held = false;
+
   bool setup_done = false;
   long long launches = 0;  // kernels launched by this context (all phases)
   Timers tm;
   float last_ms[7] = {0, 0, 0, 0, 0, 0, 0};
   double setup_ms = 0.0;
+  // near-field quadrature of the last setup: kernel time (CUDA events), quadrature points
+  // evaluated (parts x g^4 summed over the pairs integrated), pairs integrated
+  float near_quad_ms = 0.f;
+  long long near_quad_points = 0;
+  int near_quad_pairs = 0;
   efie_solve_info info{};
   std::string err;
 };
@@ -175,7 +188,8 @@ efie_status dev_alloc_work(Ctx *c);
 efie_status dev_near_blocks_f32(Ctx *c);
 efie_status dev_near_apply_batch(Ctx *c, int R, const double2 *xs, double2 *ysn, size_t vstride, cudaStream_t st);
 // Y[r] = A X[r] for r < R (host arrays of device pointers); one pass in the mixed form
-efie_status dev_matvec_batch(Ctx *c, int R, const double2 *const *X, double2 *const *Y);
+// superspace: X[r], Y[r] are superspace vectors and Y[r] = (N + F) X[r]
+efie_status dev_matvec_batch(Ctx *c, int R, const double2 *const *X, double2 *const *Y, bool superspace = false);
 // R independent GMRES solves advanced in lockstep, one batched matvec per step
 size_t gmres_batch_bytes_per_system(const Ctx *c);
 // tensor-core M2L of a batch (m2l_tc.cu)
@@ -205,44 +219,50 @@ efie_status dev_gmres_batch(Ctx *c, int R, const double2 *const *b, double2 *con
     if (s_ < 0) return s_;         \
   } while (0)
 
+// Device memory (devmem.cpp): stream-ordered allocations on the context's stream from one pool
+// per device, counted per context.  pool_ref / pool_unref bracket the lifetime of a context or
+// a server on a device; pinned_get / pinned_put hand out reusable pinned host buffers.
+efie_status pool_ref(int dev);
+void pool_unref(int dev);
+efie_status pool_alloc(Ctx *c, void **p, size_t bytes);
+void pool_free(Ctx *c, void *p);  // stream-ordered on c->stream
+void *pinned_get(size_t bytes);
+void pinned_put(void *p);
+
 template <class T>
-inline efie_status dalloc(Ctx *c, T **p, size_t count) {
-  if (*p) {
-    cudaFree(*p);
-    *p = nullptr;
-  }
-  if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
-  if (e != cudaSuccess) {
-    c->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
-    *p = nullptr;
-    return EFIE_ENOMEM;
-  }
-  return EFIE_OK;
+inline void dfree(Ctx *c, T *&p) {
+  if (p) pool_free(c, (void *)p);
+  p = nullptr;
 }
 
-// Temporary device buffers of one call, freed when the owner goes out of scope (also on the
-// early returns of EFIE_TRY / EFIE_CUDA).  cudaFree waits for work in flight on the device.
+template <class T>
+inline efie_status dalloc(Ctx *c, T **p, size_t count) {
+  dfree(c, *p);
+  void *q = nullptr;
+  efie_status s = pool_alloc(c, &q, (count ? count : 1) * sizeof(T));
+  *p = static_cast<T *>(q);
+  return s;
+}
+
+// Temporary device buffers of one call, returned to the pool (in stream order) when the owner
+// goes out of scope, also on the early returns of EFIE_TRY / EFIE_CUDA.
 struct DevTemp {
+  Ctx *c = nullptr;
   std::vector<void *> p;
   DevTemp() = default;
   DevTemp(const DevTemp &) = delete;
   DevTemp &operator=(const DevTemp &) = delete;
   ~DevTemp() {
-    for (void *q : p) cudaFree(q);
+    for (void *q : p) pool_free(c, q);
   }
   template <class T>
-  efie_status get(Ctx *c, T **out, size_t n) {
+  efie_status get(Ctx *ctx, T **out, size_t n) {
+    c = ctx;
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, (n ? n : 1) * sizeof(T));
-    if (e != cudaSuccess) {
-      c->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
-      *out = nullptr;
-      return EFIE_ENOMEM;
-    }
-    p.push_back(q);
+    efie_status s = pool_alloc(ctx, &q, (n ? n : 1) * sizeof(T));
     *out = static_cast<T *>(q);
-    return EFIE_OK;
+    if (s == EFIE_OK) p.push_back(q);
+    return s;
   }
 };
 

@@ -822,8 +822,7 @@ static efie_status launch_m2l_stored(Ctx *c, cudaStream_t st, bool f32) {
 
 // Decide whether the coupling matrices are kept (m2l_store option) and evaluate them.
 static efie_status m2l_store_matrices(Ctx *c) {
-  if (c->d_K) cudaFree(c->d_K);
-  c->d_K = nullptr;
+  dfree(c, c->d_K);
   c->k_stored = false;
   if (c->nfar == 0 || c->opt.m2l_store == 1) return EFIE_OK;
   const bool f32 = c->opt.precision == EFIE_MIXED_FP32;
@@ -835,8 +834,7 @@ static efie_status m2l_store_matrices(Ctx *c) {
   // bottleneck of that form on this GPU, while the FP32 form evaluates faster than HBM can
   // stream the stored matrices)
   if (c->opt.m2l_store == 0 && (f32 || bytes > freeb / 2)) return EFIE_OK;
-  if (cudaMalloc(&c->d_K, bytes) != cudaSuccess) {
-    cudaGetLastError();
+  if (pool_alloc(c, &c->d_K, bytes) != EFIE_OK) {
     c->d_K = nullptr;
     if (c->opt.m2l_store == 2) {
       c->err = "coupling matrices do not fit in device memory";
@@ -882,14 +880,15 @@ static efie_status m2l_f32_attrs(int bytes) {
 static efie_status m2l_f32_tables(Ctx *c) {
   const size_t n = (size_t)c->ncl * c->nI;
   std::vector<float> xf(3 * n);
-  EFIE_CUDA(cudaMemcpy(xf.data(), c->d_nodeXf, 12 * n, cudaMemcpyDeviceToHost));
+  EFIE_CUDA(cudaMemcpyAsync(xf.data(), c->d_nodeXf, 12 * n, cudaMemcpyDeviceToHost, c->stream));
+  EFIE_CUDA(cudaStreamSynchronize(c->stream));
   std::vector<float4> x4(n);
   for (size_t i = 0; i < n; ++i) x4[i] = make_float4(xf[3 * i], xf[3 * i + 1], xf[3 * i + 2], 0.f);
   EFIE_TRY(dalloc(c, &c->d_nodeX4, n));
-  EFIE_CUDA(cudaMemcpy(c->d_nodeX4, x4.data(), 16 * n, cudaMemcpyHostToDevice));
+  EFIE_CUDA(cudaMemcpyAsync(c->d_nodeX4, x4.data(), 16 * n, cudaMemcpyHostToDevice, c->stream));
   EFIE_TRY(dalloc(c, &c->d_pgeo, (size_t)std::max(c->nfar, 1)));
   EFIE_TRY(dalloc(c, &c->d_pph, (size_t)std::max(c->nfar, 1)));
-  EFIE_CUDA(cudaDeviceSynchronize());
+  EFIE_CUDA(cudaStreamSynchronize(c->stream));
   if (c->n_m2l_targets > 0) {
     k_pair_table<<<(c->n_m2l_targets + 127) / 128, 128, 0, c->stream>>>(c->n_m2l_targets, c->d_m2l_targets,
                                                                         c->d_far_ptr, c->d_far_src, c->d_center,
@@ -1029,12 +1028,12 @@ efie_status dev_alloc_work(Ctx *c) {
   EFIE_TRY(dalloc(c, &c->d_ys, c->nsup));
   EFIE_TRY(dalloc(c, &c->d_ysn, c->nsup));
   EFIE_TRY(dalloc(c, &c->d_acc, ncl * 4 * nI));
-  EFIE_CUDA(cudaMemset(c->d_acc, 0, sizeof(double2) * ncl * 4 * nI));
+  EFIE_CUDA(cudaMemsetAsync(c->d_acc, 0, sizeof(double2) * ncl * 4 * nI, c->stream));
   if (c->opt.precision == EFIE_MIXED_FP32) {
     EFIE_TRY(dalloc(c, &c->d_momf, ncl * 3 * nI));
     EFIE_TRY(dalloc(c, &c->d_srcf, ncl * 2 * nI));
     EFIE_TRY(dalloc(c, &c->d_accf, ncl * 2 * nI));
-    EFIE_CUDA(cudaMemset(c->d_accf, 0, sizeof(float4) * ncl * 2 * nI));
+    EFIE_CUDA(cudaMemsetAsync(c->d_accf, 0, sizeof(float4) * ncl * 2 * nI, c->stream));
     EFIE_TRY(dalloc(c, &c->d_locf, ncl * 3 * nI));
     EFIE_TRY(m2l_f32_tables(c));
   } else {
@@ -1045,10 +1044,10 @@ efie_status dev_alloc_work(Ctx *c) {
   EFIE_TRY(dalloc(c, &c->d_M, c->q1 * c->p1));
   EFIE_TRY(dalloc(c, &c->d_Md, c->q1 * c->p1));
   EFIE_TRY(dalloc(c, &c->d_E, 2 * c->q1 * c->q1));
-  EFIE_CUDA(cudaMemcpy(c->d_M, c->tab.M.data(), 8 * c->tab.M.size(), cudaMemcpyHostToDevice));
-  EFIE_CUDA(cudaMemcpy(c->d_Md, c->tab.Md.data(), 8 * c->tab.Md.size(), cudaMemcpyHostToDevice));
-  EFIE_CUDA(cudaMemcpy(c->d_E, c->tab.E.data(), 8 * c->tab.E.size(), cudaMemcpyHostToDevice));
-  EFIE_CUDA(cudaDeviceSynchronize());
+  EFIE_CUDA(cudaMemcpyAsync(c->d_M, c->tab.M.data(), 8 * c->tab.M.size(), cudaMemcpyHostToDevice, c->stream));
+  EFIE_CUDA(cudaMemcpyAsync(c->d_Md, c->tab.Md.data(), 8 * c->tab.Md.size(), cudaMemcpyHostToDevice, c->stream));
+  EFIE_CUDA(cudaMemcpyAsync(c->d_E, c->tab.E.data(), 8 * c->tab.E.size(), cudaMemcpyHostToDevice, c->stream));
+  EFIE_CUDA(cudaStreamSynchronize(c->stream));
   EFIE_TRY(dev_set_kernel_attrs(c));
   return m2l_store_matrices(c);
 }
@@ -1219,7 +1218,7 @@ efie_status dev_batch_alloc(Ctx *c, int R) {
   EFIE_TRY(dalloc(c, &c->d_momB, (size_t)R * ncl * 3 * nI));
   EFIE_TRY(dalloc(c, &c->d_srcB, (size_t)R * ncl * 4 * nI));
   EFIE_TRY(dalloc(c, &c->d_accB, (size_t)R * ncl * 4 * nI));
-  EFIE_CUDA(cudaMemset(c->d_accB, 0, sizeof(float2) * (size_t)R * ncl * 4 * nI));
+  EFIE_CUDA(cudaMemsetAsync(c->d_accB, 0, sizeof(float2) * (size_t)R * ncl * 4 * nI, c->stream));
   EFIE_TRY(dalloc(c, &c->d_locB, (size_t)R * ncl * 3 * nI));
   if (c->opt.precision == EFIE_MIXED_FP32 && m2l_tc_supported(c)) EFIE_TRY(m2l_tc_prepare(c));
   const int sm = (int)multi_smem(kMultiMaxNI);
@@ -1230,10 +1229,16 @@ efie_status dev_batch_alloc(Ctx *c, int R) {
   return EFIE_OK;
 }
 
-// Y[r] = A X[r], r < R (host arrays of device pointers).
-efie_status dev_matvec_batch(Ctx *c, int R, const double2 *const *X, double2 *const *Y) {
+__global__ void k_sum2(size_t n, const double2 *__restrict__ a, const double2 *__restrict__ b, double2 *__restrict__ y) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = make_double2(a[i].x + b[i].x, a[i].y + b[i].y);
+}
+
+// Y[r] = A X[r], r < R (host arrays of device pointers).  superspace: X[r] and Y[r] are
+// superspace vectors and the product is (N + F) X[r] (no T gather / scatter).
+efie_status dev_matvec_batch(Ctx *c, int R, const double2 *const *X, double2 *const *Y, bool superspace) {
   if (c->opt.precision != EFIE_MIXED_FP32 || R == 1 || (c->nI > kMultiMaxNI && !m2l_tc_supported(c))) {
-    for (int r = 0; r < R; ++r) EFIE_TRY(dev_matvec(c, X[r], Y[r]));
+    for (int r = 0; r < R; ++r) EFIE_TRY(superspace ? dev_matvec_super(c, X[r], Y[r]) : dev_matvec(c, X[r], Y[r]));
     return EFIE_OK;
   }
   EFIE_TRY(dev_batch_alloc(c, R));
@@ -1246,8 +1251,12 @@ efie_status dev_matvec_batch(Ctx *c, int R, const double2 *const *X, double2 *co
   const size_t mstride = (size_t)c->ncl * 3 * nI;
   for (int r = 0; r < R; ++r) {
     double2 *xs = c->d_xsB + (size_t)r * c->nsup;
-    k_gather<<<(c->nsup + 255) / 256, 256, 0, st>>>(c->nsup, c->d_tg_ptr, c->d_tg_col, c->d_tg_val,
-                                                    X[r], xs); ++c->launches;
+    if (superspace) {
+      EFIE_CUDA(cudaMemcpyAsync(xs, X[r], sizeof(double2) * c->nsup, cudaMemcpyDeviceToDevice, st));
+    } else {
+      k_gather<<<(c->nsup + 255) / 256, 256, 0, st>>>(c->nsup, c->d_tg_ptr, c->d_tg_col, c->d_tg_val,
+                                                      X[r], xs); ++c->launches;
+    }
   }
   EFIE_CUDA(cudaEventRecord(c->tm.ev[1], st));
   EFIE_CUDA(cudaEventRecord(c->fork, st));
@@ -1303,9 +1312,14 @@ efie_status dev_matvec_batch(Ctx *c, int R, const double2 *const *X, double2 *co
   EFIE_CUDA(cudaEventRecord(c->tm.ev[5], st));
   EFIE_CUDA(cudaStreamWaitEvent(st, c->join, 0));
   for (int r = 0; r < R; ++r) {
-    k_scatter<<<(c->ndof + 255) / 256, 256, 0, st>>>(c->ndof, c->d_ts_ptr, c->d_ts_col, c->d_ts_val,
-                                                     c->d_ysB + (size_t)r * c->nsup, c->d_ysnB + (size_t)r * c->nsup,
-                                                     Y[r]); ++c->launches;
+    if (superspace) {
+      k_sum2<<<(c->nsup + 255) / 256, 256, 0, st>>>((size_t)c->nsup, c->d_ysB + (size_t)r * c->nsup,
+                                                    c->d_ysnB + (size_t)r * c->nsup, Y[r]); ++c->launches;
+    } else {
+      k_scatter<<<(c->ndof + 255) / 256, 256, 0, st>>>(c->ndof, c->d_ts_ptr, c->d_ts_col, c->d_ts_val,
+                                                       c->d_ysB + (size_t)r * c->nsup,
+                                                       c->d_ysnB + (size_t)r * c->nsup, Y[r]); ++c->launches;
+    }
   }
   EFIE_CUDA(cudaEventRecord(c->tm.ev[6], st));
   EFIE_CUDA(cudaGetLastError());

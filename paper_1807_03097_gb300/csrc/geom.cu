@@ -41,10 +41,10 @@ efie_status dev_eval_points(Ctx *c, const std::vector<int> &patch, const std::ve
   EFIE_CUDA(cudaMemcpyAsync(X.data(), d_X, 24 * (size_t)npts, cudaMemcpyDeviceToHost, c->stream));
   if (D) EFIE_CUDA(cudaMemcpyAsync(D->data(), d_D, 48 * (size_t)npts, cudaMemcpyDeviceToHost, c->stream));
   EFIE_CUDA(cudaStreamSynchronize(c->stream));
-  cudaFree(d_pid);
-  cudaFree(d_st);
-  cudaFree(d_X);
-  if (d_D) cudaFree(d_D);
+  dfree(c, d_pid);
+  dfree(c, d_st);
+  dfree(c, d_X);
+  dfree(c, d_D);
   return EFIE_OK;
 }
 
@@ -134,9 +134,8 @@ efie_status dev_cluster_geometry(Ctx *c) {
   EFIE_TRY(dalloc(c, &d_lev, c->lev_off.size()));
   EFIE_TRY(dalloc(c, &d_ball, 4 * (size_t)c->ncl));
   EFIE_TRY(dalloc(c, &d_x, c->q1));
-  EFIE_CUDA(cudaMemcpy(d_lev, c->lev_off.data(), 4 * c->lev_off.size(), cudaMemcpyHostToDevice));
-  EFIE_CUDA(cudaMemcpy(d_x, c->tab.xcheb.data(), 8 * (size_t)c->q1, cudaMemcpyHostToDevice));
-  EFIE_CUDA(cudaDeviceSynchronize());
+  EFIE_CUDA(cudaMemcpyAsync(d_lev, c->lev_off.data(), 4 * c->lev_off.size(), cudaMemcpyHostToDevice, c->stream));
+  EFIE_CUDA(cudaMemcpyAsync(d_x, c->tab.xcheb.data(), 8 * (size_t)c->q1, cudaMemcpyHostToDevice, c->stream));
   k_cluster_balls<<<c->ncl, 128, 0, c->stream>>>(c->d_patches, c->d_knots, c->d_cpw, d_lev, nlev, c->ncl, d_ball); ++c->launches;
   EFIE_CUDA(cudaGetLastError());
   c->ball.assign(4 * (size_t)c->ncl, 0.0);
@@ -152,9 +151,9 @@ efie_status dev_cluster_geometry(Ctx *c) {
   EFIE_CUDA(cudaGetLastError());
   EFIE_CUDA(cudaMemcpyAsync(c->d_center, d_ball, 32 * (size_t)c->ncl, cudaMemcpyDeviceToDevice, c->stream));
   EFIE_CUDA(cudaStreamSynchronize(c->stream));
-  cudaFree(d_lev);
-  cudaFree(d_ball);
-  cudaFree(d_x);
+  dfree(c, d_lev);
+  dfree(c, d_ball);
+  dfree(c, d_x);
   return EFIE_OK;
 }
 

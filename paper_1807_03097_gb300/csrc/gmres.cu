@@ -233,7 +233,11 @@ efie_status dev_gmres(Ctx *c, const double2 *b, double2 *x, int *its_out, double
     EFIE_TRY(dalloc(c, &c->d_r, N));
     EFIE_TRY(dalloc(c, &c->d_sol, (size_t)kr + 1));
   }
-  if (!c->h_res) EFIE_CUDA(cudaMallocHost((void **)&c->h_res, 4 * sizeof(double)));
+  if (!c->h_res) c->h_res = static_cast<double *>(pinned_get(4 * sizeof(double)));
+  if (!c->h_res) {
+    c->err = "pinned host buffer: cudaMallocHost failed";
+    return EFIE_ENOMEM;
+  }
   double2 *V = c->d_V;
   const int blk = 256, grid = (N + blk - 1) / blk;
   // ||b||
@@ -371,10 +375,13 @@ efie_status dev_gmres_batch(Ctx *c, int R, const double2 *const *b, double2 *con
     EFIE_TRY(mem.get(c, &s.gs, (size_t)2 + 5 * kr + 2));
   }
   if (c->h_resB_cap < 4 * R) {
-    if (c->h_resB) cudaFreeHost(c->h_resB);
-    c->h_resB = nullptr;
+    pinned_put(c->h_resB);
     c->h_resB_cap = 0;
-    EFIE_CUDA(cudaMallocHost((void **)&c->h_resB, 4 * R * sizeof(double)));
+    c->h_resB = static_cast<double *>(pinned_get(4 * R * sizeof(double)));
+    if (!c->h_resB) {
+      c->err = "pinned host buffer: cudaMallocHost failed";
+      return EFIE_ENOMEM;
+    }
     c->h_resB_cap = 4 * R;
   }
   double *hr = c->h_resB;

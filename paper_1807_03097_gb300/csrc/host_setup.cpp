@@ -323,13 +323,13 @@ efie_status host_build_space(Ctx *c, const std::vector<double> &edge_pts, const 
   EFIE_TRY(dalloc(c, &c->d_ts_ptr, sptr.size()));
   EFIE_TRY(dalloc(c, &c->d_ts_col, scol.size()));
   EFIE_TRY(dalloc(c, &c->d_ts_val, sval.size()));
-  EFIE_CUDA(cudaMemcpy(c->d_tg_ptr, gptr.data(), gptr.size() * 4, cudaMemcpyHostToDevice));
-  EFIE_CUDA(cudaMemcpy(c->d_tg_col, cols.data(), cols.size() * 4, cudaMemcpyHostToDevice));
-  EFIE_CUDA(cudaMemcpy(c->d_tg_val, vals.data(), vals.size() * 8, cudaMemcpyHostToDevice));
-  EFIE_CUDA(cudaMemcpy(c->d_ts_ptr, sptr.data(), sptr.size() * 4, cudaMemcpyHostToDevice));
-  EFIE_CUDA(cudaMemcpy(c->d_ts_col, scol.data(), scol.size() * 4, cudaMemcpyHostToDevice));
-  EFIE_CUDA(cudaMemcpy(c->d_ts_val, sval.data(), sval.size() * 8, cudaMemcpyHostToDevice));
-  EFIE_CUDA(cudaDeviceSynchronize());  // pageable uploads complete before stream work reads them
+  EFIE_CUDA(cudaMemcpyAsync(c->d_tg_ptr, gptr.data(), gptr.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  EFIE_CUDA(cudaMemcpyAsync(c->d_tg_col, cols.data(), cols.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  EFIE_CUDA(cudaMemcpyAsync(c->d_tg_val, vals.data(), vals.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  EFIE_CUDA(cudaMemcpyAsync(c->d_ts_ptr, sptr.data(), sptr.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  EFIE_CUDA(cudaMemcpyAsync(c->d_ts_col, scol.data(), scol.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  EFIE_CUDA(cudaMemcpyAsync(c->d_ts_val, sval.data(), sval.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  EFIE_CUDA(cudaStreamSynchronize(c->stream));
   return EFIE_OK;
 }
 
@@ -398,14 +398,14 @@ efie_status host_build_trees(Ctx *c) {
   for (int k = 0; k < c->ncl; ++k)
     for (int f = fptr[k]; f < fptr[k + 1]; ++f) ftgt[f] = k;
   EFIE_TRY(dalloc(c, &c->d_far_tgt, ftgt.size()));
-  EFIE_CUDA(cudaMemcpy(c->d_far_tgt, ftgt.data(), ftgt.size() * 4, cudaMemcpyHostToDevice));
+  EFIE_CUDA(cudaMemcpyAsync(c->d_far_tgt, ftgt.data(), ftgt.size() * 4, cudaMemcpyHostToDevice, c->stream));
   EFIE_TRY(dalloc(c, &c->d_far_ptr, fptr.size()));
   EFIE_TRY(dalloc(c, &c->d_far_src, fsrc.size()));
   EFIE_TRY(dalloc(c, &c->d_m2l_targets, targets.size()));
-  EFIE_CUDA(cudaMemcpy(c->d_far_ptr, fptr.data(), fptr.size() * 4, cudaMemcpyHostToDevice));
-  if (c->nfar) EFIE_CUDA(cudaMemcpy(c->d_far_src, fsrc.data(), fsrc.size() * 4, cudaMemcpyHostToDevice));
+  EFIE_CUDA(cudaMemcpyAsync(c->d_far_ptr, fptr.data(), fptr.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  if (c->nfar) EFIE_CUDA(cudaMemcpyAsync(c->d_far_src, fsrc.data(), fsrc.size() * 4, cudaMemcpyHostToDevice, c->stream));
   if (!targets.empty())
-    EFIE_CUDA(cudaMemcpy(c->d_m2l_targets, targets.data(), targets.size() * 4, cudaMemcpyHostToDevice));
+    EFIE_CUDA(cudaMemcpyAsync(c->d_m2l_targets, targets.data(), targets.size() * 4, cudaMemcpyHostToDevice, c->stream));
 
   // near pairs as CSR over target elements; near_perm maps CSR slots to list entries
   std::vector<int> nptr(c->nE + 1, 0), nsrc(c->nnear);
@@ -422,9 +422,9 @@ efie_status host_build_trees(Ctx *c) {
   }
   EFIE_TRY(dalloc(c, &c->d_near_ptr, nptr.size()));
   EFIE_TRY(dalloc(c, &c->d_near_src, nsrc.size()));
-  EFIE_CUDA(cudaMemcpy(c->d_near_ptr, nptr.data(), nptr.size() * 4, cudaMemcpyHostToDevice));
-  if (c->nnear) EFIE_CUDA(cudaMemcpy(c->d_near_src, nsrc.data(), nsrc.size() * 4, cudaMemcpyHostToDevice));
-  EFIE_CUDA(cudaDeviceSynchronize());
+  EFIE_CUDA(cudaMemcpyAsync(c->d_near_ptr, nptr.data(), nptr.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  if (c->nnear) EFIE_CUDA(cudaMemcpyAsync(c->d_near_src, nsrc.data(), nsrc.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  EFIE_CUDA(cudaStreamSynchronize(c->stream));
   return EFIE_OK;
 }
 

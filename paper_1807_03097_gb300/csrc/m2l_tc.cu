@@ -357,8 +357,8 @@ efie_status m2l_tc_prepare(Ctx *c) {
   EFIE_TRY(tc_attrs<96>());
   EFIE_TRY(tc_attrs<128>());
   if (!c->d_tc_err) {
-    EFIE_CUDA(cudaMalloc((void **)&c->d_tc_err, sizeof(int)));
-    EFIE_CUDA(cudaMemset(c->d_tc_err, 0, sizeof(int)));
+    EFIE_TRY(dalloc(c, &c->d_tc_err, 1));
+    EFIE_CUDA(cudaMemsetAsync(c->d_tc_err, 0, sizeof(int), c->stream));
   }
   return EFIE_OK;
 }

@@ -234,21 +234,21 @@ efie_status dev_near_quadrature(Ctx *c, const std::vector<NearPair> &pairs, cons
   EFIE_TRY(dalloc(c, &d_src_of, src_of.size()));
   EFIE_TRY(dalloc(c, &d_rule, 2 * (size_t)(c->gr + c->gs)));
   EFIE_TRY(dalloc(c, &d_slot, slot.size()));
-  EFIE_CUDA(cudaMemcpy(d_slot, slot.data(), 4 * slot.size(), cudaMemcpyHostToDevice));
-  EFIE_CUDA(cudaMemcpy(d_pairs, pairs.data(), sizeof(NearPair) * pairs.size(), cudaMemcpyHostToDevice));
-  EFIE_CUDA(cudaMemcpy(d_todo, todo.data(), 4 * todo.size(), cudaMemcpyHostToDevice));
+  cudaStream_t s0 = c->stream;
+  EFIE_CUDA(cudaMemcpyAsync(d_slot, slot.data(), 4 * slot.size(), cudaMemcpyHostToDevice, s0));
+  EFIE_CUDA(cudaMemcpyAsync(d_pairs, pairs.data(), sizeof(NearPair) * pairs.size(), cudaMemcpyHostToDevice, s0));
+  EFIE_CUDA(cudaMemcpyAsync(d_todo, todo.data(), 4 * todo.size(), cudaMemcpyHostToDevice, s0));
   if (!todo_m.empty()) {
-    EFIE_CUDA(cudaMemcpy(d_todo_m, todo_m.data(), 4 * todo_m.size(), cudaMemcpyHostToDevice));
-    EFIE_CUDA(cudaMemcpy(d_src_of, src_of.data(), 4 * src_of.size(), cudaMemcpyHostToDevice));
+    EFIE_CUDA(cudaMemcpyAsync(d_todo_m, todo_m.data(), 4 * todo_m.size(), cudaMemcpyHostToDevice, s0));
+    EFIE_CUDA(cudaMemcpyAsync(d_src_of, src_of.data(), 4 * src_of.size(), cudaMemcpyHostToDevice, s0));
   }
   std::vector<double> rule;
   rule.insert(rule.end(), c->tab.gx.begin(), c->tab.gx.end());
   rule.insert(rule.end(), c->tab.gw.begin(), c->tab.gw.end());
   rule.insert(rule.end(), c->tab.sx.begin(), c->tab.sx.end());
   rule.insert(rule.end(), c->tab.sw.begin(), c->tab.sw.end());
-  EFIE_CUDA(cudaMemcpy(d_rule, rule.data(), 8 * rule.size(), cudaMemcpyHostToDevice));
+  EFIE_CUDA(cudaMemcpyAsync(d_rule, rule.data(), 8 * rule.size(), cudaMemcpyHostToDevice, s0));
   EFIE_TRY(dalloc(c, &c->d_nblk, (size_t)c->nnear * nb * nb));
-  EFIE_CUDA(cudaDeviceSynchronize());  // pageable uploads complete before stream work reads them
 
   QuadArgs A;
   A.patches = c->d_patches;
@@ -270,6 +270,14 @@ efie_status dev_near_quadrature(Ctx *c, const std::vector<NearPair> &pairs, cons
   A.h = 1.0 / c->n;
   A.blocks = c->d_nblk;
   size_t smem = sizeof(double) * (2 * kQC * 4 * (size_t)nb + 2 * kQC * 3 + 2 * kQC + kQC);
+  c->near_quad_pairs = (int)todo.size();
+  c->near_quad_points = 0;
+  for (int k : todo) {
+    const int kind = pairs[k].kind, g = kind == 0 ? c->gr : c->gs;
+    const int parts = kind == 0 ? 1 : (kind == 3 ? 8 : (kind == 2 ? 6 : 4));
+    c->near_quad_points += (long long)parts * g * g * g * g;
+  }
+  EFIE_CUDA(cudaEventRecord(c->tm.ev[7], c->stream));
   switch (c->p) {
 #define EFIE_QUAD_CASE(PP)                                                                          \
   case PP:                                                                                          \
@@ -288,6 +296,7 @@ efie_status dev_near_quadrature(Ctx *c, const std::vector<NearPair> &pairs, cons
       return EFIE_EINVAL;
   }
   EFIE_CUDA(cudaGetLastError());
+  EFIE_CUDA(cudaEventRecord(c->tm.ev[6], c->stream));
   if (!todo_m.empty()) {
     long long tot = (long long)todo_m.size() * nb * nb;
     k_near_mirror<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(nb, d_todo_m, d_src_of, d_slot,
@@ -295,12 +304,13 @@ efie_status dev_near_quadrature(Ctx *c, const std::vector<NearPair> &pairs, cons
     EFIE_CUDA(cudaGetLastError());
   }
   EFIE_CUDA(cudaStreamSynchronize(c->stream));
-  cudaFree(d_pairs);
-  cudaFree(d_todo);
-  cudaFree(d_todo_m);
-  cudaFree(d_src_of);
-  cudaFree(d_rule);
-  cudaFree(d_slot);
+  cudaEventElapsedTime(&c->near_quad_ms, c->tm.ev[7], c->tm.ev[6]);
+  dfree(c, d_pairs);
+  dfree(c, d_todo);
+  dfree(c, d_todo_m);
+  dfree(c, d_src_of);
+  dfree(c, d_rule);
+  dfree(c, d_slot);
   return EFIE_OK;
 }
 

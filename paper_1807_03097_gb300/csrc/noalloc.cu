@@ -161,6 +161,17 @@ extern "C" efie_status efie_far_field_noalloc(efie_ctx *ctx, const double *w_dev
     c->err = "efie_far_field_noalloc: 3 * ndir * ceil(elements / 16) exceeds the 2^18-entry scratch";
     return EFIE_EINVAL;
   }
+  if (ndir > 65535) {
+    c->err = "efie_far_field_noalloc: at most 65535 directions per call";
+    return EFIE_EINVAL;
+  }
+  // the caller's current device is put back on every return
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) return EFIE_ECUDA;
+  struct RestoreDevice {
+    int dev;
+    ~RestoreDevice() { cudaSetDevice(dev); }
+  } restore{prev};
   if (cudaSetDevice(c->device) != cudaSuccess) return EFIE_ECUDA;
   double2 *part = nullptr;
   EFIE_TRY(scratch_address(c->device, &part));

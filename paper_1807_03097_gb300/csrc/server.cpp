@@ -21,6 +21,11 @@
 #include "../../include/efie.h"
 #include "admission.h"
 
+namespace efie {
+efie_status pool_ref(int dev);  // devmem.cpp
+void pool_unref(int dev);
+}  // namespace efie
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
@@ -60,7 +65,7 @@ struct Server {
 
 size_t estimate_footprint(const Job &j) {
   return efie::request_footprint(j.np, j.opt.level_m, j.opt.p, j.opt.q, j.opt.gmres_restart, j.opt.gmres_maxit,
-                                 j.opt.precision == EFIE_MIXED_FP32, j.nrhs);
+                                 j.opt.precision == EFIE_MIXED_FP32, j.nrhs, j.ndir);
 }
 
 void run_job(Server *S, Job &j) {
@@ -87,7 +92,11 @@ void run_job(Server *S, Job &j) {
     efie_status s2 = efie_far_field(ctx, j.nrhs, j.w_out, j.ndir, j.ffdirs.data(), j.e_inf_out, EFIE_PTR_HOST);
     if (s2 < 0) st = s2;
   }
+  int64_t peak = 0;
+  if (ctx) efie_device_bytes(ctx, nullptr, &peak);
   efie_destroy(ctx);
+  r.device_peak_bytes = peak;
+  r.footprint_bytes = (int64_t)j.footprint;
   r.status = st;
   r.iterations = info.iterations;
   r.residual = info.residual;
@@ -157,6 +166,12 @@ efie_status efie_server_create(efie_server **out, size_t hbm_budget_bytes, int m
   S->device = dev;
   S->budget = hbm_budget_bytes;
   S->max_slots = max_slots;
+  // the device's memory pool lives as long as the server, so that memory a finished request
+  // returns is reused by the next one without going back to the driver
+  if (efie::pool_ref(dev) != EFIE_OK) {
+    delete S;
+    return EFIE_ECUDA;
+  }
   for (int i = 0; i < max_slots; ++i) S->workers.emplace_back(worker, S);
   *out = reinterpret_cast<efie_server *>(S);
   return EFIE_OK;
@@ -166,6 +181,10 @@ efie_status efie_server_submit(efie_server *srv, const efie_request *q, uint64_t
   Server *S = reinterpret_cast<Server *>(srv);
   if (!S || !q || !ticket || q->n_patches <= 0 || !q->deg || !q->ncp || !q->knots || !q->cp || !q->w ||
       q->nrhs <= 0 || !q->dir || !q->pol || !q->w_out || q->ndir < 0 || (q->ndir > 0 && (!q->ff_dirs || !q->e_inf_out)))
+    return EFIE_EINVAL;
+  // the options are checked here as efie_create checks them (the sizes below depend on them)
+  if (q->opt.level_m < 0 || q->opt.level_m > 10 || q->opt.p < 1 || q->opt.p > 4 || q->opt.q < 1 || q->opt.q > 16 ||
+      q->opt.gmres_restart < 1 || q->opt.gmres_maxit < 1)
     return EFIE_EINVAL;
   auto j = std::make_shared<Job>();
   j->np = q->n_patches;
@@ -232,6 +251,7 @@ efie_status efie_server_destroy(efie_server *srv) {
   }
   S->cv_work.notify_all();
   for (auto &t : S->workers) t.join();
+  efie::pool_unref(S->device);
   delete S;
   return EFIE_OK;
 }

@@ -27,6 +27,7 @@ ABI_SYMBOLS = (
     "efie_default_options", "efie_create", "efie_set_geometry", "efie_setup", "efie_num_dofs",
     "efie_matvec", "efie_rhs_plane_waves", "efie_solve", "efie_solve_plane_waves", "efie_far_field",
     "efie_block_counts", "efie_export_blocks", "efie_export_near_blocks", "efie_matvec_superspace",
+    "efie_matvec_superspace_batch", "efie_device_bytes", "efie_setup_timings",
     "efie_last_timings", "efie_launch_count", "efie_destroy", "efie_status_string", "efie_last_error", "efie_check_device_waits", "efie_exterior_field",
     "efie_rhs_dipole",
     "efie_far_field_noalloc",
@@ -57,7 +58,8 @@ class EfieRequest(ctypes.Structure):
 class EfieResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("residual", ctypes.c_double),
                 ("ndof", ctypes.c_int64), ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
-                ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+                ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("footprint_bytes", ctypes.c_int64), ("device_peak_bytes", ctypes.c_int64)]
 
 
 class EfieError(RuntimeError):
@@ -97,6 +99,9 @@ def load(path: str = LIB_PATH):
         "efie_export_blocks": (c_int, [P, I, I]),
         "efie_export_near_blocks": (c_int, [P, D]),
         "efie_matvec_superspace": (c_int, [P, P, P, c_int]),
+        "efie_matvec_superspace_batch": (c_int, [P, c_int, P, P, c_int]),
+        "efie_device_bytes": (c_int, [P, I64, I64]),
+        "efie_setup_timings": (c_int, [P, D, c_int]),
         "efie_last_timings": (c_int, [P, D, c_int]),
         "efie_launch_count": (ctypes.c_int64, [P]),
         "efie_far_field_noalloc": (c_int, [P, P, c_int, P, P]),
@@ -213,12 +218,24 @@ class Solver:
         return out
 
     def matvec_superspace(self, xs, out=None):
+        """ys = (N + F) xs for xs of shape (nsup,) or (nrhs, nsup) (several right-hand sides in
+        one batched pass)."""
         if out is None:
             out = np.empty_like(xs) if isinstance(xs, np.ndarray) else xs.new_empty(xs.shape)
         px, kx = _ptr(xs)
         py, _ = _ptr(out)
-        self._check(self._L.efie_matvec_superspace(self.h, px, py, kx), "efie_matvec_superspace")
+        if xs.ndim == 2:
+            self._check(self._L.efie_matvec_superspace_batch(self.h, xs.shape[0], px, py, kx),
+                        "efie_matvec_superspace_batch")
+        else:
+            self._check(self._L.efie_matvec_superspace(self.h, px, py, kx), "efie_matvec_superspace")
         return out
+
+    def device_bytes(self):
+        """(live, peak) bytes of device memory this context has allocated."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self._L.efie_device_bytes(self.h, ctypes.byref(a), ctypes.byref(b)), "efie_device_bytes")
+        return int(a.value), int(b.value)
 
     def rhs(self, dirs, pols, out=None):
         dirs = np.ascontiguousarray(dirs, float).reshape(-1, 3)
@@ -316,6 +333,13 @@ class Solver:
         EFIE_ETIMEOUT = -6) and efie_last_error's detail, without raising."""
         st = self._L.efie_check_device_waits(self.h, int(cycles))
         return st, self._L.efie_last_error(self.h).decode()
+
+    def setup_timings(self):
+        """Figures of the last setup: wall ms, near-field quadrature kernel ms, quadrature points,
+        element pairs integrated."""
+        out = np.zeros(4)
+        n = self._L.efie_setup_timings(self.h, _d(out), 4)
+        return dict(zip(["setup_ms", "near_quad_ms", "near_quad_points", "near_quad_pairs"], out[:n]))
 
     def last_timings(self):
         out = np.zeros(7)

@@ -50,8 +50,52 @@ int main() {
     double c[3] = {9, 1, 2};
     CHECK(pick_admission(3, fp, c, 8, 50, false, 8) == 0);
     CHECK(pick_admission(3, fp, c, 7, 50, false, 8) == 1);
+    // once passed 8 times the oldest is next even if it does not fit yet: nothing else starts
     size_t fp2[3] = {100, 10, 10};
-    CHECK(pick_admission(3, fp2, c, 8, 50, false, 8) == 1);
+    CHECK(pick_admission(3, fp2, c, 8, 50, false, 8) == -1);
+    CHECK(pick_admission(3, fp2, c, 7, 50, false, 8) == 1);
+    CHECK(pick_admission(3, fp2, c, 8, 100, false, 8) == 0);
+  }
+  {  // a large request behind a steady stream of small ones: the memory released by finishing
+     // requests is held for it, so it starts after a bounded number of releases
+    const size_t budget = 100;
+    size_t in_use = 0;
+    std::deque<std::pair<size_t, double>> q;
+    q.push_back({90, 1000.0});
+    std::deque<size_t> running;  // footprints of running requests, oldest first
+    int passed = 0, steps = 0;
+    bool started = false;
+    for (int i = 0; i < 200; ++i) q.push_back({30, 1.0});
+    while (!started && steps < 1000) {
+      ++steps;
+      // admit as many as fit (slots unlimited here), then one running request finishes
+      for (;;) {
+        size_t fp[8];
+        double c[8];
+        const int n = (int)std::min<size_t>(q.size(), 8);
+        for (int i = 0; i < n; ++i) {
+          fp[i] = q[i].first;
+          c[i] = q[i].second;
+        }
+        const int k = pick_admission(n, fp, c, passed, budget - in_use, running.empty(), 8);
+        if (k < 0) break;
+        if (k == 0) {
+          started = true;
+          break;
+        }
+        ++passed;
+        in_use += q[k].first;
+        running.push_back(q[k].first);
+        q.erase(q.begin() + k);
+      }
+      if (!started && !running.empty()) {
+        in_use -= running.front();
+        running.pop_front();
+      }
+    }
+    CHECK(started);
+    CHECK(passed == 8);
+    CHECK(steps < 20);
   }
   {  // a large request at the head of a stream of small ones is passed exactly 8 times
     std::deque<std::pair<size_t, double>> q;
@@ -89,6 +133,10 @@ int main() {
     CHECK(request_footprint(6, 5, 2, 8, 1500, 3000, false, 16) == f64);
     CHECK(request_footprint(6, 6, 2, 8, 1500, 3000, true, 1) > f32);
     CHECK(request_footprint(6, 5, 2, 8, 20, 3000, true, 1) < f32);  // shorter restart, smaller basis
+    // far-field scratch: 3 complex doubles per element and direction
+    const size_t nE = 6 * 32 * 32;
+    CHECK(request_footprint(6, 5, 2, 8, 1500, 3000, true, 1, 64) >= f32 + 48 * 64 * nE);
+    CHECK(request_footprint(6, 5, 2, 8, 1500, 3000, true, 1, 0) == f32);
   }
   if (failures == 0) std::printf("ok\n");
   return failures == 0 ? 0 : 1;

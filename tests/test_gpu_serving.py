@@ -53,6 +53,39 @@ def test_alone_and_in_the_mix_are_identical():
         tol = 1e-5 if REQUESTS[k][1].get("precision", 0) == 1 else 1e-8
         assert rm.residual <= tol * 1.05
         assert rm.latency_ms >= rm.queue_ms >= 0.0
+        # the admission's estimate covers what the request's context really held
+        assert 0 < rm.device_peak_bytes <= rm.footprint_bytes, (k, rm.device_peak_bytes, rm.footprint_bytes)
+
+
+def test_served_results_solve_the_oracle_system():
+    """One served request per geometry, checked against the FP64 oracle (Sec. 4.2 operator,
+    eq. linsys right-hand side): the true relative residual of each returned current, with the
+    oracle's operator, is within the served tolerance plus the mixed form's operator error; the
+    served far field equals the oracle's far field of the returned current."""
+    import oracle as O
+    from paper_1807_03097_gb300.efie import Server
+
+    cases = [REQUESTS[0], REQUESTS[1], REQUESTS[2]]  # sphere (FP64), torus (mixed), cube (FP64)
+    srv = Server(hbm_budget_bytes=40 << 30, max_slots=3)
+    out = run_requests(srv, cases, first=100)
+    srv.close()
+    for k, (mk, opt) in enumerate(cases):
+        r, w, e = out[k]
+        assert r.status == 0
+        rng = np.random.default_rng(100 + k)
+        d = rng.standard_normal((2, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        pol = np.cross(d, [0.3, 0.5, 0.8])
+        pol /= np.linalg.norm(pol, axis=1, keepdims=True)
+        ref = O.Problem(mk(), p=opt["p"], m=opt["level_m"], kappa=opt["kappa"], q=opt["q"], eta=opt["eta"])
+        tol = 1e-5 if opt.get("precision", 0) == 1 else 1e-8
+        ff = np.array([[0, 0, 1.0], [1.0, 0, 0]])
+        for i in range(2):
+            b = ref.rhs(d[i], pol[i])
+            res = np.linalg.norm(b - ref.fmm_matvec(w[i])[0]) / np.linalg.norm(b)
+            assert res < 2 * tol, (k, i, res)
+            e_ref = ref.far_field(w[i], ff)
+            assert np.abs(e[i] - e_ref).max() < 1e-11 * np.abs(e_ref).max(), (k, i)
 
 
 def test_tight_budget_serialises_and_errors_are_reported():

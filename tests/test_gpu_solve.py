@@ -103,3 +103,40 @@ def test_zero_right_hand_sides_and_zero_vector():
     x, info, st = s.solve(np.zeros(s.ndof, np.complex128))
     assert st == 0 and np.all(x == 0)
     s.close()
+
+
+def test_temporaries_are_returned_to_the_pool():
+    """Every call's temporary device buffers are returned (stream-ordered) when it ends: after a
+    first call of each kind (which may allocate the context's persistent work arrays), repeating
+    it leaves the context's live device bytes unchanged, and destroying the context after a
+    failed call is clean."""
+    from paper_1807_03097_gb300 import Solver
+
+    s = Solver(G.sphere(), p=2, level_m=2, kappa=3.0, q=5, eta=1.6, precision=1)
+    rng = np.random.default_rng(90)
+    x = rng.standard_normal((3, s.ndof)) + 1j * rng.standard_normal((3, s.ndof))
+    xs = rng.standard_normal((3, s.nsup)) + 1j * rng.standard_normal((3, s.nsup))
+    dirs = np.array([[0, 0, 1.0], [0, 1.0, 0]])
+    pts = np.array([[3.0, 0, 0], [0, 0, -4.0]])
+    calls = [
+        lambda: s.matvec(x[0]),
+        lambda: s.matvec(x),
+        lambda: s.matvec_superspace(xs[0]),
+        lambda: s.matvec_superspace(xs),
+        lambda: s.far_field(x, dirs),
+        lambda: s.exterior_field(x, pts),
+        lambda: s.rhs(dirs, [[1.0, 0, 0], [1.0, 0, 0]]),
+        lambda: s.solve_plane_waves(dirs, [[1.0, 0, 0], [1.0, 0, 0]]),
+    ]
+    for f in calls:
+        f()
+        live1, _ = s.device_bytes()
+        f()
+        live2, peak = s.device_bytes()
+        assert live2 == live1 and peak >= live2 > 0
+    # a call rejected after the context is set up leaves nothing behind
+    live, _ = s.device_bytes()
+    with pytest.raises(Exception):
+        s.exterior_field(x[0], np.zeros((70000, 3)) + 5.0)
+    assert s.device_bytes()[0] == live
+    s.close()

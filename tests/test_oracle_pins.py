@@ -98,10 +98,36 @@ def test_divergence_theorem_on_closed_surface(patches):
     rng = np.random.default_rng(3)
     x = rng.standard_normal(pr.ndof) + 1j * rng.standard_normal(pr.ndof)
     assert abs(pr.div_integral(x)) < 1e-12 * np.abs(x).sum()
-    # a single patch-local function alone does have flux: the test is not vacuous
-    e = np.zeros(pr.ndof, complex)
+    # Not vacuous: a basis function that crosses an interface has a nonzero flux out of each of
+    # its two patches (closed form per element: int_0^1 B_a' = B_a(1) - B_a(0), int_0^1 B_b =
+    # 1/(p+1)), and the two fluxes cancel.
+    p, n = 2, 2
+    np1, nb = p + 1, 2 * (p + 1) ** 2
     r, c, v = pr.T()
-    assert abs(pr.div_integral(e)) == 0.0
+    patch_of_row = r // nb // (n * n)
+    h = 1.0 / n
+    checked = 0
+    for j in range(pr.ndof):
+        sel = c == j
+        patches = np.unique(patch_of_row[sel])
+        if len(patches) != 2:
+            continue
+        xs = np.zeros(pr.nsup)
+        np.add.at(xs, r[sel], v[sel])
+        X = xs.reshape(-1, 2, np1, np1)  # [element][alpha][b][a]
+        flux = []
+        for P in patches:
+            E = X[P * n * n:(P + 1) * n * n]
+            f0 = (E[:, 0, :, p] - E[:, 0, :, 0]).sum()  # d/ds1 of B_a(s1) B_b(s2)
+            f1 = (E[:, 1, p, :] - E[:, 1, 0, :]).sum()  # d/ds2
+            flux.append(h / np1 * (f0 + f1))
+        assert abs(flux[0]) > 0.1 * h, flux
+        assert abs(flux[0] + flux[1]) < 1e-13, flux
+        e = np.zeros(pr.ndof, complex)
+        e[j] = 1.0
+        assert abs(pr.div_integral(e)) < 1e-13
+        checked += 1
+    assert checked > 0
 
 
 # ---------------------------------------------------------------- quadrature (Sec. 4.1, [SS97])
@@ -385,3 +411,21 @@ def test_far_only_rows_plus_near_blocks_give_the_rows():
             if a == e:
                 ref += r.pair_block(int(a), int(b)) @ X[b]
         assert np.abs(full[i] - far[i] - ref).max() < 1e-12 * np.abs(full[i]).max()
+
+
+def test_fmm_rows_equal_rows_of_the_full_superspace_product():
+    """orc_fmm_rows (the checker of the full-size GPU tests) restricts the far field to the blocks
+    whose target cluster contains the element and integrates the near blocks on demand: its rows
+    must equal the same rows of the full superspace product (Sec. 4.2, eq. FMMlr), on a case with
+    far pairs on several levels."""
+    r = O.Problem(G.sphere(), p=1, m=3, kappa=2.0, q=4, eta=1.6)
+    far = r.far_pairs()
+    assert len(np.unique(far[:, 0])) >= 2
+    rng = np.random.default_rng(61)
+    xs = rng.standard_normal(r.nsup) + 1j * rng.standard_normal(r.nsup)
+    ys = r.fmm_matvec_superspace(xs).reshape(r.nE, r.nb)
+    n2 = 8 * 8
+    elems = np.array([0, 1, 9, 27, n2 - 1, n2, 2 * n2 + 35, 5 * n2 + 63])
+    rows = r.fmm_rows(xs, elems)
+    scale = np.abs(ys).max()
+    assert np.abs(rows - ys[elems]).max() < 1e-13 * scale
