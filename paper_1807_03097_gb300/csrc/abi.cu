@@ -192,6 +192,19 @@ efie_status efie_set_geometry(efie_ctx *ctx, int n_patches, const int *deg, cons
       if (knots[ko] != 0.0 || knots[ko + nk - 1] != 1.0) return EFIE_EINVAL;
       ko += nk;
     }
+    // reciprocal knot differences, so that the device evaluator divides by no knot span
+    for (int t = 0; t < 2; ++t) {
+      const int nk = d.ncp[t] + d.deg[t] + 1;
+      const double *kt = kn.data() + d.kofs[t];
+      std::vector<double> inv((size_t)d.deg[t] * nk, 0.0);
+      for (int dd = 1; dd <= d.deg[t]; ++dd)
+        for (int f = 0; f + dd < nk; ++f) {
+          const double den = kt[f + dd] - kt[f];
+          inv[(size_t)(dd - 1) * nk + f] = den > 0.0 ? 1.0 / den : 0.0;
+        }
+      d.iofs[t] = (int)kn.size();
+      kn.insert(kn.end(), inv.begin(), inv.end());
+    }
     d.cofs = (int)(hw.size() / 4);
     int nc = d.ncp[0] * d.ncp[1];
     for (int i = 0; i < nc; ++i) {

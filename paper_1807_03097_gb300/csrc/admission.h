@@ -17,10 +17,13 @@ namespace efie {
 // ndir directions (3 complex values per element and direction, plus the output).  In the
 // mixed form the directions of a request are solved in lockstep (up to 64 at a time), each
 // with its own Krylov basis, and the batched product holds per-direction superspace vectors
-// and cluster fields.  np patches, 2^level_m elements per patch direction, degree p,
-// interpolation degree q.
+// and cluster fields.  When the coupling matrices of the admissible blocks are kept in device
+// memory (m2l_store: the FP64 form by default, the mixed form on request), they are counted
+// with at most 130 admissible source clusters per cluster (the block trees of the sphere and
+// torus workloads have 63 to 115).  np patches, 2^level_m elements per patch direction,
+// degree p, interpolation degree q.
 inline size_t request_footprint(int np, int level_m, int p, int q, int gmres_restart, int gmres_maxit, bool mixed,
-                                int nrhs, int ndir = 0) {
+                                int nrhs, int ndir = 0, int m2l_store = 0) {
   const size_t n = size_t(1) << level_m, nE = size_t(np) * n * n;
   const size_t p1 = p + 1, nb = 2 * p1 * p1, nI = size_t(q + 1) * (q + 1);
   const size_t ndof = 2 * size_t(np) * (n + p - 1) * (n + p - 1);
@@ -33,7 +36,9 @@ inline size_t request_footprint(int np, int level_m, int p, int q, int gmres_res
   const size_t vecs = nE * nb * 16 * 6 + ndof * 16 * 8;
   const size_t batch = lockstep > 1 ? lockstep * (5 * nE * nb * 16 + 14 * ncl * nI * 8 + 4 * ndof * 16) : 0;
   const size_t farfield = ndir > 0 ? 48 * size_t(ndir) * nE + 48 * size_t(ndir) + 24 * size_t(ndir) : 0;
-  return near + krylov + clusters + vecs + batch + farfield + (size_t(64) << 20);
+  const bool stored = mixed ? m2l_store == 2 : m2l_store != 1;
+  const size_t coupling = stored ? 130 * ncl * nI * nI * (mixed ? 8 : 16) : 0;
+  return near + krylov + clusters + vecs + batch + farfield + coupling + (size_t(64) << 20);
 }
 
 inline int pick_admission(int nqueued, const size_t *footprint, const double *cost, int oldest_passed, size_t left,

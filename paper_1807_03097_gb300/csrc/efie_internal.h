@@ -24,6 +24,8 @@ struct PatchDesc {
   int deg[2];
   int ncp[2];
   int kofs[2];  // offset of the s1 / s2 knot vector in the knot array
+  int iofs[2];  // offset of the reciprocal knot differences 1 / (t_{f+d} - t_f) of each
+                // direction in the knot array, [deg][ncp + deg + 1] (0 where t_{f+d} = t_f)
   int cofs;     // offset of the [ncp1][ncp0] homogeneous control net (w x, w y, w z, w)
 };
 

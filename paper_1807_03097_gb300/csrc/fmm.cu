@@ -326,18 +326,30 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
   return *reinterpret_cast<float2 *>(&D);
 }
 
-// FP32 M2L, one warp per target cluster, lane owns target nodes m = lane + j T (j < NT,
-// T = ceil(nI / NT) <= 32).  With e = x_t - x_s (offsets from the cluster centres) and the
-// pair's centre offset d, r0 = |d|:
-//   num = 2 d.e + |e|^2 = r^2 - r0^2 (no cancellation), r = sqrt(r0^2 + num),
-//   r - r0 = num / (r + r0),  G = e^{i kappa r0}/(4 pi) * e^{i kappa (r - r0)} / r.
-// The pair factor e^{i kappa r0}/(4 pi) is applied to the source fields while they are
-// staged in shared memory, together with the rotated copy (-Im, Re) that lets a complex
-// multiply-add run as two packed FMAs.  MODE 2: phase reduced to [-pi, pi] by two-constant
-// Cody-Waite before the hardware sine / cosine; MODE 1: the host has checked that every
-// phase lies within +-100 pi; MODE 0 (direct): the host has checked that
-// kappa * max r * 2^-24 < 2e-6, and the phase is taken as kappa r - kappa r0 with
-// r = |d + x_t - x_s| (a fixed perturbation of the matrix, below 2e-6 rad per entry).
+// FP32 M2L, one warp per target cluster; lane owns target nodes m = lane + j T (j < NT,
+// T = ceil(nI / NT) <= 32) and sweeps the source nodes of every admissible source cluster two
+// at a time, so that the kernel values of two entries (m, m'), (m, m'+1) are generated and
+// applied with packed FP32 instructions (fma / add / mul .f32x2 on the pair).  With x_t, x_s
+// the node offsets from the cluster centres, d = c_t - c_s and r0 = |d|:
+//   MODE 0 (direct): r^2 = |u|^2 + |x_s|^2 - 2 u.x_s with u = d + x_t, phase = kappa r -
+//     kappa r0; used when the host has checked that kappa * max r * 2^-24 < 2e-6 (a fixed
+//     perturbation of the matrix below 2e-6 rad per entry);
+//   MODE 1 (split): num = r^2 - r0^2 = (|x_t|^2 + 2 d.x_t) + (|x_s|^2 - 2 d.x_s) - 2 x_t.x_s,
+//     every term of the size of num (no cancellation against r0^2), r = sqrt(r0^2 + num),
+//     phase = kappa (r - r0) = num / ((r + r0) / kappa); the host has checked that every phase
+//     lies within +-100 pi;  MODE 2: MODE 1 plus a two-constant Cody-Waite reduction of the
+//     phase to [-pi, pi] before the hardware sine / cosine.
+// G = e^{i kappa r0}/(4 pi) * e^{i phase} / r.  The pair factor e^{i kappa r0}/(4 pi) is
+// applied to the source fields while they are staged in shared memory.  Staging of a source
+// pair k (nodes 2k, 2k+1; an odd last node is paired with a copy of itself with zero fields):
+//   sC[2k]   = (-2x_e, -2x_o, -2y_e, -2y_o),  sC[2k+1] = (-2z_e, -2z_o, b_e, b_o)
+//     (b = |x_s|^2 in MODE 0, |x_s|^2 - 2 d.x_s otherwise),
+//   sF[6k..6k+5] = Re w (fields 0-1, 2-3), Im w (0-1, 2-3), -Im w (0-1, 2-3), each float4 holding
+//     (field f even node, field f odd node, field f+1 even node, field f+1 odd node).
+// Per pair the packed partial sums (even and odd source nodes separately) are folded and
+// added to running sums over all source clusters with two-sum (compensated) addition; the
+// running sums and their compensation terms live in shared memory ([NT][16][32 lanes] per warp,
+// touched once per source cluster), which keeps the registers for the inner loop.
 template <int NT, int MODE>
 __global__ void __launch_bounds__(128, (NT <= 3 ? 4 : 2)) k_m2l_f32w(const int *__restrict__ targets, int ntarget,
                                                   const int *__restrict__ fptr, const int *__restrict__ fsrc,
@@ -348,96 +360,151 @@ __global__ void __launch_bounds__(128, (NT <= 3 ? 4 : 2)) k_m2l_f32w(const int *
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wg = blockIdx.x * (blockDim.x >> 5) + wib;
   if (wg >= ntarget) return;
-  float4 *sX = sm4 + (size_t)wib * 5 * nI;
-  float4 *sW = sX + nI;       // [nI][2]: (w0, w1), (w2, w3)
-  float4 *sR = sW + 2 * nI;   // [nI][2]: rotated (-Im, Re) copies
+  const int NSP = (nI + 1) >> 1;  // source node pairs
+  float4 *sT = sm4 + (size_t)wib * (nI + 8 * NSP + 4 * 32 * NT);
+  float4 *sC = sT + nI;   // [2 NSP]
+  float4 *sF = sC + 2 * NSP;  // [6 NSP]
+  float *sA = reinterpret_cast<float *>(sF + 6 * NSP);  // [NT][16][32]: running sums, compensation
   const int t = targets[wg];
   const int T = (nI + NT - 1) / NT;
-  float xt[NT][3];
-  float ah[NT][8], al[NT][8];  // compensated accumulators over all source clusters
+  for (int i = lane; i < nI; i += 32) sT[i] = nodeX4[(size_t)t * nI + i];
 #pragma unroll
-  for (int j = 0; j < NT; ++j) {
-    int mi = lane + j * T;
-    float4 x = (lane < T && mi < nI) ? nodeX4[(size_t)t * nI + mi] : make_float4(0.f, 0.f, 0.f, 0.f);
-    xt[j][0] = x.x;
-    xt[j][1] = x.y;
-    xt[j][2] = x.z;
+  for (int j = 0; j < NT; ++j)
 #pragma unroll
-    for (int q = 0; q < 8; ++q) ah[j][q] = al[j][q] = 0.f;
-  }
+    for (int q = 0; q < 16; ++q) sA[(j * 16 + q) * 32 + lane] = 0.f;
   const float inv2pi = 0.15915494309189535f, c1 = 6.28318548202514648f, c2 = -1.7484555e-7f;
+  const float kinv = 1.f / kappa;
   for (int k = fptr[t]; k < fptr[t + 1]; ++k) {
     const int s = fsrc[k];
     const float4 g = pgeo[k];
     const float2 ph = pph[k];
     __syncwarp();
-    for (int i = lane; i < nI; i += 32) {
-      sX[i] = nodeX4[(size_t)s * nI + i];
-      float4 u = src[2 * ((size_t)s * nI + i)], v = src[2 * ((size_t)s * nI + i) + 1];
-      float4 pu = make_float4(ph.x * u.x - ph.y * u.y, ph.x * u.y + ph.y * u.x, ph.x * u.z - ph.y * u.w,
-                              ph.x * u.w + ph.y * u.z);
-      float4 pv = make_float4(ph.x * v.x - ph.y * v.y, ph.x * v.y + ph.y * v.x, ph.x * v.z - ph.y * v.w,
-                              ph.x * v.w + ph.y * v.z);
-      sW[2 * i] = pu;
-      sW[2 * i + 1] = pv;
-      sR[2 * i] = make_float4(-pu.y, pu.x, -pu.w, pu.z);
-      sR[2 * i + 1] = make_float4(-pv.y, pv.x, -pv.w, pv.z);
+    for (int i = lane; i < 2 * NSP; i += 32) {
+      const int kp = i >> 1, e = i & 1;
+      const int n = min(2 * kp + e, nI - 1);
+      const bool real = 2 * kp + e < nI;
+      const float4 x = nodeX4[(size_t)s * nI + n];
+      float4 u = make_float4(0.f, 0.f, 0.f, 0.f), v = u;
+      if (real) {
+        u = src[2 * ((size_t)s * nI + n)];
+        v = src[2 * ((size_t)s * nI + n) + 1];
+      }
+      const float bb = MODE == 0 ? x.x * x.x + x.y * x.y + x.z * x.z
+                                 : x.x * x.x + x.y * x.y + x.z * x.z - 2.f * (g.x * x.x + g.y * x.y + g.z * x.z);
+      // fields w_f = ph * (u.xy, u.zw, v.xy, v.zw)
+      const float wr[4] = {ph.x * u.x - ph.y * u.y, ph.x * u.z - ph.y * u.w, ph.x * v.x - ph.y * v.y,
+                           ph.x * v.z - ph.y * v.w};
+      const float wi[4] = {ph.x * u.y + ph.y * u.x, ph.x * u.w + ph.y * u.z, ph.x * v.y + ph.y * v.x,
+                           ph.x * v.w + ph.y * v.z};
+      float *c = reinterpret_cast<float *>(sC + 2 * kp);
+      c[e] = -2.f * x.x;
+      c[2 + e] = -2.f * x.y;
+      c[4 + e] = -2.f * x.z;
+      c[6 + e] = bb;
+      float *f = reinterpret_cast<float *>(sF + 6 * kp);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int o = (q >> 1) * 4 + (q & 1) * 2 + e;
+        f[o] = wr[q];
+        f[8 + o] = wi[q];
+        f[16 + o] = -wi[q];
+      }
     }
     __syncwarp();
-    const float r0 = g.w, r0sq = g.w * g.w, kr0 = kappa * g.w;
-    float ut[NT][3];  // d + x_t (direct mode)
+    // per-lane constants of this pair for each target node
+    float2 U[NT][4];
 #pragma unroll
     for (int j = 0; j < NT; ++j) {
-      ut[j][0] = g.x + xt[j][0];
-      ut[j][1] = g.y + xt[j][1];
-      ut[j][2] = g.z + xt[j][2];
+      const int mi = lane + j * T;
+      const float4 x = sT[(lane < T && mi < nI) ? mi : 0];
+      float ax, ay, az, aa;
+      if (MODE == 0) {
+        ax = g.x + x.x;
+        ay = g.y + x.y;
+        az = g.z + x.z;
+        aa = ax * ax + ay * ay + az * az;
+      } else {
+        ax = x.x;
+        ay = x.y;
+        az = x.z;
+        aa = x.x * x.x + x.y * x.y + x.z * x.z + 2.f * (g.x * x.x + g.y * x.y + g.z * x.z);
+      }
+      U[j][0] = make_float2(ax, ax);
+      U[j][1] = make_float2(ay, ay);
+      U[j][2] = make_float2(az, az);
+      U[j][3] = make_float2(aa, aa);
     }
-    float2 a[NT][4];  // this pair's partial sums (q + 1)^2 terms
+    const float2 r0sq = make_float2(g.w * g.w, g.w * g.w), nkr0 = make_float2(-kappa * g.w, -kappa * g.w);
+    const float2 kap2 = make_float2(kappa, kappa), kinv2 = make_float2(kinv, kinv);
+    const float2 r0k = make_float2(g.w * kinv, g.w * kinv);
+    float2 are[NT][4], aim[NT][4];  // this pair's packed partial sums (even, odd source nodes)
 #pragma unroll
     for (int j = 0; j < NT; ++j)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) a[j][q] = make_float2(0.f, 0.f);
-#pragma unroll 2
-    for (int mj = 0; mj < nI; ++mj) {
-      const float4 xs = sX[mj], wa = sW[2 * mj], wb = sW[2 * mj + 1], ra = sR[2 * mj], rb = sR[2 * mj + 1];
+      for (int q = 0; q < 4; ++q) are[j][q] = aim[j][q] = make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int kp = 0; kp < NSP; ++kp) {
+      const float4 ca = sC[2 * kp], cb = sC[2 * kp + 1];
+      const float2 sx = make_float2(ca.x, ca.y), sy = make_float2(ca.z, ca.w), sz = make_float2(cb.x, cb.y),
+                   sb = make_float2(cb.z, cb.w);
+      float2 gr[NT], gi[NT];
 #pragma unroll
       for (int j = 0; j < NT; ++j) {
-        float rinv, phs;
+        float2 v = __fadd2_rn(U[j][3], sb);
+        v = __ffma2_rn(U[j][0], sx, v);
+        v = __ffma2_rn(U[j][1], sy, v);
+        v = __ffma2_rn(U[j][2], sz, v);
+        float2 rinv, phs;
         if (MODE == 0) {
-          float vx = ut[j][0] - xs.x, vy = ut[j][1] - xs.y, vz = ut[j][2] - xs.z;
-          float r2 = vx * vx + vy * vy + vz * vz;
-          rinv = rsqrtf(r2);
-          phs = fmaf(kappa, r2 * rinv, -kr0);
+          rinv = make_float2(rsqrtf(v.x), rsqrtf(v.y));
+          phs = __ffma2_rn(kap2, __fmul2_rn(v, rinv), nkr0);
         } else {
-          float ex = xt[j][0] - xs.x, ey = xt[j][1] - xs.y, ez = xt[j][2] - xs.z;
-          float de = g.x * ex + g.y * ey + g.z * ez;
-          float ee = ex * ex + ey * ey + ez * ez;
-          float num = fmaf(2.f, de, ee);
-          float r2 = r0sq + num;
-          rinv = rsqrtf(r2);
-          float r = r2 * rinv;
-          phs = kappa * __fdividef(num, r + r0);
+          const float2 r2 = __fadd2_rn(v, r0sq);
+          rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+          const float2 den = __ffma2_rn(__fmul2_rn(r2, rinv), kinv2, r0k);
+          phs = __fmul2_rn(v, make_float2(__fdividef(1.f, den.x), __fdividef(1.f, den.y)));
           if (MODE == 2) {
-            float kk = rintf(phs * inv2pi);
-            phs = fmaf(-kk, c1, phs);
-            phs = fmaf(-kk, c2, phs);
+            const float2 qq = __fmul2_rn(phs, make_float2(inv2pi, inv2pi));
+            const float2 qn = make_float2(-rintf(qq.x), -rintf(qq.y));
+            phs = __ffma2_rn(qn, make_float2(c1, c1), phs);
+            phs = __ffma2_rn(qn, make_float2(c2, c2), phs);
           }
         }
-        float sn, cs;
-        __sincosf(phs, &sn, &cs);
-        const float2 gr = make_float2(cs * rinv, cs * rinv), gi = make_float2(sn * rinv, sn * rinv);
-        a[j][0] = ffma2(gi, make_float2(ra.x, ra.y), ffma2(gr, make_float2(wa.x, wa.y), a[j][0]));
-        a[j][1] = ffma2(gi, make_float2(ra.z, ra.w), ffma2(gr, make_float2(wa.z, wa.w), a[j][1]));
-        a[j][2] = ffma2(gi, make_float2(rb.x, rb.y), ffma2(gr, make_float2(wb.x, wb.y), a[j][2]));
-        a[j][3] = ffma2(gi, make_float2(rb.z, rb.w), ffma2(gr, make_float2(wb.z, wb.w), a[j][3]));
+        float2 sn, cs;
+        __sincosf(phs.x, &sn.x, &cs.x);
+        __sincosf(phs.y, &sn.y, &cs.y);
+        gr[j] = __fmul2_rn(cs, rinv);
+        gi[j] = __fmul2_rn(sn, rinv);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float4 fr = sF[6 * kp + h], fi = sF[6 * kp + 2 + h], fn = sF[6 * kp + 4 + h];
+#pragma unroll
+        for (int qq = 0; qq < 2; ++qq) {
+          const int q = 2 * h + qq;
+          const float2 wr = qq ? make_float2(fr.z, fr.w) : make_float2(fr.x, fr.y);
+          const float2 wi = qq ? make_float2(fi.z, fi.w) : make_float2(fi.x, fi.y);
+          const float2 wn = qq ? make_float2(fn.z, fn.w) : make_float2(fn.x, fn.y);
+#pragma unroll
+          for (int j = 0; j < NT; ++j) {
+            are[j][q] = __ffma2_rn(gi[j], wn, __ffma2_rn(gr[j], wr, are[j][q]));
+            aim[j][q] = __ffma2_rn(gi[j], wr, __ffma2_rn(gr[j], wi, aim[j][q]));
+          }
+        }
       }
     }
 #pragma unroll
     for (int j = 0; j < NT; ++j)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        two_sum_acc(ah[j][2 * q], al[j][2 * q], a[j][q].x);
-        two_sum_acc(ah[j][2 * q + 1], al[j][2 * q + 1], a[j][q].y);
+        float *h0 = sA + (j * 16 + 2 * q) * 32 + lane, *h1 = h0 + 32, *l0 = h0 + 8 * 32, *l1 = h1 + 8 * 32;
+        float vh0 = *h0, vl0 = *l0, vh1 = *h1, vl1 = *l1;
+        two_sum_acc(vh0, vl0, are[j][q].x + are[j][q].y);
+        two_sum_acc(vh1, vl1, aim[j][q].x + aim[j][q].y);
+        *h0 = vh0;
+        *l0 = vl0;
+        *h1 = vh1;
+        *l1 = vl1;
       }
   }
 #pragma unroll
@@ -446,7 +513,7 @@ __global__ void __launch_bounds__(128, (NT <= 3 ? 4 : 2)) k_m2l_f32w(const int *
     if (lane < T && mi < nI) {
       float o[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) o[q] = ah[j][q] + al[j][q];
+      for (int q = 0; q < 8; ++q) o[q] = sA[(j * 16 + q) * 32 + lane] + sA[(j * 16 + 8 + q) * 32 + lane];
       acc[2 * ((size_t)t * nI + mi)] = make_float4(o[0], o[1], o[2], o[3]);
       acc[2 * ((size_t)t * nI + mi) + 1] = make_float4(o[4], o[5], o[6], o[7]);
     }
@@ -745,7 +812,10 @@ __global__ void k_leaf_eval(int nE, int leaf_off, int p1, int q1, R h, const dou
 // ------------------------------------------------------------------------ drivers
 constexpr int kM2LWarps = 4;
 
-static size_t m2l_f32_smem(int nI) { return sizeof(float4) * 5 * (size_t)nI * kM2LWarps; }
+// per warp: target nodes, staged source pairs, running sums [NT][16][32] (NT = ceil(nI / 32))
+static size_t m2l_f32_smem(int nI) {
+  return sizeof(float4) * ((size_t)nI + 8 * (size_t)((nI + 1) / 2) + 4 * 32 * (size_t)((nI + 31) / 32)) * kM2LWarps;
+}
 
 template <int MODE>
 static efie_status launch_m2l_f32_t(Ctx *c, cudaStream_t st) {

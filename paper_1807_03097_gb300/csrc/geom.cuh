@@ -14,8 +14,12 @@ namespace efie {
 // Values and first derivatives of the deg+1 B-splines that do not vanish at x; returns the
 // knot span k (functions k-deg .. k).  Triangular Cox-de Boor scheme; the derivative uses
 // the degree deg-1 values: b_f' = deg (b_f^{deg-1}/(t_{f+deg}-t_f) -
-// b_{f+1}^{deg-1}/(t_{f+deg+1}-t_{f+1})).
-__device__ inline int dev_bspline(const double *kn, int deg, int ncp, double x, double *N, double *dN) {
+// b_{f+1}^{deg-1}/(t_{f+deg+1}-t_{f+1})).  inv holds the reciprocal knot differences
+// inv[(d-1) nk + f] = 1 / (t_{f+d} - t_f) (0 where the difference is 0), nk = ncp + deg + 1,
+// so that no division is evaluated here.  Loops run to the compile-time bound GD >= deg.
+template <int GD>
+__device__ inline int dev_bspline(const double *kn, const double *inv, int deg, int ncp, double x, double *N,
+                                  double *dN) {
   int k;
   if (x >= kn[ncp]) {
     k = ncp - 1;
@@ -27,81 +31,80 @@ __device__ inline int dev_bspline(const double *kn, int deg, int ncp, double x, 
     }
     k = lo;
   }
-  double cur[kMaxGeoDeg + 1], prev[kMaxGeoDeg + 1];
+  const int nk = ncp + deg + 1;
+  double cur[GD + 1], prev[GD + 1];
 #pragma unroll
-  for (int i = 0; i <= kMaxGeoDeg; ++i) {
+  for (int i = 0; i <= GD; ++i) {
     cur[i] = 0.0;
     prev[i] = 0.0;
   }
   cur[0] = 1.0;
 #pragma unroll
-  for (int d = 1; d <= kMaxGeoDeg; ++d) {
+  for (int d = 1; d <= GD; ++d) {
     if (d <= deg) {
 #pragma unroll
-      for (int i = 0; i <= kMaxGeoDeg; ++i) prev[i] = cur[i];
+      for (int i = 0; i <= GD; ++i) prev[i] = cur[i];
+      const double *iv = inv + (d - 1) * nk;
 #pragma unroll
-      for (int i = 0; i <= kMaxGeoDeg; ++i) {
+      for (int i = 0; i <= GD; ++i) {
         if (i <= d) {
           int f = k - d + i;
           double v = 0.0;
-          if (i >= 1) {
-            double den = kn[f + d] - kn[f];
-            if (den > 0.0) v += (x - kn[f]) / den * prev[i - 1];
-          }
-          if (i < d) {
-            double den = kn[f + d + 1] - kn[f + 1];
-            if (den > 0.0) v += (kn[f + d + 1] - x) / den * prev[i];
-          }
+          if (i >= 1) v += (x - kn[f]) * iv[f] * prev[i - 1];
+          if (i < d) v += (kn[f + d + 1] - x) * iv[f + 1] * prev[i];
           cur[i] = v;
         }
       }
     }
   }
+  const double *iv = inv + (deg - 1) * nk;
 #pragma unroll
-  for (int i = 0; i <= kMaxGeoDeg; ++i) {
+  for (int i = 0; i <= GD; ++i) {
     N[i] = cur[i];
     double v = 0.0;
     if (i <= deg) {
       int f = k - deg + i;
-      if (i >= 1) {
-        double den = kn[f + deg] - kn[f];
-        if (den > 0.0) v += deg * prev[i - 1] / den;
-      }
-      if (i < deg) {
-        double den = kn[f + deg + 1] - kn[f + 1];
-        if (den > 0.0) v -= deg * prev[i] / den;
-      }
+      if (i >= 1) v += deg * prev[i - 1] * iv[f];
+      if (i < deg) v -= deg * prev[i] * iv[f + 1];
     }
     dN[i] = v;
   }
   return k;
 }
 
-// F(s), d1F(s), d2F(s) of one patch (rational, quotient rule).
+// F(s), d1F(s), d2F(s) of one patch (rational, quotient rule); the patch degrees must not
+// exceed GD.
+template <int GD = kMaxGeoDeg>
 __device__ inline void dev_patch_eval(const PatchDesc &Pg, const double *knots, const double4 *cpw, double s1,
                                       double s2, double X[3], double D1[3], double D2[3]) {
   const PatchDesc P = Pg;
-  double Nu[kMaxGeoDeg + 1], dNu[kMaxGeoDeg + 1], Nv[kMaxGeoDeg + 1], dNv[kMaxGeoDeg + 1];
-  int ku = dev_bspline(knots + P.kofs[0], P.deg[0], P.ncp[0], s1, Nu, dNu);
-  int kv = dev_bspline(knots + P.kofs[1], P.deg[1], P.ncp[1], s2, Nv, dNv);
+  double Nu[GD + 1], dNu[GD + 1], Nv[GD + 1], dNv[GD + 1];
+  int ku = dev_bspline<GD>(knots + P.kofs[0], knots + P.iofs[0], P.deg[0], P.ncp[0], s1, Nu, dNu);
+  int kv = dev_bspline<GD>(knots + P.kofs[1], knots + P.iofs[1], P.deg[1], P.ncp[1], s2, Nv, dNv);
+  // contraction in two stages: along s1 for each of the deg[1]+1 rows, then along s2
   double A[4] = {0, 0, 0, 0}, Au[4] = {0, 0, 0, 0}, Av[4] = {0, 0, 0, 0};
 #pragma unroll
-  for (int b = 0; b <= kMaxGeoDeg; ++b) {
+  for (int b = 0; b <= GD; ++b) {
     if (b <= P.deg[1]) {
       int r = kv - P.deg[1] + b;
+      double R[4] = {0, 0, 0, 0}, Ru[4] = {0, 0, 0, 0};
 #pragma unroll
-      for (int a = 0; a <= kMaxGeoDeg; ++a) {
+      for (int a = 0; a <= GD; ++a) {
         if (a <= P.deg[0]) {
           double4 h = cpw[P.cofs + r * P.ncp[0] + ku - P.deg[0] + a];
           double c4[4] = {h.x, h.y, h.z, h.w};
-          double w0 = Nu[a] * Nv[b], wu = dNu[a] * Nv[b], wv = Nu[a] * dNv[b];
 #pragma unroll
           for (int t = 0; t < 4; ++t) {
-            A[t] += w0 * c4[t];
-            Au[t] += wu * c4[t];
-            Av[t] += wv * c4[t];
+            R[t] += Nu[a] * c4[t];
+            Ru[t] += dNu[a] * c4[t];
           }
         }
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        A[t] += Nv[b] * R[t];
+        Au[t] += Nv[b] * Ru[t];
+        Av[t] += dNv[b] * R[t];
       }
     }
   }

@@ -3,6 +3,7 @@
 // and the Sauter-Schwab singularity-removing substitutions [SS97] for touching pairs
 // (identical: 8 Duffy parts, common edge: 6, common vertex: 4), and their application
 // y*_e = sum_{e'} N_{e e'} x*_{e'} as an HBM-streaming block-sparse product.
+#include <algorithm>
 #include <cmath>
 
 #include "geom.cuh"
@@ -76,20 +77,47 @@ __device__ inline void canonical_point(int kind, int g, const double *x, const d
   }
 }
 
-// One block per element pair.  Each chunk of kQC points: threads [0, kQC) evaluate the
-// target element, [kQC, 2 kQC) the source element (every thread of the block), then every
-// thread accumulates its block entries: B[r][c] += G w (sum_k U_k[r] V_k[c]) with U_k = h^2 d_alpha F_k psi_r
-// (k < 3), U_3 = h d_alpha psi_r, V_3 = -kappa^-2 h d_beta psi_c.
+// Points staged per chunk: 64 for p <= 3, 32 for p = 4 (shared memory).
+template <int P> struct QuadChunk { static constexpr int n = P <= 3 ? 64 : 32; };
+
+// Shared memory of one block of k_near_quad<P> (doubles).
 template <int P>
+__host__ __device__ constexpr size_t quad_smem_doubles() {
+  constexpr int Q = QuadChunk<P>::n, NS = (P + 1) * (P + 1), NB = 2 * NS;
+  return (size_t)Q * (NS + 2 * NS)       // psi, d psi at the target points
+         + (size_t)Q * (NS + 2 * NS)     // psi, d psi at the source points
+         + (size_t)Q * 2 * NB * 2        // SA
+         + (size_t)Q * NB * 2            // SC
+         + (size_t)2 * Q * 10            // X, d1F, d2F (+ weight) of both sides
+         + (size_t)Q * 10;               // cA[alpha][beta], cB
+}
+
+// One block per element pair.  The block entry of eq. Vkh for target row r = (alpha, a, b)
+// and source column c = (beta, c1, c2) is, at a quadrature point with weight W and points
+// s, t in the two elements (h = 1/n the element size, psi_ab = B_a B_b the Bernstein products,
+// d_alpha psi their derivatives in the element coordinates, G = e^{i kappa |x-y|}/(4 pi |x-y|)):
+//   W G [ h^4 <d_alpha F(s), d_beta F'(t)> psi_ab(s) psi'_c(t) - kappa^-2 h^2 d_alpha psi_ab(s) d_beta psi'_c(t) ].
+// Per chunk of Q points: (1) one thread per (point, side) evaluates the NURBS map and the
+// Bernstein values; (2) one thread per point forms the kernel value and the five complex
+// coefficients cA_ab = W G h^4 <d_a F, d_b F'> and cB = -W G kappa^-2 h^2; (3) the products of
+// the source-side values with the coefficients, SA[alpha][c] = cA_{alpha beta(c)} psi'_c and
+// SC[c] = cB d_beta psi'_c; (4) every thread adds to its entries
+//   B[r][c] += psi_ab SA[alpha][c] + d_alpha psi_ab SC[c]    (4 FP64 FMAs per entry and point).
+// GD bounds the NURBS degrees at compile time.
+template <int P, int GD>
 __global__ void __launch_bounds__(kQuadThreads) k_near_quad(QuadArgs A) {
-  constexpr int P1 = P + 1, NB = 2 * P1 * P1, NB2 = NB * NB;
+  constexpr int Q = QuadChunk<P>::n;
+  constexpr int P1 = P + 1, NS = P1 * P1, NB = 2 * NS, NB2 = NB * NB;
   constexpr int EPT = (NB2 + kQuadThreads - 1) / kQuadThreads;
   extern __shared__ double sm[];
-  double *U = sm;                       // [kQC][4][NB]
-  double *V = U + kQC * 4 * NB;         // [kQC][4][NB]
-  double *XY = V + kQC * 4 * NB;        // [2][kQC][3]
-  double *GW = XY + 2 * kQC * 3;        // [kQC][2]
-  double *wts = GW + 2 * kQC;           // [kQC]
+  double *Pt = sm;                    // [Q][NS]
+  double *Dt = Pt + Q * NS;           // [Q][2][NS]
+  double *Ps = Dt + Q * 2 * NS;       // [Q][NS]
+  double *Ds = Ps + Q * NS;           // [Q][2][NS]
+  double2 *SA = reinterpret_cast<double2 *>(Ds + Q * 2 * NS);  // [Q][2][NB]
+  double2 *SC = SA + Q * 2 * NB;      // [Q][NB]
+  double *Gm = reinterpret_cast<double *>(SC + Q * NB);  // [2][Q][10]: X, d1F, d2F, weight
+  double *Cf = Gm + 2 * Q * 10;       // [Q][10]: cA_00, cA_01, cA_10, cA_11, cB (re, im)
   int pi = blockIdx.x;
   if (pi >= A.ntodo) return;
   const NearPair pr = A.pairs[A.todo[pi]];
@@ -99,7 +127,7 @@ __global__ void __launch_bounds__(kQuadThreads) k_near_quad(QuadArgs A) {
   const double *gw = pr.kind == 0 ? A.rw : A.sw;
   const int parts = pr.kind == 0 ? 1 : (pr.kind == 3 ? 8 : (pr.kind == 2 ? 6 : 4));
   const int nq = parts * g * g * g * g;
-  const double h = A.h, h2 = h * h, ik2 = 1.0 / (A.kappa * A.kappa);
+  const double h = A.h, h2 = h * h, h4 = h2 * h2, ik2 = 1.0 / (A.kappa * A.kappa);
 
   // element placement
   int ej = pr.e / n2, eK = pr.e % n2, fj = pr.e2 / n2, fK = pr.e2 % n2;
@@ -114,79 +142,104 @@ __global__ void __launch_bounds__(kQuadThreads) k_near_quad(QuadArgs A) {
   double2 acc[EPT];
 #pragma unroll
   for (int t = 0; t < EPT; ++t) acc[t] = make_double2(0.0, 0.0);
+  const int tid = threadIdx.x;
 
-  for (int q0 = 0; q0 < nq; q0 += kQC) {
-    int tid = threadIdx.x;
-    if (tid < 2 * kQC) {
-      int side = tid / kQC, ql = tid % kQC, k = q0 + ql;
-      double *Us = side == 0 ? U : V;
+  for (int q0 = 0; q0 < nq; q0 += Q) {
+    // (1) geometry and Bernstein values, one thread per (point, side)
+    for (int it = tid; it < 2 * Q; it += kQuadThreads) {
+      const int side = it / Q, ql = it % Q, k = q0 + ql;
+      double *G = Gm + (side * Q + ql) * 10;
+      double *Pv = (side == 0 ? Pt : Ps) + ql * NS, *Dv = (side == 0 ? Dt : Ds) + ql * 2 * NS;
       if (k < nq) {
         double sh[2], th[2], W;
         canonical_point(pr.kind, g, gx, gw, k, sh, th, W);
         double sg0, sg1;
-        int code = side == 0 ? pr.r1 : pr.r2;
+        const int code = side == 0 ? pr.r1 : pr.r2;
         sym_apply(code, side == 0 ? sh[0] : th[0], side == 0 ? sh[1] : th[1], sg0, sg1);
-        int pj = side == 0 ? ej : fj;
-        int ia = side == 0 ? ea : fa, ib = side == 0 ? eb : fb;
+        const int pj = side == 0 ? ej : fj;
+        const int ia = side == 0 ? ea : fa, ib = side == 0 ? eb : fb;
         double X[3], D1[3], D2[3];
-        dev_patch_eval(A.patches[pj], A.knots, A.cpw, (ia + sg0) * h, (ib + sg1) * h, X, D1, D2);
+        dev_patch_eval<GD>(A.patches[pj], A.knots, A.cpw, (ia + sg0) * h, (ib + sg1) * h, X, D1, D2);
         double B0[kMaxP1], dB0[kMaxP1], B1[kMaxP1], dB1[kMaxP1];
         dev_bernstein(P, sg0, B0, dB0);
         dev_bernstein(P, sg1, B1, dB1);
-        double f3 = side == 0 ? h : -ik2 * h;
-        for (int al = 0; al < 2; ++al) {
-          const double *D = al == 0 ? D1 : D2;
-          for (int b = 0; b < P1; ++b)
-            for (int a = 0; a < P1; ++a) {
-              int r = (al * P1 + b) * P1 + a;
-              double ps = B0[a] * B1[b];
-              double dps = al == 0 ? dB0[a] * B1[b] : B0[a] * dB1[b];
-              Us[(ql * 4 + 0) * NB + r] = h2 * D[0] * ps;
-              Us[(ql * 4 + 1) * NB + r] = h2 * D[1] * ps;
-              Us[(ql * 4 + 2) * NB + r] = h2 * D[2] * ps;
-              Us[(ql * 4 + 3) * NB + r] = f3 * dps;
-            }
+#pragma unroll
+        for (int b = 0; b < P1; ++b)
+#pragma unroll
+          for (int a = 0; a < P1; ++a) {
+            Pv[b * P1 + a] = B0[a] * B1[b];
+            Dv[b * P1 + a] = dB0[a] * B1[b];
+            Dv[NS + b * P1 + a] = B0[a] * dB1[b];
+          }
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) {
+          G[kk] = X[kk];
+          G[3 + kk] = D1[kk];
+          G[6 + kk] = D2[kk];
         }
-        XY[(side * kQC + ql) * 3 + 0] = X[0];
-        XY[(side * kQC + ql) * 3 + 1] = X[1];
-        XY[(side * kQC + ql) * 3 + 2] = X[2];
-        if (side == 0) wts[ql] = W;
+        G[9] = W;
       } else {
-        for (int r = 0; r < 4 * NB; ++r) Us[ql * 4 * NB + r] = 0.0;
-        XY[(side * kQC + ql) * 3 + 0] = 0.0;
-        XY[(side * kQC + ql) * 3 + 1] = 0.0;
-        XY[(side * kQC + ql) * 3 + 2] = (double)side;  // dummy pair at distance 1; weight 0
-        if (side == 0) wts[ql] = 0.0;
+        for (int r = 0; r < NS; ++r) {
+          Pv[r] = 0.0;
+          Dv[r] = 0.0;
+          Dv[NS + r] = 0.0;
+        }
+        for (int kk = 0; kk < 9; ++kk) G[kk] = 0.0;
+        G[2] = (double)side;  // dummy pair at distance 1; weight 0
+        G[9] = 0.0;
       }
     }
     __syncthreads();
-    if (tid < kQC) {
-      double dx = XY[tid * 3] - XY[(kQC + tid) * 3];
-      double dy = XY[tid * 3 + 1] - XY[(kQC + tid) * 3 + 1];
-      double dz = XY[tid * 3 + 2] - XY[(kQC + tid) * 3 + 2];
-      double r = sqrt(dx * dx + dy * dy + dz * dz);
+    // (2) kernel value and coefficients, one thread per point
+    for (int ql = tid; ql < Q; ql += kQuadThreads) {
+      const double *Gs = Gm + ql * 10, *Gt = Gm + (Q + ql) * 10;
+      const double dx = Gs[0] - Gt[0], dy = Gs[1] - Gt[1], dz = Gs[2] - Gt[2];
+      const double r = sqrt(dx * dx + dy * dy + dz * dz);
       double sn, cs;
       sincos(A.kappa * r, &sn, &cs);
-      double f = wts[tid] / (4.0 * M_PI * r);
-      GW[2 * tid] = f * cs;
-      GW[2 * tid + 1] = f * sn;
+      const double f = Gs[9] / (4.0 * M_PI * r);
+      const double gre = f * cs, gim = f * sn;
+      double *C = Cf + ql * 10;
+#pragma unroll
+      for (int al = 0; al < 2; ++al)
+#pragma unroll
+        for (int be = 0; be < 2; ++be) {
+          const double *Da = Gs + 3 + 3 * al, *Db = Gt + 3 + 3 * be;
+          const double gg = h4 * (Da[0] * Db[0] + Da[1] * Db[1] + Da[2] * Db[2]);
+          C[2 * (2 * al + be)] = gre * gg;
+          C[2 * (2 * al + be) + 1] = gim * gg;
+        }
+      C[8] = -ik2 * h2 * gre;
+      C[9] = -ik2 * h2 * gim;
     }
     __syncthreads();
+    // (3) source-side products SA, SC
+    for (int it = tid; it < Q * NB; it += kQuadThreads) {
+      const int ql = it / NB, cc = it % NB, be = cc / NS, cd = cc % NS;
+      const double *C = Cf + ql * 10;
+      const double ps = Ps[ql * NS + cd], ds = Ds[ql * 2 * NS + be * NS + cd];
+#pragma unroll
+      for (int al = 0; al < 2; ++al)
+        SA[(ql * 2 + al) * NB + cc] = make_double2(C[2 * (2 * al + be)] * ps, C[2 * (2 * al + be) + 1] * ps);
+      SC[ql * NB + cc] = make_double2(C[8] * ds, C[9] * ds);
+    }
+    __syncthreads();
+    // (4) accumulation of this thread's entries (column-major index cc NB + rr)
 #pragma unroll
     for (int t = 0; t < EPT; ++t) {
-      int idx = tid + t * kQuadThreads;
+      const int idx = tid + t * kQuadThreads;
       if (idx < NB2) {
-        int cc = idx / NB, rr = idx % NB;  // column-major block entry (rr, cc)
-        double sre = 0.0, sim = 0.0;
-        for (int ql = 0; ql < kQC; ++ql) {
-          const double *u = U + ql * 4 * NB, *v = V + ql * 4 * NB;
-          double s = u[rr] * v[cc] + u[NB + rr] * v[NB + cc] + u[2 * NB + rr] * v[2 * NB + cc] +
-                     u[3 * NB + rr] * v[3 * NB + cc];
-          sre += GW[2 * ql] * s;
-          sim += GW[2 * ql + 1] * s;
+        const int cc = idx / NB, rr = idx % NB, al = rr / NS, ab = rr % NS;
+        double re = 0.0, im = 0.0;
+#pragma unroll 4
+        for (int ql = 0; ql < Q; ++ql) {
+          const double pt = Pt[ql * NS + ab], dt = Dt[ql * 2 * NS + al * NS + ab];
+          const double2 sa = SA[(ql * 2 + al) * NB + cc], sc = SC[ql * NB + cc];
+          re = fma(pt, sa.x, fma(dt, sc.x, re));
+          im = fma(pt, sa.y, fma(dt, sc.y, im));
         }
-        acc[t].x += sre;
-        acc[t].y += sim;
+        acc[t].x += re;
+        acc[t].y += im;
       }
     }
     __syncthreads();
@@ -269,7 +322,6 @@ efie_status dev_near_quadrature(Ctx *c, const std::vector<NearPair> &pairs, cons
   A.kappa = c->kappa;
   A.h = 1.0 / c->n;
   A.blocks = c->d_nblk;
-  size_t smem = sizeof(double) * (2 * kQC * 4 * (size_t)nb + 2 * kQC * 3 + 2 * kQC + kQC);
   c->near_quad_pairs = (int)todo.size();
   c->near_quad_points = 0;
   for (int k : todo) {
@@ -277,23 +329,29 @@ efie_status dev_near_quadrature(Ctx *c, const std::vector<NearPair> &pairs, cons
     const int parts = kind == 0 ? 1 : (kind == 3 ? 8 : (kind == 2 ? 6 : 4));
     c->near_quad_points += (long long)parts * g * g * g * g;
   }
+  // compile-time bound of the NURBS degrees of this geometry
+  int gdeg = 1;
+  for (const PatchDesc &pd : c->patches) gdeg = std::max(gdeg, std::max(pd.deg[0], pd.deg[1]));
+  const int GDsel = gdeg <= 2 ? 2 : (gdeg <= 4 ? 4 : 8);
   EFIE_CUDA(cudaEventRecord(c->tm.ev[7], c->stream));
-  switch (c->p) {
-#define EFIE_QUAD_CASE(PP)                                                                          \
-  case PP:                                                                                          \
-    EFIE_CUDA(cudaFuncSetAttribute(k_near_quad<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                   (int)smem));                                                    \
-    k_near_quad<PP><<<A.ntodo, kQuadThreads, smem, c->stream>>>(A);                                 \
-    ++c->launches;                                                                                  \
-    break;
-    EFIE_QUAD_CASE(1)
-    EFIE_QUAD_CASE(2)
-    EFIE_QUAD_CASE(3)
-    EFIE_QUAD_CASE(4)
-#undef EFIE_QUAD_CASE
-    default:
-      c->err = "device near-field quadrature supports 1 <= p <= 4";
-      return EFIE_EINVAL;
+  bool launched = false;
+#define EFIE_QUAD(PP, GG)                                                                                 \
+  if (c->p == PP && GDsel == GG) {                                                                        \
+    const size_t smem = sizeof(double) * quad_smem_doubles<PP>();                                         \
+    EFIE_CUDA(cudaFuncSetAttribute(k_near_quad<PP, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                   (int)smem));                                                          \
+    k_near_quad<PP, GG><<<A.ntodo, kQuadThreads, smem, c->stream>>>(A);                                   \
+    ++c->launches;                                                                                        \
+    launched = true;                                                                                      \
+  }
+  EFIE_QUAD(1, 2) EFIE_QUAD(1, 4) EFIE_QUAD(1, 8)
+  EFIE_QUAD(2, 2) EFIE_QUAD(2, 4) EFIE_QUAD(2, 8)
+  EFIE_QUAD(3, 2) EFIE_QUAD(3, 4) EFIE_QUAD(3, 8)
+  EFIE_QUAD(4, 2) EFIE_QUAD(4, 4) EFIE_QUAD(4, 8)
+#undef EFIE_QUAD
+  if (!launched) {
+    c->err = "device near-field quadrature supports 1 <= p <= 4";
+    return EFIE_EINVAL;
   }
   EFIE_CUDA(cudaGetLastError());
   EFIE_CUDA(cudaEventRecord(c->tm.ev[6], c->stream));

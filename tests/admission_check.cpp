@@ -123,14 +123,18 @@ int main() {
   {  // footprint estimate: the mixed form stores an FP32 copy of the near blocks; directions
      // solved in lockstep each hold a Krylov basis (at most 64); FP64 solves are sequential
     using efie::request_footprint;
-    const size_t f64 = request_footprint(6, 5, 2, 8, 1500, 3000, false, 1);
+    const size_t f64 = request_footprint(6, 5, 2, 8, 1500, 3000, false, 1, 0, 1);  // matrices evaluated
     const size_t f32 = request_footprint(6, 5, 2, 8, 1500, 3000, true, 1);
+    // kept FP64 coupling matrices (the default of the FP64 form): 16 bytes per node pair
+    const size_t ncl = 6 * 1365;
+    CHECK(request_footprint(6, 5, 2, 8, 1500, 3000, false, 1) >= f64 + 130 * ncl * 81 * 81 * 16);
+    CHECK(request_footprint(6, 5, 2, 8, 1500, 3000, true, 1, 0, 2) >= f32 + 130 * ncl * 81 * 81 * 8);
     CHECK(f32 > f64);
     const size_t ndof = 2 * 6 * 33 * 33, krylov1 = 1501 * ndof * 16;
     const size_t f32x16 = request_footprint(6, 5, 2, 8, 1500, 3000, true, 16);
     CHECK(f32x16 >= f32 + 15 * krylov1);
     CHECK(request_footprint(6, 5, 2, 8, 1500, 3000, true, 100) == request_footprint(6, 5, 2, 8, 1500, 3000, true, 64));
-    CHECK(request_footprint(6, 5, 2, 8, 1500, 3000, false, 16) == f64);
+    CHECK(request_footprint(6, 5, 2, 8, 1500, 3000, false, 16, 0, 1) == f64);
     CHECK(request_footprint(6, 6, 2, 8, 1500, 3000, true, 1) > f32);
     CHECK(request_footprint(6, 5, 2, 8, 20, 3000, true, 1) < f32);  // shorter restart, smaller basis
     // far-field scratch: 3 complex doubles per element and direction
