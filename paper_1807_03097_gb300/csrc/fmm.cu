@@ -16,6 +16,7 @@
 #include <cmath>
 
 #include "efie_internal.h"
+#include "fastmath.cuh"
 
 namespace efie {
 
@@ -456,13 +457,13 @@ __global__ void __launch_bounds__(128, (NT <= 3 ? 4 : 2)) k_m2l_f32w(const int *
         v = __ffma2_rn(U[j][2], sz, v);
         float2 rinv, phs;
         if (MODE == 0) {
-          rinv = make_float2(rsqrtf(v.x), rsqrtf(v.y));
+          rinv = make_float2(rsqrt_ftz(v.x), rsqrt_ftz(v.y));
           phs = __ffma2_rn(kap2, __fmul2_rn(v, rinv), nkr0);
         } else {
           const float2 r2 = __fadd2_rn(v, r0sq);
-          rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+          rinv = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
           const float2 den = __ffma2_rn(__fmul2_rn(r2, rinv), kinv2, r0k);
-          phs = __fmul2_rn(v, make_float2(__fdividef(1.f, den.x), __fdividef(1.f, den.y)));
+          phs = __fmul2_rn(v, make_float2(rcp_ftz(den.x), rcp_ftz(den.y)));
           if (MODE == 2) {
             const float2 qq = __fmul2_rn(phs, make_float2(inv2pi, inv2pi));
             const float2 qn = make_float2(-rintf(qq.x), -rintf(qq.y));
@@ -470,9 +471,8 @@ __global__ void __launch_bounds__(128, (NT <= 3 ? 4 : 2)) k_m2l_f32w(const int *
             phs = __ffma2_rn(qn, make_float2(c2, c2), phs);
           }
         }
-        float2 sn, cs;
-        __sincosf(phs.x, &sn.x, &cs.x);
-        __sincosf(phs.y, &sn.y, &cs.y);
+        const float2 sn = make_float2(sin_ftz(phs.x), sin_ftz(phs.y));
+        const float2 cs = make_float2(cos_ftz(phs.x), cos_ftz(phs.y));
         gr[j] = __fmul2_rn(cs, rinv);
         gi[j] = __fmul2_rn(sn, rinv);
       }
@@ -1224,21 +1224,20 @@ __global__ void __launch_bounds__(kMultiThreads) k_m2l_f32_multi(
       if (mode == 0) {
         float vx = g.x + ex, vy = g.y + ey, vz = g.z + ez;
         float r2 = vx * vx + vy * vy + vz * vz;
-        rinv = rsqrtf(r2);
+        rinv = rsqrt_ftz(r2);
         phs = fmaf(kappa, r2 * rinv, -kr0);
       } else {
         float num = fmaf(2.f, g.x * ex + g.y * ey + g.z * ez, ex * ex + ey * ey + ez * ez);
         float r2 = r0sq + num;
-        rinv = rsqrtf(r2);
-        phs = kappa * __fdividef(num, r2 * rinv + r0);
+        rinv = rsqrt_ftz(r2);
+        phs = kappa * num * rcp_ftz(r2 * rinv + r0);
         if (mode == 2) {
           float q = rintf(phs * inv2pi);
           phs = fmaf(-q, c1, phs);
           phs = fmaf(-q, c2, phs);
         }
       }
-      float sn, cs;
-      __sincosf(phs, &sn, &cs);
+      const float sn = sin_ftz(phs), cs = cos_ftz(phs);
       const float gr = cs * rinv, gi = sn * rinv;
       sG[e] = make_float2(ph.x * gr - ph.y * gi, ph.x * gi + ph.y * gr);
     }

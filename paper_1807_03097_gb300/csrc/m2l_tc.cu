@@ -22,6 +22,7 @@
 // bounded and a wait that runs out sets an error flag for the host.
 #include "efie_internal.h"
 #include "tc.cuh"
+#include "fastmath.cuh"
 
 namespace efie {
 
@@ -54,22 +55,21 @@ __device__ __forceinline__ float2 kernel_entry(float4 g, float2 ph, float kappa,
   if (MODE == 0) {
     float vx = ut.x - xs.x, vy = ut.y - xs.y, vz = ut.z - xs.z;
     float r2 = vx * vx + vy * vy + vz * vz;
-    rinv = rsqrtf(r2);
+    rinv = rsqrt_ftz(r2);
     phs = fmaf(kappa, r2 * rinv, -kappa * g.w);
   } else {
     float ex = xt.x - xs.x, ey = xt.y - xs.y, ez = xt.z - xs.z;
     float num = fmaf(2.f, g.x * ex + g.y * ey + g.z * ez, ex * ex + ey * ey + ez * ez);
     float r2 = g.w * g.w + num;
-    rinv = rsqrtf(r2);
-    phs = kappa * __fdividef(num, r2 * rinv + g.w);
+    rinv = rsqrt_ftz(r2);
+    phs = kappa * num * rcp_ftz(r2 * rinv + g.w);
     if (MODE == 2) {
       float q = rintf(phs * inv2pi);
       phs = fmaf(-q, c1, phs);
       phs = fmaf(-q, c2, phs);
     }
   }
-  float sn, cs;
-  __sincosf(phs, &sn, &cs);
+  const float sn = sin_ftz(phs), cs = cos_ftz(phs);
   const float gr = cs * rinv, gi = sn * rinv;
   return make_float2(ph.x * gr - ph.y * gi, ph.x * gi + ph.y * gr);
 }
