@@ -88,6 +88,11 @@ typedef struct {
                         0 automatic (tensor cores when q <= 10, else FP32 on the CUDA cores),
                         1 FP32 on the CUDA cores, 2 tensor cores (split TF32 with FP32
                         accumulation, q <= 10; EFIE_EINVAL at setup otherwise) */
+  int leaf_dense;    /* 0: the paper's block tree (Algorithm 1); 1: leaf-level variant, in which
+                        an admissible pair of two elements is integrated as an element block
+                        (tensor Gauss, quad_regular points) like a separated near pair instead of
+                        being compressed, when (p+1)^2 < (q+1)^2.  A departure from the paper's
+                        FMM (more accurate, more near-field storage, fewer M2L blocks). */
 } efie_options;
 
 typedef struct {
@@ -200,10 +205,11 @@ efie_status efie_matvec_superspace_batch(efie_ctx *ctx, int nrhs, const double *
 int efie_last_timings(const efie_ctx *ctx, double *out, int n);
 
 /* Figures of the last efie_setup: out[0] wall time of the setup (ms), [1] device time of the
- * near-field quadrature kernel (ms, CUDA events on the context stream), [2] quadrature points
- * it evaluated (Duffy parts x g^4, summed over the pairs integrated), [3] element pairs it
- * integrated (the others are mirrored, B(e', e) = B(e, e')^T).  Returns the number of values
- * written (<= n). */
+ * near-field quadrature of touching element pairs (Sauter-Schwab kernel, ms, CUDA events on
+ * the context stream), [2] quadrature points it evaluated (Duffy parts x g^4 summed over its
+ * pairs), [3] touching pairs it integrated, [4] device time of the separated pairs (tensor
+ * Gauss from element tables, ms), [5] separated pairs integrated; pairs (e', e) with e' > e
+ * are mirrored, B(e', e) = B(e, e')^T.  Returns the number of values written (<= n). */
 int efie_setup_timings(const efie_ctx *ctx, double *out, int n);
 
 /* Far field like efie_far_field, for callers that must not allocate device memory during

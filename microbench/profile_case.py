@@ -1,6 +1,6 @@
 """Run a few matrix-vector products of one configurable case (for profiling a kernel on a
 case smaller than the benchmark's).  Example:
-    python -m paper_1807_03097_gb300.profile_case --p 2 --m 4 --kappa 10 --q 8 --precision mixed --matvecs 3
+    python microbench/profile_case.py --p 2 --m 4 --kappa 10 --q 8 --precision mixed --matvecs 3
 --nrhs R > 1 applies each product to R random right-hand sides at once (batched product).
 """
 import argparse
@@ -24,8 +24,12 @@ def main():
     ap.add_argument("--matvecs", type=int, default=3)
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--m2l-batch", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--lib", default=None, help="path of another build of libefie.so")
     a = ap.parse_args()
-    from paper_1807_03097_gb300 import Solver
+    from paper_1807_03097_gb300 import Solver, efie
+
+    if a.lib:
+        efie.load(a.lib)
     from workloads import geometry as G
 
     geo = {"sphere": G.sphere, "torus": G.torus, "cube": G.cube}[a.geometry]()

@@ -38,6 +38,8 @@ def _load():
     c_int, c_double = ctypes.c_int, ctypes.c_double
     sig = {
         "orc_create": (P, [c_int, I, I, D, D, D, c_int, c_int, c_double, c_int, c_double, c_int, c_int]),
+        "orc_create_variant": (P, [c_int, I, I, D, D, D, c_int, c_int, c_double, c_int, c_double, c_int, c_int,
+                                   c_int]),
         "orc_destroy": (None, [P]),
         "orc_status": (c_int, [P, ctypes.c_char_p, c_int]),
         "orc_num_dofs": (c_int, [P]),
@@ -132,7 +134,7 @@ def dipole_field(kappa, x0, p0, pts):
 class Problem:
     """One discretised EFIE problem in the oracle."""
 
-    def __init__(self, patches, p, m, kappa, q, eta, g_reg=None, g_sing=None):
+    def __init__(self, patches, p, m, kappa, q, eta, g_reg=None, g_sing=None, leaf_dense=False):
         from workloads.geometry import flatten
 
         L = _load()
@@ -142,8 +144,8 @@ class Problem:
         self.p, self.m, self.kappa, self.q, self.eta = p, m, kappa, q, eta
         self.g_reg = g_reg if g_reg is not None else p + 4
         self.g_sing = g_sing if g_sing is not None else p + 4
-        self.h = L.orc_create(len(patches), _i(deg), _i(ncp), _d(knots), _d(cp), _d(w), p, m, kappa, q, eta,
-                              self.g_reg, self.g_sing)
+        self.h = L.orc_create_variant(len(patches), _i(deg), _i(ncp), _d(knots), _d(cp), _d(w), p, m, kappa, q,
+                                      eta, self.g_reg, self.g_sing, int(bool(leaf_dense)))
         if not self.h:
             raise MemoryError("oracle allocation failed")
         buf = ctypes.create_string_buffer(256)

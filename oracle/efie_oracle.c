@@ -171,6 +171,7 @@ typedef struct {
 } Patch;
 
 struct orc_problem {
+  int leaf_dense; /* leaf-level variant of Algorithm 1 (see build_bct) */
   int np;
   Patch *pat;
   int p, m, n, q, nI, greg, gsing;
@@ -488,11 +489,19 @@ static void push_near(orc_problem *P, int e, int e2) {
   ++P->nnear;
 }
 
-/* Algorithm 1, BuildBlockClusterTree. */
+/* Algorithm 1, BuildBlockClusterTree.  Leaf-level variant (leaf_dense): an admissible pair
+ * of two leaves (single elements) is kept as an element block integrated by quadrature instead
+ * of being compressed, when an element carries fewer basis functions per component than a
+ * cluster carries interpolation nodes ((p+1)^2 < (q+1)^2); the paper's tree is leaf_dense = 0. */
 static void build_bct(orc_problem *P, int l, int j, int K, int j2, int K2) {
   int a = cl_id(P, l, j, K), b = cl_id(P, l, j2, K2);
   if (admissible(P, a, b)) {
-    push_far(P, l, a, b);
+    if (P->leaf_dense && l == P->m && (P->p + 1) * (P->p + 1) < P->nI) {
+      int n2 = P->n * P->n;
+      push_near(P, j * n2 + K, j2 * n2 + K2);
+    } else {
+      push_far(P, l, a, b);
+    }
     return;
   }
   if (l == P->m) {
@@ -507,8 +516,15 @@ static void build_bct(orc_problem *P, int l, int j, int K, int j2, int K2) {
 orc_problem *orc_create(int np, const int *deg, const int *ncp, const double *knots,
                         const double *cp, const double *w, int p, int m, double kappa,
                         int q, double eta, int g_reg, int g_sing) {
+  return orc_create_variant(np, deg, ncp, knots, cp, w, p, m, kappa, q, eta, g_reg, g_sing, 0);
+}
+
+orc_problem *orc_create_variant(int np, const int *deg, const int *ncp, const double *knots,
+                                const double *cp, const double *w, int p, int m, double kappa,
+                                int q, double eta, int g_reg, int g_sing, int leaf_dense) {
   orc_problem *P = calloc(1, sizeof(orc_problem));
   if (!P) return NULL;
+  P->leaf_dense = leaf_dense;
   if (np <= 0 || np > 1024 || p < 1 || p > 6 || m < 0 || m > 10 || q < 1 || q > 20 ||
       !(kappa > 0) || !(eta > 0) || g_reg < 1 || g_sing < 1 || g_reg > 60 || g_sing > 60) {
     set_err(P, -1, "invalid argument");

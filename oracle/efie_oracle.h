@@ -31,6 +31,11 @@ typedef struct orc_problem orc_problem;
 orc_problem *orc_create(int np, const int *deg, const int *ncp, const double *knots,
                         const double *cp, const double *w, int p, int m, double kappa,
                         int q, double eta, int g_reg, int g_sing);
+/* As orc_create, with the leaf-level variant of Algorithm 1 when leaf_dense = 1: admissible
+ * pairs of two leaves are integrated as element blocks (tensor Gauss) instead of compressed. */
+orc_problem *orc_create_variant(int np, const int *deg, const int *ncp, const double *knots,
+                                const double *cp, const double *w, int p, int m, double kappa,
+                                int q, double eta, int g_reg, int g_sing, int leaf_dense);
 void orc_destroy(orc_problem *P);
 int orc_status(const orc_problem *P, char *msg, int msglen);
 

@@ -20,14 +20,15 @@ namespace efie {
 // and cluster fields.  When the coupling matrices of the admissible blocks are kept in device
 // memory (m2l_store: the FP64 form by default, the mixed form on request), they are counted
 // with at most 130 admissible source clusters per cluster (the block trees of the sphere and
-// torus workloads have 63 to 115).  np patches, 2^level_m elements per patch direction,
-// degree p, interpolation degree q.
+// torus workloads have 63 to 115).  With the leaf-level variant (leaf_dense) the admissible
+// pairs of two elements are near-field blocks too: at most 130 more per element.  np patches,
+// 2^level_m elements per patch direction, degree p, interpolation degree q.
 inline size_t request_footprint(int np, int level_m, int p, int q, int gmres_restart, int gmres_maxit, bool mixed,
-                                int nrhs, int ndir = 0, int m2l_store = 0) {
+                                int nrhs, int ndir = 0, int m2l_store = 0, int leaf_dense = 0) {
   const size_t n = size_t(1) << level_m, nE = size_t(np) * n * n;
   const size_t p1 = p + 1, nb = 2 * p1 * p1, nI = size_t(q + 1) * (q + 1);
   const size_t ndof = 2 * size_t(np) * (n + p - 1) * (n + p - 1);
-  const size_t near = 30 * nE * nb * nb * (mixed ? 24 : 16);
+  const size_t near = (leaf_dense ? 160 : 30) * nE * nb * nb * (mixed ? 24 : 16);
   const size_t kr = (size_t)std::min(gmres_restart, gmres_maxit) + 1;
   const size_t lockstep = (mixed && nrhs > 1) ? (size_t)std::min(nrhs, 64) : 1;
   const size_t krylov = lockstep * (kr * ndof * 16 + kr * kr * 16);

@@ -164,6 +164,9 @@ struct Ctx {
   float near_quad_ms = 0.f;
   long long near_quad_points = 0;
   int near_quad_pairs = 0;
+  // separated pairs (element-table kernel): kernel time, pairs integrated
+  float near_sep_ms = 0.f;
+  int near_sep_pairs = 0;
   efie_solve_info info{};
   std::string err;
 };

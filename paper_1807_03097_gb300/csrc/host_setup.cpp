@@ -351,11 +351,16 @@ efie_status host_build_trees(Ctx *c) {
   for (int j = np - 1; j >= 0; --j)
     for (int j2 = np - 1; j2 >= 0; --j2) stack.push_back({0, j, 0, j2, 0});
   const int n2 = c->n * c->n;
+  const bool leaf_dense = c->opt.leaf_dense != 0 && c->p1 * c->p1 < c->nI;
   while (!stack.empty()) {
     Item it = stack.back();
     stack.pop_back();
+    // leaf-level variant (option leaf_dense): an admissible pair of two leaves (single
+    // elements) becomes an element block integrated by quadrature instead of an M2L block,
+    // when an element carries fewer Bernstein functions per component than a cluster carries
+    // interpolation nodes ((p+1)^2 < (q+1)^2)
     int a = id(it.l, it.j, it.K), b = id(it.l, it.j2, it.K2);
-    if (admissible(a, b)) {
+    if (admissible(a, b) && !(leaf_dense && it.l == m)) {
       c->far.insert(c->far.end(), {it.l, a, b});
     } else if (it.l == m) {
       c->nearl.insert(c->nearl.end(), {it.j * n2 + it.K, it.j2 * n2 + it.K2});

@@ -252,6 +252,166 @@ __global__ void __launch_bounds__(kQuadThreads) k_near_quad(QuadArgs A) {
   }
 }
 
+// ------------------------------------------------------------------ separated pairs
+// A separated pair (no common point) is integrated with the tensor Gauss rule of g points per
+// direction on each element, so every point of the rule on an element is the same for all of
+// that element's separated pairs.  Element tables hold, per element and Gauss point
+// p = i0 g + i1 (s1 = x_i0, s2 = x_i1): F, d1F, d2F and the weight w_i0 w_i1.
+__global__ void k_elem_table(const PatchDesc *patches, const double *knots, const double4 *cpw, int n, int nE, int g,
+                             const double *gx, const double *gw, double *tab) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int G2 = g * g;
+  if (t >= (long long)nE * G2) return;
+  const int e = (int)(t / G2), p = (int)(t % G2), i0 = p / g, i1 = p % g;
+  const int n2 = n * n, j = e / n2, K = e % n2;
+  int ia = 0, ib = 0;
+  for (int b = 0; b < 15; ++b) {
+    ia |= ((K >> (2 * b)) & 1) << b;
+    ib |= ((K >> (2 * b + 1)) & 1) << b;
+  }
+  const double h = 1.0 / n;
+  double X[3], D1[3], D2[3];
+  dev_patch_eval(patches[j], knots, cpw, (ia + gx[i0]) * h, (ib + gx[i1]) * h, X, D1, D2);
+  double *o = tab + (size_t)t * 10;
+  for (int k = 0; k < 3; ++k) {
+    o[k] = X[k];
+    o[3 + k] = D1[k];
+    o[6 + k] = D2[k];
+  }
+  o[9] = gw[i0] * gw[i1];
+}
+
+constexpr int kSepMaxG = 8;  // largest rule of the separated-pair kernel (shared memory)
+
+struct SepArgs {
+  const NearPair *pairs;
+  const int *list;  // pairs integrated here
+  const int *slot;
+  int nlist, g;
+  const double *tab;  // element tables [nE][g^2][10]
+  const double *gx;   // Gauss points on [0, 1]
+  double kappa, h;
+  double2 *blocks;
+};
+
+// Shared memory (bytes) of k_near_sep<P> for a rule of g points.
+template <int P>
+__host__ __device__ constexpr size_t sep_smem(int g) {
+  return (size_t)g * g * g * g * 16 + (size_t)g * g * (P + 1) * (P + 1) * (8 + 16 + 16) + (size_t)2 * g * g * 10 * 8 +
+         (size_t)2 * g * (P + 1) * 8;
+}
+
+// Separated pair (e, e'), rule of g points per direction: with the weighted kernel matrix
+// Km[i][j] = W_i W_j e^{i kappa r_ij} / (4 pi r_ij) between the Gauss points of the two elements,
+// the block entry of eq. Vkh is
+//   B[(alpha, ab)][(beta, cd)] = sum_{k = 0..3} sum_i T_{alpha k}[i][ab] (Km S_{beta k})[i][cd],
+//   T_{alpha k} = h^2 d_alpha F_k psi_ab (k < 3), h d_alpha psi_ab (k = 3)   (target points),
+//   S_{beta k}  = h^2 d_beta F'_k psi'_cd (k < 3), -kappa^-2 h d_beta psi'_cd (k = 3)   (source).
+// The sum over the source points is done once per (beta, k) for all target points (a g^2 x g^2
+// by g^2 x (p+1)^2 complex-by-real product), which costs g^2 (p+1)^2 of the g^4 (2 (p+1)^2)^2
+// per-point products of the direct form.
+template <int P>
+__global__ void __launch_bounds__(128) k_near_sep(SepArgs A) {
+  constexpr int P1 = P + 1, NS = P1 * P1, NB = 2 * NS, NB2 = NB * NB;
+  constexpr int EPT = (NB2 + 127) / 128;
+  const int g = A.g, G2 = g * g;
+  extern __shared__ double sm[];
+  double2 *Km = reinterpret_cast<double2 *>(sm);  // [G2][G2]
+  double2 *KS = Km + G2 * G2;                     // [G2][NS]
+  double *S = reinterpret_cast<double *>(KS + G2 * NS);  // [G2][NS]
+  double *T = S + G2 * NS;                        // [2 alpha][G2][NS]
+  double *Et = T + 2 * G2 * NS;                   // [G2][10]
+  double *Es = Et + G2 * 10;                      // [G2][10]
+  double *Bx = Es + G2 * 10;                      // [g][P1] Bernstein values at the Gauss points
+  double *dBx = Bx + g * P1;                      // [g][P1] derivatives
+  const int pi = blockIdx.x;
+  if (pi >= A.nlist) return;
+  const int k = A.list[pi];
+  const NearPair pr = A.pairs[k];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < G2 * 10; i += 128) {
+    Et[i] = A.tab[(size_t)pr.e * G2 * 10 + i];
+    Es[i] = A.tab[(size_t)pr.e2 * G2 * 10 + i];
+  }
+  for (int i = tid; i < g; i += 128) {
+    double B[kMaxP1], dB[kMaxP1];
+    dev_bernstein(P, A.gx[i], B, dB);
+    for (int a = 0; a < P1; ++a) {
+      Bx[i * P1 + a] = B[a];
+      dBx[i * P1 + a] = dB[a];
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < G2 * G2; idx += 128) {
+    const int i = idx / G2, j = idx % G2;
+    const double *xt = Et + i * 10, *xs = Es + j * 10;
+    const double dx = xt[0] - xs[0], dy = xt[1] - xs[1], dz = xt[2] - xs[2];
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    double sn, cs;
+    sincos(A.kappa * r, &sn, &cs);
+    const double f = xt[9] * xs[9] / (4.0 * M_PI * r);
+    Km[idx] = make_double2(f * cs, f * sn);
+  }
+  const double h = A.h, h2 = h * h, ik2 = 1.0 / (A.kappa * A.kappa);
+  double2 acc[EPT];
+#pragma unroll
+  for (int t = 0; t < EPT; ++t) acc[t] = make_double2(0.0, 0.0);
+  for (int be = 0; be < 2; ++be) {
+    for (int kk = 0; kk < 4; ++kk) {
+      __syncthreads();
+      // S_{beta k} at the source points, T_{alpha k} (alpha = 0, 1) at the target points
+      for (int idx = tid; idx < G2 * NS; idx += 128) {
+        const int pt = idx / NS, cd = idx % NS, c0 = cd % P1, c1 = cd / P1, i0 = pt / g, i1 = pt % g;
+        const double psi = Bx[i0 * P1 + c0] * Bx[i1 * P1 + c1];
+        const double dps[2] = {dBx[i0 * P1 + c0] * Bx[i1 * P1 + c1], Bx[i0 * P1 + c0] * dBx[i1 * P1 + c1]};
+        const double *xs = Es + pt * 10, *xt = Et + pt * 10;
+        S[idx] = kk < 3 ? h2 * xs[3 + 3 * be + kk] * psi : -ik2 * h * dps[be];
+        T[idx] = kk < 3 ? h2 * xt[3 + kk] * psi : h * dps[0];
+        T[G2 * NS + idx] = kk < 3 ? h2 * xt[6 + kk] * psi : h * dps[1];
+      }
+      __syncthreads();
+      for (int idx = tid; idx < G2 * NS; idx += 128) {
+        const int i = idx / NS, cd = idx % NS;
+        double re = 0.0, im = 0.0;
+        for (int j = 0; j < G2; ++j) {
+          const double2 kv = Km[i * G2 + j];
+          const double sv = S[j * NS + cd];
+          re = fma(kv.x, sv, re);
+          im = fma(kv.y, sv, im);
+        }
+        KS[idx] = make_double2(re, im);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int t = 0; t < EPT; ++t) {
+        const int idx = tid + t * 128;
+        if (idx < NB2) {
+          const int cc = idx / NB, rr = idx % NB;
+          if (cc / NS == be) {
+            const int al = rr / NS, ab = rr % NS, cd = cc % NS;
+            const double *Ta = T + al * G2 * NS;
+            double re = 0.0, im = 0.0;
+            for (int i = 0; i < G2; ++i) {
+              const double tv = Ta[i * NS + ab];
+              const double2 kv = KS[i * NS + cd];
+              re = fma(tv, kv.x, re);
+              im = fma(tv, kv.y, im);
+            }
+            acc[t].x += re;
+            acc[t].y += im;
+          }
+        }
+      }
+    }
+  }
+  double2 *out = A.blocks + (size_t)A.slot[k] * NB2;
+#pragma unroll
+  for (int t = 0; t < EPT; ++t) {
+    const int idx = tid + t * 128;
+    if (idx < NB2) out[idx] = acc[t];
+  }
+}
+
 // B(e2, e) = B(e, e2)^T for the pairs that were not integrated directly.
 __global__ void k_near_mirror(int nb, const int *todo_m, const int *src_of, const int *slot, int nm,
                               double2 *blocks) {
@@ -267,22 +427,28 @@ __global__ void k_near_mirror(int nb, const int *todo_m, const int *src_of, cons
 efie_status dev_near_quadrature(Ctx *c, const std::vector<NearPair> &pairs, const std::vector<int> &mirror) {
   if (c->nnear == 0) return EFIE_OK;
   const int nb = c->nb;
-  std::vector<int> todo, todo_m, src_of;
+  // pairs integrated here (the others are mirrored): touching pairs by the Duffy kernel,
+  // separated pairs by the element-table kernel when its rule fits in shared memory
+  const bool sep_fast = c->gr <= kSepMaxG;
+  std::vector<int> todo, todo_sep, todo_m, src_of;
   for (int k = 0; k < c->nnear; ++k) {
     if (pairs[k].e <= pairs[k].e2) {
-      todo.push_back(k);
+      if (sep_fast && pairs[k].kind == 0) todo_sep.push_back(k);
+      else todo.push_back(k);
     } else {
       todo_m.push_back(k);
       src_of.push_back(mirror[k]);
     }
   }
   NearPair *d_pairs = nullptr;
-  int *d_todo = nullptr, *d_todo_m = nullptr, *d_src_of = nullptr, *d_slot = nullptr;
+  int *d_todo = nullptr, *d_todo_m = nullptr, *d_src_of = nullptr, *d_slot = nullptr, *d_sep = nullptr;
+  double *d_tab = nullptr;
   std::vector<int> slot(c->nnear);
   for (int at = 0; at < c->nnear; ++at) slot[c->near_perm[at]] = at;
   double *d_rule = nullptr;
   EFIE_TRY(dalloc(c, &d_pairs, pairs.size()));
   EFIE_TRY(dalloc(c, &d_todo, todo.size()));
+  EFIE_TRY(dalloc(c, &d_sep, todo_sep.size()));
   EFIE_TRY(dalloc(c, &d_todo_m, todo_m.size()));
   EFIE_TRY(dalloc(c, &d_src_of, src_of.size()));
   EFIE_TRY(dalloc(c, &d_rule, 2 * (size_t)(c->gr + c->gs)));
@@ -290,7 +456,9 @@ efie_status dev_near_quadrature(Ctx *c, const std::vector<NearPair> &pairs, cons
   cudaStream_t s0 = c->stream;
   EFIE_CUDA(cudaMemcpyAsync(d_slot, slot.data(), 4 * slot.size(), cudaMemcpyHostToDevice, s0));
   EFIE_CUDA(cudaMemcpyAsync(d_pairs, pairs.data(), sizeof(NearPair) * pairs.size(), cudaMemcpyHostToDevice, s0));
-  EFIE_CUDA(cudaMemcpyAsync(d_todo, todo.data(), 4 * todo.size(), cudaMemcpyHostToDevice, s0));
+  if (!todo.empty()) EFIE_CUDA(cudaMemcpyAsync(d_todo, todo.data(), 4 * todo.size(), cudaMemcpyHostToDevice, s0));
+  if (!todo_sep.empty())
+    EFIE_CUDA(cudaMemcpyAsync(d_sep, todo_sep.data(), 4 * todo_sep.size(), cudaMemcpyHostToDevice, s0));
   if (!todo_m.empty()) {
     EFIE_CUDA(cudaMemcpyAsync(d_todo_m, todo_m.data(), 4 * todo_m.size(), cudaMemcpyHostToDevice, s0));
     EFIE_CUDA(cudaMemcpyAsync(d_src_of, src_of.data(), 4 * src_of.size(), cudaMemcpyHostToDevice, s0));
@@ -323,6 +491,7 @@ efie_status dev_near_quadrature(Ctx *c, const std::vector<NearPair> &pairs, cons
   A.h = 1.0 / c->n;
   A.blocks = c->d_nblk;
   c->near_quad_pairs = (int)todo.size();
+  c->near_sep_pairs = (int)todo_sep.size();
   c->near_quad_points = 0;
   for (int k : todo) {
     const int kind = pairs[k].kind, g = kind == 0 ? c->gr : c->gs;
@@ -334,9 +503,9 @@ efie_status dev_near_quadrature(Ctx *c, const std::vector<NearPair> &pairs, cons
   for (const PatchDesc &pd : c->patches) gdeg = std::max(gdeg, std::max(pd.deg[0], pd.deg[1]));
   const int GDsel = gdeg <= 2 ? 2 : (gdeg <= 4 ? 4 : 8);
   EFIE_CUDA(cudaEventRecord(c->tm.ev[7], c->stream));
-  bool launched = false;
+  bool launched = A.ntodo == 0;
 #define EFIE_QUAD(PP, GG)                                                                                 \
-  if (c->p == PP && GDsel == GG) {                                                                        \
+  if (!launched && c->p == PP && GDsel == GG) {                                                           \
     const size_t smem = sizeof(double) * quad_smem_doubles<PP>();                                         \
     EFIE_CUDA(cudaFuncSetAttribute(k_near_quad<PP, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                    (int)smem));                                                          \
@@ -355,6 +524,46 @@ efie_status dev_near_quadrature(Ctx *c, const std::vector<NearPair> &pairs, cons
   }
   EFIE_CUDA(cudaGetLastError());
   EFIE_CUDA(cudaEventRecord(c->tm.ev[6], c->stream));
+  c->near_sep_ms = 0.f;
+  if (!todo_sep.empty()) {
+    // element tables at the g_reg x g_reg Gauss points, then one block per separated pair
+    const int g = c->gr;
+    EFIE_TRY(dalloc(c, &d_tab, (size_t)c->nE * g * g * 10));
+    const long long tot = (long long)c->nE * g * g;
+    k_elem_table<<<(unsigned)((tot + 127) / 128), 128, 0, s0>>>(c->d_patches, c->d_knots, c->d_cpw, c->n, c->nE, g,
+                                                              d_rule, d_rule + g, d_tab); ++c->launches;
+    SepArgs S;
+    S.pairs = d_pairs;
+    S.list = d_sep;
+    S.slot = d_slot;
+    S.nlist = (int)todo_sep.size();
+    S.g = g;
+    S.tab = d_tab;
+    S.gx = d_rule;
+    S.kappa = c->kappa;
+    S.h = 1.0 / c->n;
+    S.blocks = c->d_nblk;
+    switch (c->p) {
+#define EFIE_SEP(PP)                                                                                   \
+  case PP: {                                                                                           \
+    const size_t smem = sep_smem<PP>(g);                                                               \
+    EFIE_CUDA(cudaFuncSetAttribute(k_near_sep<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    k_near_sep<PP><<<S.nlist, 128, smem, s0>>>(S);                                                     \
+    ++c->launches;                                                                                     \
+    break;                                                                                             \
+  }
+      EFIE_SEP(1)
+      EFIE_SEP(2)
+      EFIE_SEP(3)
+      EFIE_SEP(4)
+#undef EFIE_SEP
+      default:
+        c->err = "device near-field quadrature supports 1 <= p <= 4";
+        return EFIE_EINVAL;
+    }
+    EFIE_CUDA(cudaGetLastError());
+  }
+  EFIE_CUDA(cudaEventRecord(c->tm.ev[5], c->stream));
   if (!todo_m.empty()) {
     long long tot = (long long)todo_m.size() * nb * nb;
     k_near_mirror<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(nb, d_todo_m, d_src_of, d_slot,
@@ -363,12 +572,15 @@ efie_status dev_near_quadrature(Ctx *c, const std::vector<NearPair> &pairs, cons
   }
   EFIE_CUDA(cudaStreamSynchronize(c->stream));
   cudaEventElapsedTime(&c->near_quad_ms, c->tm.ev[7], c->tm.ev[6]);
+  if (!todo_sep.empty()) cudaEventElapsedTime(&c->near_sep_ms, c->tm.ev[6], c->tm.ev[5]);
   dfree(c, d_pairs);
   dfree(c, d_todo);
   dfree(c, d_todo_m);
   dfree(c, d_src_of);
   dfree(c, d_rule);
   dfree(c, d_slot);
+  dfree(c, d_sep);
+  dfree(c, d_tab);
   return EFIE_OK;
 }
 

@@ -65,7 +65,8 @@ struct Server {
 
 size_t estimate_footprint(const Job &j) {
   return efie::request_footprint(j.np, j.opt.level_m, j.opt.p, j.opt.q, j.opt.gmres_restart, j.opt.gmres_maxit,
-                                 j.opt.precision == EFIE_MIXED_FP32, j.nrhs, j.ndir, j.opt.m2l_store);
+                                 j.opt.precision == EFIE_MIXED_FP32, j.nrhs, j.ndir, j.opt.m2l_store,
+                                 j.opt.leaf_dense);
 }
 
 void run_job(Server *S, Job &j) {

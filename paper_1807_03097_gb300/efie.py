@@ -40,7 +40,7 @@ class EfieOptions(ctypes.Structure):
                 ("eta", ctypes.c_double), ("precision", ctypes.c_int), ("quad_regular", ctypes.c_int),
                 ("quad_singular", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("gmres_tol", ctypes.c_double),
                 ("gmres_maxit", ctypes.c_int), ("tol_is_relative", ctypes.c_int), ("m2l_store", ctypes.c_int),
-                ("m2l_batch", ctypes.c_int)]
+                ("m2l_batch", ctypes.c_int), ("leaf_dense", ctypes.c_int)]
 
 
 class EfieSolveInfo(ctypes.Structure):
@@ -335,11 +335,12 @@ class Solver:
         return st, self._L.efie_last_error(self.h).decode()
 
     def setup_timings(self):
-        """Figures of the last setup: wall ms, near-field quadrature kernel ms, quadrature points,
-        element pairs integrated."""
-        out = np.zeros(4)
-        n = self._L.efie_setup_timings(self.h, _d(out), 4)
-        return dict(zip(["setup_ms", "near_quad_ms", "near_quad_points", "near_quad_pairs"], out[:n]))
+        """Figures of the last setup: wall ms; touching-pair quadrature kernel ms, its quadrature
+        points and pairs; separated-pair kernel ms and pairs."""
+        out = np.zeros(6)
+        n = self._L.efie_setup_timings(self.h, _d(out), 6)
+        return dict(zip(["setup_ms", "near_quad_ms", "near_quad_points", "near_quad_pairs", "near_sep_ms",
+                         "near_sep_pairs"], out[:n]))
 
     def last_timings(self):
         out = np.zeros(7)

@@ -429,3 +429,47 @@ def test_fmm_rows_equal_rows_of_the_full_superspace_product():
     rows = r.fmm_rows(xs, elems)
     scale = np.abs(ys).max()
     assert np.abs(rows - ys[elems]).max() < 1e-13 * scale
+
+
+# ---------------------------------------------------------------- leaf-level variant (dense leaf blocks)
+def test_leaf_dense_variant_equals_dense_when_every_far_pair_is_a_leaf_pair():
+    """Variant of Algorithm 1 in which admissible pairs of two elements are integrated as element
+    blocks: on the sphere at m = 1, eta = 1.6 every admissible pair is a pair of leaves, so the
+    variant's product is the dense Galerkin product (same quadrature rules), and the paper's FMM
+    product is not."""
+    kw = dict(p=1, m=1, kappa=2.0, q=4, eta=1.6)
+    fmm = O.Problem(G.sphere(), **kw)
+    var = O.Problem(G.sphere(), leaf_dense=True, **kw)
+    far = fmm.far_pairs()
+    assert len(far) > 0 and np.all(far[:, 0] == kw["m"])
+    assert len(var.far_pairs()) == 0
+    assert len(var.near_pairs()) == len(fmm.near_pairs()) + len(far)
+    rng = np.random.default_rng(70)
+    x = rng.standard_normal(var.ndof) + 1j * rng.standard_normal(var.ndof)
+    yd = var.dense_matvec(x)[0]
+    yv = var.fmm_matvec(x)[0]
+    yf = fmm.fmm_matvec(x)[0]
+    assert np.linalg.norm(yv - yd) < 1e-13 * np.linalg.norm(yd)
+    assert np.linalg.norm(yf - yd) > 1e-6 * np.linalg.norm(yd)
+
+
+def test_leaf_dense_variant_moves_only_leaf_pairs_and_is_closer_to_dense():
+    kw = dict(p=1, m=2, kappa=2.0, q=3, eta=1.6)
+    fmm = O.Problem(G.sphere(), **kw)
+    var = O.Problem(G.sphere(), leaf_dense=True, **kw)
+    far, farv = fmm.far_pairs(), var.far_pairs()
+    leaf = far[far[:, 0] == kw["m"]]
+    assert len(leaf) > 0 and len(farv) == len(far) - len(leaf) > 0
+    assert set(map(tuple, farv)) == set(map(tuple, far[far[:, 0] < kw["m"]]))
+    # the moved pairs, as element pairs, complete the near list
+    n2 = (1 << kw["m"]) ** 2
+    off = 6 * sum(4 ** l for l in range(kw["m"]))  # first leaf cluster id
+    moved = {(int(t) - off, int(s) - off) for _, t, s in leaf}
+    assert set(map(tuple, var.near_pairs())) == set(map(tuple, fmm.near_pairs())) | moved
+    assert all(0 <= a < 6 * n2 and 0 <= b < 6 * n2 for a, b in moved)
+    rng = np.random.default_rng(71)
+    x = rng.standard_normal(var.ndof) + 1j * rng.standard_normal(var.ndof)
+    yd = var.dense_matvec(x)[0]
+    ev = np.linalg.norm(var.fmm_matvec(x)[0] - yd)
+    ef = np.linalg.norm(fmm.fmm_matvec(x)[0] - yd)
+    assert ev < ef, (ev, ef)  # the FMM error left comes from the upper-level blocks
