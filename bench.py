@@ -30,7 +30,9 @@ Other workloads (--workload):
   serving  32 Poisson-arriving scattering requests through the serving loop: solves/s and
            p50/p99 latency;
   batch    256 independent solves of a seeded mix of spheres, cubes and tori through the
-           serving loop: solves/s.
+           serving loop: solves/s;
+  tesla    the paper's Tesla settings (p = 4, eta = 0.1, q = 14) on a synthetic 232-patch
+           surface of revolution: setup, matvec/s, mixed-vs-FP64 error, one solve.
 """
 from __future__ import annotations
 
@@ -453,7 +455,10 @@ def run_gpu(args):
                   "achieved": quad_flop / (st_["near_quad_ms"] * 1e-3) / 1e12, "near_quad_ms": st_["near_quad_ms"],
                   "setup_ms": st_["setup_ms"], "work": f"{st_['near_quad_points']:.3e} quadrature points x "
                                                         f"{s.nb}^2 entries x 8 flop",
-                  "pairs_integrated": int(st_["near_quad_pairs"])}
+                  "pairs_integrated": int(st_["near_quad_pairs"]),
+                  "separated_pairs_ms": st_.get("near_sep_ms"), "separated_pairs": int(st_.get("near_sep_pairs", 0)),
+                  "note": "touching pairs (Sauter-Schwab); the separated near pairs run in a second kernel "
+                          "(element tables), timed separately"}
     if pk_alu:
         roof_setup["peak"] = pk_alu["dfma_flops"] / 1e12
         roof_setup["frac"] = roof_setup["achieved"] / roof_setup["peak"]
@@ -478,9 +483,13 @@ def run_gpu(args):
     s64.close()
     s_e2e.close()
 
+    variant = None
+    if not args.no_variant:
+        variant = variant_leg(args, stream, geo, kw, prec, d_inc, p_inc, dirs, e_mixed)
     extra = {}
     if rank == 0 and world == 1 and not args.no_extras:
         extra["multi"] = multi_leg(args, steps=args.multi_steps, pk_alu=pk_alu)
+        extra["tesla_settings"] = tesla_leg(args)
         extra["serving"] = serving_leg(args)
 
     cpu = None
@@ -506,6 +515,7 @@ def run_gpu(args):
             "matvec_per_s_fp64": 1000.0 / mv64["total"], "matvec_ms_phases_fp64": mv64,
             "matvec_rel_err_vs_fp64": err_vs_fp64,
             "fp64_solve": fp64,
+            "variant_dense_leaf": variant,
             "roofline": roof, "roofline_near": near_roof, "roofline_setup": roof_setup,
             "peaks_measured": pk_alu, "peaks_hbm_bf16": {k: pk.get(k) for k in ("hbm_gbs", "bf16_tflops",
                                                                                "bf16_tflops_sustained")},
@@ -521,6 +531,53 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def variant_leg(args, stream, geo, kw, prec, d_inc, p_inc, dirs, e_ref):
+    """The leaf-level variant of the block tree (admissible pairs of two elements integrated as
+    element blocks instead of compressed; option leaf_dense, a departure from the paper's FMM)
+    on the same workload and form: solves/s over whole steps (setup, solve, far field), product
+    phases, and the far-field difference from the paper's FMM solution."""
+    import torch
+    from paper_1807_03097_gb300 import Solver
+
+    s = Solver(geo, stream=stream.cuda_stream, precision=prec, leaf_dense=1, **kw)
+    N = s.ndof
+    wdev = torch.zeros((1, N), dtype=torch.complex128, device="cuda")
+    edev = torch.zeros((1, 64, 3), dtype=torch.complex128, device="cuda")
+    for _ in range(2):
+        s.setup()
+        s.solve_plane_waves(d_inc, p_inc, out=wdev)
+        s.far_field(wdev[0], dirs, out=edev)
+    steps = 3
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its = []
+    for _ in range(steps):
+        s.setup()
+        _, info, _ = s.solve_plane_waves(d_inc, p_inc, out=wdev)
+        s.far_field(wdev[0], dirs, out=edev)
+        its.append(info.iterations)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / steps
+    st = s.setup_timings()
+    x = torch.from_numpy(np.random.default_rng(0).standard_normal(N) + 0j).cuda()
+    y = torch.empty_like(x)
+    ph = []
+    for i in range(13):
+        s.matvec(x, out=y)
+        if i >= 3:
+            ph.append(s.last_timings())
+    mv = {k: statistics.median([p[k] for p in ph]) for k in ph[0]}
+    e = edev[0].cpu().numpy()
+    out = {"solves_per_s": 1000.0 / ms, "ms_per_step": ms, "gmres_iterations": int(np.median(its)),
+           "setup_ms": st["setup_ms"], "separated_pairs": int(st["near_sep_pairs"]),
+           "separated_pairs_ms": st["near_sep_ms"], "far_pairs": int(s.nfar), "near_pairs": int(s.nnear),
+           "matvec_per_s": 1000.0 / mv["total"], "matvec_ms_phases": mv,
+           "far_field_rel_diff_vs_fmm": float(np.abs(e - e_ref).max() / np.abs(e_ref).max()),
+           "note": "timed on the host clock around synchronous calls, 3 steps after 2 warm-up steps"}
+    s.close()
+    return out
 
 
 # ---------------------------------------------------------------------------- many right-hand sides
@@ -647,6 +704,68 @@ def multi_leg(args, steps=None, pk_alu=None):
 def run_multi(args):
     pk_alu, _ = measured_peaks()
     print(json.dumps(multi_leg(args, pk_alu=pk_alu)))
+    return 0
+
+
+# ---------------------------------------------------------------------------- Tesla settings
+TESLA = {
+    "workload": "multicell232_nurbs_p4_n2_kappa4_q14_eta0.1",
+    "geometry": "synthetic surface of revolution of 9 bulges (232 rational biquadratic patches; stand-in for "
+                "the paper's multi-cell cavities, whose geometry is not available)",
+    "p": 4, "elements_per_patch": "2x2", "level_m": 1, "kappa": 4.0, "q": 14, "eta": 0.1, "gmres_tol": 1e-6,
+    "incident": "dir +z, pol x", "precision": "mixed",
+}
+
+
+def tesla_leg(args):
+    """The paper's Tesla settings (p = 4, eta = 0.1, q = 14) on the 232-patch stand-in: setup,
+    matvec/s of the mixed and FP64 forms, their difference, and one mixed solve."""
+    import torch
+    from paper_1807_03097_gb300 import Solver
+
+    w = TESLA
+    geo = G.multicell()
+    stream = torch.cuda.current_stream()
+    kw = dict(p=w["p"], level_m=w["level_m"], kappa=w["kappa"], q=w["q"], eta=w["eta"], gmres_tol=w["gmres_tol"],
+              gmres_maxit=3000)
+    t0 = time.perf_counter()
+    s = Solver(geo, stream=stream.cuda_stream, precision=1, **kw)
+    setup_s = time.perf_counter() - t0
+    N = s.ndof
+    x = torch.from_numpy(np.random.default_rng(0).standard_normal(N) + 1j * np.random.default_rng(1).standard_normal(N)).cuda()
+    y = torch.empty_like(x)
+    ph = []
+    for i in range(8):
+        s.matvec(x, out=y)
+        if i >= 3:
+            ph.append(s.last_timings())
+    mv = {k: statistics.median([p_[k] for p_ in ph]) for k in ph[0]}
+    y32 = y.clone()
+    s64 = Solver(geo, stream=stream.cuda_stream, precision=0, **kw)
+    y64 = torch.empty_like(x)
+    ph64 = []
+    for i in range(3):
+        s64.matvec(x, out=y64)
+        ph64.append(s64.last_timings())
+    mv64 = {k: statistics.median([p_[k] for p_ in ph64]) for k in ph64[0]}
+    err = float(torch.linalg.norm(y32 - y64) / torch.linalg.norm(y64))
+    s64.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, info, st = s.solve_plane_waves(np.array([[0, 0, 1.0]]), np.array([[1.0, 0, 0]]))
+    torch.cuda.synchronize()
+    solve_s = time.perf_counter() - t0
+    out = {"config": TESLA, "ndof": int(N), "far_pairs": int(s.nfar), "near_pairs": int(s.nnear),
+           "setup_s": setup_s, "matvec_per_s": 1000.0 / mv["total"], "matvec_ms_phases": mv,
+           "matvec_per_s_fp64": 1000.0 / mv64["total"], "matvec_rel_err_vs_fp64": err,
+           "solve_s": solve_s, "gmres_iterations": int(info.iterations), "converged": bool(info.converged),
+           "status": int(st)}
+    s.close()
+    return out
+
+
+def run_tesla(args):
+    print(json.dumps(tesla_leg(args)))
     return 0
 
 
@@ -800,11 +919,12 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload only: skip the 64-right-hand-side torus and serving legs")
     ap.add_argument("--no-fp64-solve", action="store_true", help="skip the plain FP64 solve of the workload")
+    ap.add_argument("--no-variant", action="store_true", help="skip the leaf-level block-tree variant")
     ap.add_argument("--multi-steps", type=int, default=3, help="timed batched products of the torus leg")
     ap.add_argument("--ref-iterations", type=int, default=WORKLOAD_ITERATIONS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-steps", action="store_true", help="time the steps only (for launch-list profiling)")
-    ap.add_argument("--workload", default="solve", choices=["solve", "serving", "multi", "batch"])
+    ap.add_argument("--workload", default="solve", choices=["solve", "serving", "multi", "batch", "tesla"])
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--budget-gib", type=int, default=192, help="serving: device-memory budget of the admission")
     ap.add_argument("--check-fp64", action="store_true",
@@ -820,6 +940,8 @@ def main():
         return run_multi(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "tesla":
+        return run_tesla(args)
     return run_gpu(args)
 
 

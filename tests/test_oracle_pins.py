@@ -473,3 +473,28 @@ def test_leaf_dense_variant_moves_only_leaf_pairs_and_is_closer_to_dense():
     ev = np.linalg.norm(var.fmm_matvec(x)[0] - yd)
     ef = np.linalg.norm(fmm.fmm_matvec(x)[0] - yd)
     assert ev < ef, (ev, ef)  # the FMM error left comes from the upper-level blocks
+
+
+# ---------------------------------------------------------------- many-patch stand-in (f2 settings)
+def test_multicell_geometry_area_by_pappus_and_closedness():
+    """The 232-patch surface of revolution: the oracle's surface area equals Pappus' area
+    2 pi int rho ds of the profile (1-D Gauss on each quadratic profile piece), the DOF count is
+    2 N (n + p - 1)^2 of a closed surface, and int div w = 0 for a random current."""
+    geo = G.multicell()
+    assert len(geo) == 232
+    pr = O.Problem(geo, p=1, m=0, kappa=1.0, q=2, eta=1.6, g_reg=16)  # area rule: 16 x 16 Gauss per element
+    assert pr.ndof == 2 * 232 * (1 + 1 - 1) ** 2
+    # profile pieces: the s2 control points of every 4th patch (one quarter turn), rho = |(x, y)|
+    x, w = np.polynomial.legendre.leggauss(20)
+    t, w = (x + 1) / 2, w / 2
+    area = 0.0
+    for pt in geo[::4]:
+        c = pt["cp"][:, 0, :]  # [b][xyz] at the quarter's start angle (y = 0)
+        rho, z = c[:, 0], c[:, 2]
+        B = np.stack([(1 - t) ** 2, 2 * t * (1 - t), t * t], 1)
+        dB = np.stack([-2 * (1 - t), 2 - 4 * t, 2 * t], 1)
+        area += 2 * math.pi * np.sum(w * (B @ rho) * np.hypot(dB @ rho, dB @ z))
+    assert abs(pr.area() - area) < 1e-10 * area
+    rng = np.random.default_rng(72)
+    xs = rng.standard_normal(pr.ndof) + 1j * rng.standard_normal(pr.ndof)
+    assert abs(pr.div_integral(xs)) < 1e-12 * np.abs(xs).sum()

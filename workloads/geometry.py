@@ -146,6 +146,63 @@ def torus(R: float = 2.0, r: float = 0.5):
     return out
 
 
+def _split_quadratic(ctrl, parts):
+    """Split a quadratic Bezier curve (ctrl[3][2], polynomial) into `parts` equal parameter
+    pieces by de Casteljau subdivision; returns the pieces' control points."""
+    out = []
+    for k in range(parts):
+        t0, t1 = k / parts, (k + 1) / parts
+
+        def at(t):
+            return (1 - t) ** 2 * ctrl[0] + 2 * t * (1 - t) * ctrl[1] + t * t * ctrl[2]
+
+        def d(t):
+            return 2 * (1 - t) * (ctrl[1] - ctrl[0]) + 2 * t * (ctrl[2] - ctrl[1])
+
+        p0, p2 = at(t0), at(t1)
+        p1 = p0 + d(t0) * (t1 - t0) / 2.0
+        out.append(np.stack([p0, p1, p2]))
+    return out
+
+
+def multicell(cells: int = 9, length: float = 1.0, r_eq: float = 0.9, r_iris: float = 0.35, r_in: float = 0.2,
+              split: int = 2):
+    """Synthetic many-patch surface of revolution (stand-in for multi-cell cavities): a closed
+    profile in the (rho, z) half-plane, traversed counterclockwise, revolved about the z axis in
+    four rational quarter turns.  The outer wall is `cells` bulges, each two quadratic arcs
+    iris -> equator -> iris (horizontal tangent at the irises, vertical at the equator), then
+    a flat end, a straight inner wall at rho = r_in and the other flat end; every profile piece
+    (the bulge arcs split in `split` parts) gives 4 patches of bidegree (2, 2).  The default
+    has 4 (2 cells split + 2 cells + 4) = 232 patches."""
+    segs = []
+    for c in range(cells):
+        z0 = c * length
+        up = np.array([[r_iris, z0], [r_eq, z0], [r_eq, z0 + length / 2]])
+        down = np.array([[r_eq, z0 + length / 2], [r_eq, z0 + length], [r_iris, z0 + length]])
+        segs += _split_quadratic(up, split) + _split_quadratic(down, split)
+
+    def line(a, b, parts):
+        a, b = np.asarray(a, float), np.asarray(b, float)
+        return _split_quadratic(np.stack([a, (a + b) / 2, b]), parts)
+
+    top = cells * length
+    segs += line((r_iris, top), (r_in, top), 2)
+    segs += line((r_in, top), (r_in, 0.0), 2 * cells)
+    segs += line((r_in, 0.0), (r_iris, 0.0), 2)
+    rev = _quarter_arcs(1.0)
+    out = []
+    for pc in segs:                  # s2 direction: the profile piece
+        for (rc, rw) in rev:         # s1 direction: a quarter turn
+            cp = np.zeros((3, 3, 3))
+            w = np.zeros((3, 3))
+            for b in range(3):
+                for a in range(3):
+                    cp[b, a] = [pc[b, 0] * rc[a, 0], pc[b, 0] * rc[a, 1], pc[b, 1]]
+                    w[b, a] = rw[a]
+            out.append(_patch((2, 2), cp, w))
+    return out
+
+
 def plane_waves(n: int, seed: int):
     """n seeded incident directions, uniform on S^2 (normalised Gaussians), each with a
     seeded random unit polarisation orthogonal to it."""
