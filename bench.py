@@ -727,7 +727,7 @@ def tesla_leg(args):
     geo = G.multicell()
     stream = torch.cuda.current_stream()
     kw = dict(p=w["p"], level_m=w["level_m"], kappa=w["kappa"], q=w["q"], eta=w["eta"], gmres_tol=w["gmres_tol"],
-              gmres_maxit=3000)
+              gmres_maxit=1000)
     t0 = time.perf_counter()
     s = Solver(geo, stream=stream.cuda_stream, precision=1, **kw)
     setup_s = time.perf_counter() - t0
@@ -759,7 +759,9 @@ def tesla_leg(args):
            "setup_s": setup_s, "matvec_per_s": 1000.0 / mv["total"], "matvec_ms_phases": mv,
            "matvec_per_s_fp64": 1000.0 / mv64["total"], "matvec_rel_err_vs_fp64": err,
            "solve_s": solve_s, "gmres_iterations": int(info.iterations), "converged": bool(info.converged),
-           "status": int(st)}
+           "relative_residual": float(info.residual), "status": int(st),
+           "note": "unpreconditioned GMRES at p = 4 converges slowly (the paper's Tab. 2: up to ~8000 iterations); "
+                   "the solve is capped at 1000 iterations and its residual reported"}
     s.close()
     return out
 

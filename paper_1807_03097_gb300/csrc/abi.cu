@@ -34,6 +34,9 @@ void release_device(Ctx *c) {
   dfree(c, c->d_mom); dfree(c, c->d_src); dfree(c, c->d_acc); dfree(c, c->d_loc);
   dfree(c, c->d_momf); dfree(c, c->d_srcf); dfree(c, c->d_locf); dfree(c, c->d_accm); dfree(c, c->d_accf);
   dfree(c, c->d_nodeX4); dfree(c, c->d_pgeo); dfree(c, c->d_pph); dfree(c, c->d_far_tgt);
+  dfree(c, c->d_own_ptr); dfree(c, c->d_own_src); dfree(c, c->d_own_slot); dfree(c, c->d_own_targets);
+  dfree(c, c->d_par_ptr); dfree(c, c->d_par_slot); dfree(c, c->d_red); dfree(c, c->d_own_pgeo);
+  dfree(c, c->d_own_pph); dfree(c, c->d_back);
   dfree(c, c->d_K);
   c->k_stored = false;
   dfree(c, c->d_V); dfree(c, c->d_H); dfree(c, c->d_h); dfree(c, c->d_h2); dfree(c, c->d_part); dfree(c, c->d_gs);

@@ -102,6 +102,19 @@ struct Ctx {
   int n_m2l_targets = 0;
   int m2l_mode = 2;  // FP32 M2L phase: 0 direct kappa r - kappa r0, 1 split, 2 split + explicit reduction
   int *d_far_tgt = nullptr;   // target cluster of every far pair (CSR order)
+  // unordered far pairs of the single right-hand-side FP32 M2L: each pair {t, s} is owned by
+  // one of its clusters (balanced), which receives K_ts w_s; the other receives K_ts^T w_t
+  // through the pair's slot of d_back, summed per cluster in a fixed order
+  int npairs = 0;
+  int *d_own_ptr = nullptr, *d_own_src = nullptr, *d_own_slot = nullptr;  // CSR by owner cluster
+  int *d_own_targets = nullptr;  // owners with at least one pair, most pairs first
+  int n_own_targets = 0;
+  int *d_par_ptr = nullptr, *d_par_slot = nullptr;  // CSR by the non-owner cluster
+  int *d_red = nullptr;          // clusters with any far pair
+  int n_red = 0;
+  float4 *d_own_pgeo = nullptr;  // per owned pair: c_owner - c_other, r0
+  float2 *d_own_pph = nullptr;   // per owned pair: e^{i kappa r0} / (4 pi)
+  float4 *d_back = nullptr;      // [npairs][nI][2]: K^T contributions to the non-owner
   void *d_K = nullptr;        // stored coupling matrices [pair][m'][m] (double2 or float2)
   bool k_stored = false;
   // several right-hand sides (mixed form)

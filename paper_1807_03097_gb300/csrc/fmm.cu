@@ -520,6 +520,200 @@ __global__ void __launch_bounds__(128, (NT <= 3 ? 4 : 2)) k_m2l_f32w(const int *
   }
 }
 
+// FP32 M2L over unordered admissible pairs: every coupling tile K_ts (entries as in
+// k_m2l_f32w) is evaluated once and applied in both directions, acc_t += K_ts w_s and
+// acc_s += K_ts^T w_t (K is symmetric in the two clusters: it depends on |x_t - x_s| only).
+// One warp per owner cluster t; lane l < T owns the target rows m = l + j T (j < NT).  The
+// tile is swept along its diagonals: at step k lane l takes the source column c = (l + k) mod
+// nI, so the row sums stay in the lane (forward) and the column sum of column c moves one lane
+// down per step (shuffle) while it collects the rows of every lane (backward); lane 0 stores a
+// column when its sum has passed all lanes, and the columns that started mid-way are completed
+// after the sweep.  Column sums of a pair go to the pair's slot of `back`; a second kernel adds
+// the slots of every non-owner cluster in a fixed order.  Row sums enter running sums over the
+// pairs with two-sum compensation (shared memory, [NT][16][32] per warp).
+template <int NT, int MODE>
+__global__ void __launch_bounds__(128, (NT <= 3 ? 4 : 2)) k_m2l_sym(
+    const int *__restrict__ targets, int ntarget, const int *__restrict__ optr, const int *__restrict__ osrc,
+    const int *__restrict__ oslot, const float4 *__restrict__ pgeo, const float2 *__restrict__ pph, int nI,
+    float kappa, const float4 *__restrict__ nodeX4, const float4 *__restrict__ src, float4 *__restrict__ acc,
+    float4 *__restrict__ back) {
+  extern __shared__ float4 sm4[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wg = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (wg >= ntarget) return;
+  float4 *sT = sm4 + (size_t)wib * (6 * nI + 4 * 32 * NT);
+  float4 *sC = sT + nI;      // [nI] (-2x, -2y, -2z, b) of the source nodes
+  float4 *sW = sC + nI;      // [nI][2] phase-rotated source fields
+  float4 *sO = sW + 2 * nI;  // [nI][2] column sums of the pair
+  float *sA = reinterpret_cast<float *>(sO + 2 * nI);
+  const int t = targets[wg];
+  const int T = (nI + NT - 1) / NT;
+  const bool act = lane < T;
+  for (int i = lane; i < nI; i += 32) sT[i] = nodeX4[(size_t)t * nI + i];
+#pragma unroll
+  for (int j = 0; j < NT; ++j)
+#pragma unroll
+    for (int q = 0; q < 16; ++q) sA[(j * 16 + q) * 32 + lane] = 0.f;
+  const float inv2pi = 0.15915494309189535f, c1 = 6.28318548202514648f, c2 = -1.7484555e-7f;
+  const float kinv = 1.f / kappa;
+  for (int kp = optr[t]; kp < optr[t + 1]; ++kp) {
+    const int s = osrc[kp], u = oslot[kp];
+    const float4 g = pgeo[kp];
+    const float2 ph = pph[kp];
+    __syncwarp();
+    for (int i = lane; i < nI; i += 32) {
+      const float4 x = nodeX4[(size_t)s * nI + i];
+      const float bb = MODE == 0 ? x.x * x.x + x.y * x.y + x.z * x.z
+                                 : x.x * x.x + x.y * x.y + x.z * x.z - 2.f * (g.x * x.x + g.y * x.y + g.z * x.z);
+      sC[i] = make_float4(-2.f * x.x, -2.f * x.y, -2.f * x.z, bb);
+      const float4 a = src[2 * ((size_t)s * nI + i)], b = src[2 * ((size_t)s * nI + i) + 1];
+      sW[2 * i] = make_float4(ph.x * a.x - ph.y * a.y, ph.x * a.y + ph.y * a.x, ph.x * a.z - ph.y * a.w,
+                              ph.x * a.w + ph.y * a.z);
+      sW[2 * i + 1] = make_float4(ph.x * b.x - ph.y * b.y, ph.x * b.y + ph.y * b.x, ph.x * b.z - ph.y * b.w,
+                                  ph.x * b.w + ph.y * b.z);
+    }
+    __syncwarp();
+    float U[NT][4], wt[NT][8], at[NT][8];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const int m = lane + j * T;
+      const bool ok = act && m < nI;
+      const float4 x = sT[ok ? m : 0];
+      if (MODE == 0) {
+        U[j][0] = g.x + x.x;
+        U[j][1] = g.y + x.y;
+        U[j][2] = g.z + x.z;
+        U[j][3] = U[j][0] * U[j][0] + U[j][1] * U[j][1] + U[j][2] * U[j][2];
+      } else {
+        U[j][0] = x.x;
+        U[j][1] = x.y;
+        U[j][2] = x.z;
+        U[j][3] = x.x * x.x + x.y * x.y + x.z * x.z + 2.f * (g.x * x.x + g.y * x.y + g.z * x.z);
+      }
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+      if (ok) {
+        a = src[2 * ((size_t)t * nI + m)];
+        b = src[2 * ((size_t)t * nI + m) + 1];
+      }
+      wt[j][0] = ph.x * a.x - ph.y * a.y;
+      wt[j][1] = ph.x * a.y + ph.y * a.x;
+      wt[j][2] = ph.x * a.z - ph.y * a.w;
+      wt[j][3] = ph.x * a.w + ph.y * a.z;
+      wt[j][4] = ph.x * b.x - ph.y * b.y;
+      wt[j][5] = ph.x * b.y + ph.y * b.x;
+      wt[j][6] = ph.x * b.z - ph.y * b.w;
+      wt[j][7] = ph.x * b.w + ph.y * b.z;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) at[j][q] = 0.f;
+    }
+    const float r0 = g.w, r0sq = g.w * g.w, nkr0 = -kappa * g.w, r0k = g.w * kinv;
+    float ac[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ac[q] = 0.f;
+#pragma unroll 1
+    for (int k = 0; k < nI; ++k) {
+      int cix = lane + k;
+      if (cix >= nI) cix -= nI;
+      if (act) {
+        const float4 c4 = sC[cix], w0 = sW[2 * cix], w1 = sW[2 * cix + 1];
+        const float ws[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+          if (lane + j * T < nI) {
+            const float v = fmaf(U[j][0], c4.x, fmaf(U[j][1], c4.y, fmaf(U[j][2], c4.z, U[j][3] + c4.w)));
+            float rinv, phs;
+            if (MODE == 0) {
+              rinv = rsqrt_ftz(v);
+              phs = fmaf(kappa, v * rinv, nkr0);
+            } else {
+              const float r2 = v + r0sq;
+              rinv = rsqrt_ftz(r2);
+              phs = v * rcp_ftz(fmaf(r2 * rinv, kinv, r0k));
+              if (MODE == 2) {
+                const float qn = -rintf(phs * inv2pi);
+                phs = fmaf(qn, c1, phs);
+                phs = fmaf(qn, c2, phs);
+              }
+            }
+            const float gr = cos_ftz(phs) * rinv, gi = sin_ftz(phs) * rinv;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+              at[j][2 * f] = fmaf(gr, ws[2 * f], fmaf(-gi, ws[2 * f + 1], at[j][2 * f]));
+              at[j][2 * f + 1] = fmaf(gr, ws[2 * f + 1], fmaf(gi, ws[2 * f], at[j][2 * f + 1]));
+              ac[2 * f] = fmaf(gr, wt[j][2 * f], fmaf(-gi, wt[j][2 * f + 1], ac[2 * f]));
+              ac[2 * f + 1] = fmaf(gr, wt[j][2 * f + 1], fmaf(gi, wt[j][2 * f], ac[2 * f + 1]));
+            }
+          }
+        }
+      }
+      if (lane == 0) {
+        sO[2 * k] = make_float4(ac[0], ac[1], ac[2], ac[3]);
+        sO[2 * k + 1] = make_float4(ac[4], ac[5], ac[6], ac[7]);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) ac[q] = __shfl_down_sync(0xffffffffu, ac[q], 1);
+    }
+    __syncwarp();
+    // columns 0 .. T-2 started mid-way: lane l now holds the rest of column l
+    if (lane + 1 < T && lane < nI) {
+      float4 o0 = sO[2 * lane], o1 = sO[2 * lane + 1];
+      sO[2 * lane] = make_float4(o0.x + ac[0], o0.y + ac[1], o0.z + ac[2], o0.w + ac[3]);
+      sO[2 * lane + 1] = make_float4(o1.x + ac[4], o1.y + ac[5], o1.z + ac[6], o1.w + ac[7]);
+    }
+    __syncwarp();
+    for (int i = lane; i < 2 * nI; i += 32) back[(size_t)u * 2 * nI + i] = sO[i];
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        float *hp = sA + (j * 16 + q) * 32 + lane, *lp = hp + 8 * 32;
+        float vh = *hp, vl = *lp;
+        two_sum_acc(vh, vl, at[j][q]);
+        *hp = vh;
+        *lp = vl;
+      }
+  }
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    const int m = lane + j * T;
+    if (act && m < nI) {
+      float o[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) o[q] = sA[(j * 16 + q) * 32 + lane] + sA[(j * 16 + 8 + q) * 32 + lane];
+      acc[2 * ((size_t)t * nI + m)] = make_float4(o[0], o[1], o[2], o[3]);
+      acc[2 * ((size_t)t * nI + m) + 1] = make_float4(o[4], o[5], o[6], o[7]);
+    }
+  }
+}
+
+// acc_c (node m) = [owner's row sums] + sum over the pairs where c is the other cluster of their
+// column sums, added in list order with two-sum compensation.
+__global__ void k_m2l_sym_reduce(int nred, const int *__restrict__ red, const int *__restrict__ optr,
+                                 const int *__restrict__ pptr, const int *__restrict__ pslot, int nI,
+                                 const float4 *__restrict__ back, float4 *__restrict__ acc) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)nred * nI) return;
+  const int c = red[i / nI], m = (int)(i % nI);
+  float h[8], l[8];
+  float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+  if (optr[c + 1] > optr[c]) {
+    a = acc[2 * ((size_t)c * nI + m)];
+    b = acc[2 * ((size_t)c * nI + m) + 1];
+  }
+  h[0] = a.x; h[1] = a.y; h[2] = a.z; h[3] = a.w; h[4] = b.x; h[5] = b.y; h[6] = b.z; h[7] = b.w;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) l[q] = 0.f;
+  for (int j = pptr[c]; j < pptr[c + 1]; ++j) {
+    const size_t o = ((size_t)pslot[j] * nI + m) * 2;
+    const float4 x = back[o], y = back[o + 1];
+    const float v[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) two_sum_acc(h[q], l[q], v[q]);
+  }
+  acc[2 * ((size_t)c * nI + m)] = make_float4(h[0] + l[0], h[1] + l[1], h[2] + l[2], h[3] + l[3]);
+  acc[2 * ((size_t)c * nI + m) + 1] = make_float4(h[4] + l[4], h[5] + l[5], h[6] + l[6], h[7] + l[7]);
+}
+
 __global__ void k_unfold_f32n(long long tot, int nI, float ik2, const double *__restrict__ nodeD,
                               const float4 *__restrict__ acc, float2 *__restrict__ loc) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -817,8 +1011,54 @@ static size_t m2l_f32_smem(int nI) {
   return sizeof(float4) * ((size_t)nI + 8 * (size_t)((nI + 1) / 2) + 4 * 32 * (size_t)((nI + 31) / 32)) * kM2LWarps;
 }
 
+static size_t m2l_sym_smem(int nI) {
+  return sizeof(float4) * (6 * (size_t)nI + 4 * 32 * (size_t)((nI + 31) / 32)) * kM2LWarps;
+}
+
+template <int MODE>
+static efie_status launch_m2l_sym_t(Ctx *c, cudaStream_t st) {
+  const int nI = c->nI, NT = (nI + 31) / 32;
+  const unsigned blocks = (unsigned)((c->n_own_targets + kM2LWarps - 1) / kM2LWarps);
+  const size_t sm = m2l_sym_smem(nI);
+  const float kf = (float)c->kappa;
+  if (c->n_own_targets > 0) {
+    switch (NT) {
+#define EFIE_SYM_CASE(N)                                                                                     \
+  case N:                                                                                                   \
+    k_m2l_sym<N, MODE><<<blocks, 32 * kM2LWarps, sm, st>>>(c->d_own_targets, c->n_own_targets, c->d_own_ptr,   \
+                                                          c->d_own_src, c->d_own_slot, c->d_own_pgeo,          \
+                                                          c->d_own_pph, nI, kf, c->d_nodeX4, c->d_srcf,        \
+                                                          c->d_accf, c->d_back);                               \
+    ++c->launches;                                                                                          \
+    break;
+      EFIE_SYM_CASE(1)
+      EFIE_SYM_CASE(2)
+      EFIE_SYM_CASE(3)
+      EFIE_SYM_CASE(4)
+      EFIE_SYM_CASE(5)
+      EFIE_SYM_CASE(6)
+      EFIE_SYM_CASE(7)
+      EFIE_SYM_CASE(8)
+      EFIE_SYM_CASE(9)
+      EFIE_SYM_CASE(10)
+#undef EFIE_SYM_CASE
+      default:
+        c->err = "q too large for the FP32 M2L kernel";
+        return EFIE_EINVAL;
+    }
+  }
+  const long long tot = (long long)c->n_red * nI;
+  if (tot > 0) {
+    k_m2l_sym_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(c->n_red, c->d_red, c->d_own_ptr, c->d_par_ptr,
+                                                                    c->d_par_slot, nI, c->d_back, c->d_accf);
+    ++c->launches;
+  }
+  return EFIE_OK;
+}
+
 template <int MODE>
 static efie_status launch_m2l_f32_t(Ctx *c, cudaStream_t st) {
+  if (c->d_back) return launch_m2l_sym_t<MODE>(c, st);
   const int nI = c->nI, NT = (nI + 31) / 32;
   const unsigned blocks = (unsigned)((c->n_m2l_targets + kM2LWarps - 1) / kM2LWarps);
   const size_t sm = m2l_f32_smem(nI);
@@ -937,6 +1177,16 @@ static efie_status m2l_store_matrices(Ctx *c) {
 }
 
 template <int MODE>
+static efie_status m2l_sym_attrs(int bytes) {
+  cudaError_t e = cudaSuccess;
+  for (auto f : {k_m2l_sym<1, MODE>, k_m2l_sym<2, MODE>, k_m2l_sym<3, MODE>, k_m2l_sym<4, MODE>,
+                 k_m2l_sym<5, MODE>, k_m2l_sym<6, MODE>, k_m2l_sym<7, MODE>, k_m2l_sym<8, MODE>,
+                 k_m2l_sym<9, MODE>, k_m2l_sym<10, MODE>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e == cudaSuccess ? EFIE_OK : EFIE_ECUDA;
+}
+
+template <int MODE>
 static efie_status m2l_f32_attrs(int bytes) {
   cudaError_t e = cudaSuccess;
   for (auto f : {k_m2l_f32w<1, MODE>, k_m2l_f32w<2, MODE>, k_m2l_f32w<3, MODE>, k_m2l_f32w<4, MODE>,
@@ -969,6 +1219,27 @@ static efie_status m2l_f32_tables(Ctx *c) {
   EFIE_TRY(m2l_f32_attrs<0>((int)m2l_f32_smem(kMaxQ1 * kMaxQ1)));
   EFIE_TRY(m2l_f32_attrs<1>((int)m2l_f32_smem(kMaxQ1 * kMaxQ1)));
   EFIE_TRY(m2l_f32_attrs<2>((int)m2l_f32_smem(kMaxQ1 * kMaxQ1)));
+  // unordered-pair form: the column sums of every pair take npairs x nI x 32 bytes; used when
+  // they fit in a quarter of the free memory, else the one-sided kernel evaluates every tile twice
+  dfree(c, c->d_back);
+  if (c->npairs > 0) {
+    size_t freeb = 0, totb = 0;
+    EFIE_CUDA(cudaMemGetInfo(&freeb, &totb));
+    const size_t bytes = (size_t)c->npairs * c->nI * 2 * sizeof(float4);
+    if (bytes <= freeb / 4) {
+      EFIE_TRY(dalloc(c, &c->d_own_pgeo, (size_t)c->npairs));
+      EFIE_TRY(dalloc(c, &c->d_own_pph, (size_t)c->npairs));
+      EFIE_TRY(dalloc(c, &c->d_back, (size_t)c->npairs * c->nI * 2));
+      k_pair_table<<<(c->n_own_targets + 127) / 128, 128, 0, c->stream>>>(c->n_own_targets, c->d_own_targets,
+                                                                          c->d_own_ptr, c->d_own_src, c->d_center,
+                                                                          c->kappa, c->d_own_pgeo, c->d_own_pph);
+      ++c->launches;
+      EFIE_CUDA(cudaGetLastError());
+      EFIE_TRY(m2l_sym_attrs<0>((int)m2l_sym_smem(kMaxQ1 * kMaxQ1)));
+      EFIE_TRY(m2l_sym_attrs<1>((int)m2l_sym_smem(kMaxQ1 * kMaxQ1)));
+      EFIE_TRY(m2l_sym_attrs<2>((int)m2l_sym_smem(kMaxQ1 * kMaxQ1)));
+    }
+  }
   EFIE_CUDA(cudaStreamSynchronize(c->stream));
   return EFIE_OK;
 }

@@ -4,6 +4,7 @@
 // near-field element pairs for the singular quadrature.  No floating-point work of the
 // operator itself happens here; geometry values come from the device evaluator.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <unordered_map>
@@ -411,6 +412,69 @@ efie_status host_build_trees(Ctx *c) {
   if (c->nfar) EFIE_CUDA(cudaMemcpyAsync(c->d_far_src, fsrc.data(), fsrc.size() * 4, cudaMemcpyHostToDevice, c->stream));
   if (!targets.empty())
     EFIE_CUDA(cudaMemcpyAsync(c->d_m2l_targets, targets.data(), targets.size() * 4, cudaMemcpyHostToDevice, c->stream));
+
+  // unordered far pairs (the list is symmetric: (t, s) and (s, t) are both admissible): owner
+  // chosen to balance the owned counts, visiting pairs by decreasing level then ids
+  {
+    std::vector<std::array<int, 3>> up;  // (level, t, s) with t < s
+    for (int f = 0; f < c->nfar; ++f)
+      if (c->far[3 * f + 1] < c->far[3 * f + 2]) up.push_back({c->far[3 * f], c->far[3 * f + 1], c->far[3 * f + 2]});
+    std::sort(up.begin(), up.end(), [](const std::array<int, 3> &a, const std::array<int, 3> &b) {
+      if (a[0] != b[0]) return a[0] > b[0];
+      if (a[1] != b[1]) return a[1] < b[1];
+      return a[2] < b[2];
+    });
+    c->npairs = (int)up.size();
+    std::vector<int> owned(c->ncl, 0), owner(up.size());
+    for (size_t u = 0; u < up.size(); ++u) {
+      const int a = up[u][1], b = up[u][2];
+      owner[u] = owned[a] <= owned[b] ? a : b;
+      ++owned[owner[u]];
+    }
+    std::vector<int> optr(c->ncl + 1, 0), osrc(up.size()), oslot(up.size());
+    std::vector<int> pptr(c->ncl + 1, 0), pslot(up.size());
+    for (size_t u = 0; u < up.size(); ++u) {
+      optr[owner[u] + 1]++;
+      pptr[(owner[u] == up[u][1] ? up[u][2] : up[u][1]) + 1]++;
+    }
+    for (int k = 0; k < c->ncl; ++k) {
+      optr[k + 1] += optr[k];
+      pptr[k + 1] += pptr[k];
+    }
+    std::vector<int> of(optr.begin(), optr.end() - 1), pf(pptr.begin(), pptr.end() - 1);
+    for (size_t u = 0; u < up.size(); ++u) {
+      const int o = owner[u], other = o == up[u][1] ? up[u][2] : up[u][1];
+      osrc[of[o]] = other;
+      oslot[of[o]++] = (int)u;
+      pslot[pf[other]++] = (int)u;
+    }
+    std::vector<int> otg, red;
+    for (int k = 0; k < c->ncl; ++k) {
+      if (optr[k + 1] > optr[k]) otg.push_back(k);
+      if (optr[k + 1] > optr[k] || pptr[k + 1] > pptr[k]) red.push_back(k);
+    }
+    std::stable_sort(otg.begin(), otg.end(),
+                     [&](int a, int b) { return optr[a + 1] - optr[a] > optr[b + 1] - optr[b]; });
+    c->n_own_targets = (int)otg.size();
+    c->n_red = (int)red.size();
+    EFIE_TRY(dalloc(c, &c->d_own_ptr, optr.size()));
+    EFIE_TRY(dalloc(c, &c->d_own_src, std::max<size_t>(osrc.size(), 1)));
+    EFIE_TRY(dalloc(c, &c->d_own_slot, std::max<size_t>(oslot.size(), 1)));
+    EFIE_TRY(dalloc(c, &c->d_own_targets, std::max<size_t>(otg.size(), 1)));
+    EFIE_TRY(dalloc(c, &c->d_par_ptr, pptr.size()));
+    EFIE_TRY(dalloc(c, &c->d_par_slot, std::max<size_t>(pslot.size(), 1)));
+    EFIE_TRY(dalloc(c, &c->d_red, std::max<size_t>(red.size(), 1)));
+    EFIE_CUDA(cudaMemcpyAsync(c->d_own_ptr, optr.data(), optr.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    EFIE_CUDA(cudaMemcpyAsync(c->d_par_ptr, pptr.data(), pptr.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    if (!up.empty()) {
+      EFIE_CUDA(cudaMemcpyAsync(c->d_own_src, osrc.data(), osrc.size() * 4, cudaMemcpyHostToDevice, c->stream));
+      EFIE_CUDA(cudaMemcpyAsync(c->d_own_slot, oslot.data(), oslot.size() * 4, cudaMemcpyHostToDevice, c->stream));
+      EFIE_CUDA(cudaMemcpyAsync(c->d_own_targets, otg.data(), otg.size() * 4, cudaMemcpyHostToDevice, c->stream));
+      EFIE_CUDA(cudaMemcpyAsync(c->d_par_slot, pslot.data(), pslot.size() * 4, cudaMemcpyHostToDevice, c->stream));
+      EFIE_CUDA(cudaMemcpyAsync(c->d_red, red.data(), red.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    }
+    EFIE_CUDA(cudaStreamSynchronize(c->stream));
+  }
 
   // near pairs as CSR over target elements; near_perm maps CSR slots to list entries
   std::vector<int> nptr(c->nE + 1, 0), nsrc(c->nnear);
