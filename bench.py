@@ -483,9 +483,10 @@ def run_gpu(args):
     s64.close()
     s_e2e.close()
 
-    variant = None
+    variant = pairs = None
     if not args.no_variant:
         variant = variant_leg(args, stream, geo, kw, prec, d_inc, p_inc, dirs, e_mixed)
+        pairs = m2l_pairs_leg(stream, geo, kw, prec, mv["m2l"])
     extra = {}
     if rank == 0 and world == 1 and not args.no_extras:
         extra["multi"] = multi_leg(args, steps=args.multi_steps, pk_alu=pk_alu)
@@ -516,6 +517,7 @@ def run_gpu(args):
             "matvec_rel_err_vs_fp64": err_vs_fp64,
             "fp64_solve": fp64,
             "variant_dense_leaf": variant,
+            "variant_m2l_unordered_pairs": pairs,
             "roofline": roof, "roofline_near": near_roof, "roofline_setup": roof_setup,
             "peaks_measured": pk_alu, "peaks_hbm_bf16": {k: pk.get(k) for k in ("hbm_gbs", "bf16_tflops",
                                                                                "bf16_tflops_sustained")},
@@ -578,6 +580,28 @@ def variant_leg(args, stream, geo, kw, prec, d_inc, p_inc, dirs, e_ref):
            "note": "timed on the host clock around synchronous calls, 3 steps after 2 warm-up steps"}
     s.close()
     return out
+
+
+def m2l_pairs_leg(stream, geo, kw, prec, m2l_ms_ordered):
+    """The M2L over unordered admissible pairs (option m2l_pairs: each coupling tile evaluated
+    once and applied in both directions) on the same workload: product phases and the M2L
+    time against the default form's."""
+    import torch
+    from paper_1807_03097_gb300 import Solver
+
+    s = Solver(geo, stream=stream.cuda_stream, precision=prec, m2l_pairs=1, **kw)
+    N = s.ndof
+    x = torch.from_numpy(np.random.default_rng(0).standard_normal(N) + 0j).cuda()
+    y = torch.empty_like(x)
+    ph = []
+    for i in range(13):
+        s.matvec(x, out=y)
+        if i >= 3:
+            ph.append(s.last_timings())
+    mv = {k: statistics.median([p[k] for p in ph]) for k in ph[0]}
+    s.close()
+    return {"matvec_per_s": 1000.0 / mv["total"], "matvec_ms_phases": mv, "m2l_ms_ordered_pairs": m2l_ms_ordered,
+            "note": "M2L phase = pair kernel + per-cluster sum of the transposed contributions"}
 
 
 # ---------------------------------------------------------------------------- many right-hand sides

@@ -93,6 +93,12 @@ typedef struct {
                         (tensor Gauss, quad_regular points) like a separated near pair instead of
                         being compressed, when (p+1)^2 < (q+1)^2.  A departure from the paper's
                         FMM (more accurate, more near-field storage, fewer M2L blocks). */
+  int m2l_pairs;     /* M2L of one right-hand side in the mixed form: 0 every ordered admissible
+                        pair (t, s) evaluates its coupling tile; 1 every unordered pair {t, s}
+                        evaluates it once and applies it in both directions (K_st = K_ts^T),
+                        with npairs x (q+1)^2 x 32 bytes of column sums (used when they fit in a
+                        quarter of the free memory).  A variant of the M2L's cost, same results
+                        within the mixed tolerance. */
 } efie_options;
 
 typedef struct {

@@ -62,6 +62,7 @@ efie_status check_options(const efie_options *o) {
   if (o->m2l_batch < 0 || o->m2l_batch > 2) return EFIE_EINVAL;
   if (o->m2l_batch == 2 && (o->q + 1) * (o->q + 1) > 128) return EFIE_EINVAL;
   if (o->leaf_dense < 0 || o->leaf_dense > 1) return EFIE_EINVAL;
+  if (o->m2l_pairs < 0 || o->m2l_pairs > 1) return EFIE_EINVAL;
   return EFIE_OK;
 }
 

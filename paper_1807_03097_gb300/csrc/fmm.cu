@@ -1219,10 +1219,10 @@ static efie_status m2l_f32_tables(Ctx *c) {
   EFIE_TRY(m2l_f32_attrs<0>((int)m2l_f32_smem(kMaxQ1 * kMaxQ1)));
   EFIE_TRY(m2l_f32_attrs<1>((int)m2l_f32_smem(kMaxQ1 * kMaxQ1)));
   EFIE_TRY(m2l_f32_attrs<2>((int)m2l_f32_smem(kMaxQ1 * kMaxQ1)));
-  // unordered-pair form: the column sums of every pair take npairs x nI x 32 bytes; used when
-  // they fit in a quarter of the free memory, else the one-sided kernel evaluates every tile twice
+  // unordered-pair form (option m2l_pairs): the column sums of every pair take npairs x nI x 32
+  // bytes; used when they fit in a quarter of the free memory, else the one-sided kernel runs
   dfree(c, c->d_back);
-  if (c->npairs > 0) {
+  if (c->opt.m2l_pairs == 1 && c->npairs > 0) {
     size_t freeb = 0, totb = 0;
     EFIE_CUDA(cudaMemGetInfo(&freeb, &totb));
     const size_t bytes = (size_t)c->npairs * c->nI * 2 * sizeof(float4);

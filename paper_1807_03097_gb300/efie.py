@@ -40,7 +40,7 @@ class EfieOptions(ctypes.Structure):
                 ("eta", ctypes.c_double), ("precision", ctypes.c_int), ("quad_regular", ctypes.c_int),
                 ("quad_singular", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("gmres_tol", ctypes.c_double),
                 ("gmres_maxit", ctypes.c_int), ("tol_is_relative", ctypes.c_int), ("m2l_store", ctypes.c_int),
-                ("m2l_batch", ctypes.c_int), ("leaf_dense", ctypes.c_int)]
+                ("m2l_batch", ctypes.c_int), ("leaf_dense", ctypes.c_int), ("m2l_pairs", ctypes.c_int)]
 
 
 class EfieSolveInfo(ctypes.Structure):

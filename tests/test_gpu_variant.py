@@ -51,3 +51,41 @@ def test_leaf_dense_variant_vs_oracle(name):
         assert relmax(s.matvec(x), yd) < TOL64
     s.close()
     s32.close()
+
+
+@pytest.mark.parametrize("name", ["sphere_p2_m2_q5", "torus_p1_m2_q4"])
+def test_unordered_pair_m2l_vs_oracle(name):
+    """Option m2l_pairs = 1: each admissible pair's coupling tile evaluated once and applied in
+    both directions (K_st = K_ts^T); the mixed product against the oracle (1e-5) and against the
+    default form, including the full-size sphere workload's sampled rows."""
+    from paper_1807_03097_gb300 import Solver
+
+    mk, p, m, k, q, eta = CASES[name]
+    geo = mk()
+    s = Solver(geo, p=p, level_m=m, kappa=k, q=q, eta=eta, precision=1, m2l_pairs=1)
+    s0 = Solver(geo, p=p, level_m=m, kappa=k, q=q, eta=eta, precision=1)
+    r = O.Problem(geo, p=p, m=m, kappa=k, q=q, eta=eta)
+    rng = np.random.default_rng(81)
+    x = rng.standard_normal(s.ndof) + 1j * rng.standard_normal(s.ndof)
+    yr = r.fmm_matvec(x)[0]
+    y = s.matvec(x)
+    assert np.linalg.norm(y - yr) / np.linalg.norm(yr) < TOL32
+    assert np.linalg.norm(y - s0.matvec(x)) / np.linalg.norm(yr) < TOL32
+    s.close()
+    s0.close()
+
+
+def test_unordered_pair_m2l_full_size_rows():
+    from paper_1807_03097_gb300 import Solver
+
+    geo = G.sphere()
+    kw = dict(p=2, level_m=5, kappa=10.0, q=8, eta=1.6)
+    s = Solver(geo, precision=1, m2l_pairs=1, **kw)
+    r = O.Problem(geo, p=2, m=5, kappa=10.0, q=8, eta=1.6)
+    rng = np.random.default_rng(82)
+    xs = rng.standard_normal(s.nsup) + 1j * rng.standard_normal(s.nsup)
+    y = s.matvec_superspace(xs).reshape(-1, 18)
+    elems = np.array([0, 777, 3 * 1024 + 517, 6143])
+    rows = r.fmm_rows(xs, elems)
+    assert np.abs(y[elems] - rows).max() / np.abs(rows).max() < TOL32
+    s.close()
