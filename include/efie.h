@@ -198,6 +198,11 @@ efie_status efie_block_counts(const efie_ctx *ctx, int64_t *nfar, int64_t *nnear
 efie_status efie_export_blocks(const efie_ctx *ctx, int *far, int *near);
 efie_status efie_export_near_blocks(efie_ctx *ctx, double *blocks);
 efie_status efie_matvec_superspace(efie_ctx *ctx, const double *xs, double *ys, int ptr_kind);
+/* ys = N xs: the near-field part of the product alone (the element blocks of eq. Vkh of the
+ * non-admissible leaf pairs, Sec. 4.1; FP32 blocks in the mixed form), on one superspace vector
+ * (ptr_kind memory).  Its device time is reported by efie_last_timings (total and near field).
+ * Errors: EFIE_ESTATE, EFIE_EINVAL, EFIE_ECUDA. */
+efie_status efie_near_apply(efie_ctx *ctx, const double *xs, double *ys, int ptr_kind);
 /* ys[r] = (N + F) xs[r] for nrhs superspace vectors, [nrhs][nE][2][p+1][p+1] complex in
  * ptr_kind memory: the product of several right-hand sides (eq. FMMlr) without the T gather
  * and scatter, in one batched pass per 64 vectors in the mixed form (the M2L chosen by

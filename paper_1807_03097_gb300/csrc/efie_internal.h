@@ -127,6 +127,7 @@ struct Ctx {
   int *d_near_ptr = nullptr, *d_near_src = nullptr;  // CSR by target element
   double2 *d_nblk = nullptr;  // [nnear][nb (col)][nb (row)]
   float2 *d_nblkf = nullptr;  // FP32 copy of the blocks (mixed-precision apply)
+  float2 *d_xsf = nullptr;    // x* in FP32 for the FP32 block product [nsup]
   std::vector<int> near_perm;  // CSR position -> index in nearl
 
   // tables on the device

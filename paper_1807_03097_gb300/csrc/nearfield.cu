@@ -7,8 +7,16 @@
 #include <cmath>
 
 #include "geom.cuh"
+#include "tc.cuh"
 
 namespace efie {
+
+// s + e = a + b exactly (Knuth's two-sum): running FP32 sums with a compensation term
+__device__ __forceinline__ void two_sum(float &hi, float &lo, float b) {
+  const float s = hi + b, bp = s - hi;
+  lo += (hi - (s - bp)) + (b - bp);
+  hi = s;
+}
 
 constexpr int kQC = 64;          // quadrature points staged per chunk
 constexpr int kQuadThreads = 2 * kQC;  // one thread per (point, side) in the geometry phase
@@ -684,6 +692,90 @@ __global__ void __launch_bounds__(32 * kApplyWarps) k_near_apply(int nE, const i
   }
 }
 
+// x* in FP32 for the FP32 block product (converted once per product, not once per lane)
+__global__ void k_vec_to_f32(int n, const double2 *__restrict__ x, float2 *__restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = make_float2((float)x[i].x, (float)x[i].y);
+}
+
+// FP32 blocks, one right-hand side, streamed with 16-byte loads: one block of 4 warps per target
+// element, warp w taking the source blocks w, w + 4, ... kBIF at a time (their loads in flight
+// together).  A block column of NB rows is read by LPC = NB / 2 lanes, each loading two
+// consecutive rows (one float4), so a warp instruction reads CPR = 32 / LPC consecutive columns
+// (contiguous in the column-major block) and a block takes NB / CPR rounds.  Lane l keeps the
+// rows 2 (l % LPC), 2 (l % LPC) + 1 and the columns l / LPC + CPR k; its x* entries (FP32 copy)
+// come through the cache.  Per source block the partial sums enter running sums with two-sum
+// compensation; the lanes and warps that hold the same rows are combined in a fixed order at
+// the end.
+constexpr int kBIF = 2;
+
+template <int NB>
+__device__ __forceinline__ void near_v4_block(const float4 *__restrict__ B, const float2 *__restrict__ x, int rp,
+                                              int cg, bool act, float4 *b, float2 *xv) {
+  constexpr int LPC = NB / 2, CPR = 32 / LPC, ROUNDS = (NB + CPR - 1) / CPR;
+#pragma unroll
+  for (int t = 0; t < ROUNDS; ++t) {
+    const int col = cg + CPR * t;
+    const bool ok = act && col < NB;
+    b[t] = ok ? __ldcs(B + col * LPC + rp) : make_float4(0.f, 0.f, 0.f, 0.f);
+    xv[t] = ok ? x[col] : make_float2(0.f, 0.f);
+  }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(128) k_near_apply_v4(int nE, const int *__restrict__ ptr,
+                                                       const int *__restrict__ src,
+                                                       const float4 *__restrict__ blocks,
+                                                       const float2 *__restrict__ xs,
+                                                       double2 *__restrict__ ysn) {
+  constexpr int LPC = NB / 2, CPR = 32 / LPC, ROUNDS = (NB + CPR - 1) / CPR;
+  constexpr int F4 = NB * NB / 2;  // float4 per block
+  const int e = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (e >= nE) return;
+  const int rp = lane % LPC, cg = lane / LPC;
+  const bool act = cg < CPR;
+  float h[4] = {0.f, 0.f, 0.f, 0.f}, cmp[4] = {0.f, 0.f, 0.f, 0.f};
+  const int k0 = ptr[e], k1 = ptr[e + 1];
+  for (int k = k0 + warp; k < k1; k += 4 * kBIF) {
+    float4 b[kBIF][ROUNDS];
+    float2 xv[kBIF][ROUNDS];
+#pragma unroll
+    for (int i = 0; i < kBIF; ++i) {
+      const int ki = k + 4 * i;
+      const bool have = ki < k1;
+      const int kk = have ? ki : k;
+      near_v4_block<NB>(blocks + (size_t)kk * F4, xs + (size_t)src[kk] * NB, rp, cg, act && have, b[i], xv[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < kBIF; ++i) {
+      float p[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int t = 0; t < ROUNDS; ++t) {
+        p[0] = fmaf(b[i][t].x, xv[i][t].x, fmaf(-b[i][t].y, xv[i][t].y, p[0]));
+        p[1] = fmaf(b[i][t].x, xv[i][t].y, fmaf(b[i][t].y, xv[i][t].x, p[1]));
+        p[2] = fmaf(b[i][t].z, xv[i][t].x, fmaf(-b[i][t].w, xv[i][t].y, p[2]));
+        p[3] = fmaf(b[i][t].z, xv[i][t].y, fmaf(b[i][t].w, xv[i][t].x, p[3]));
+      }
+      if (k + 4 * i < k1)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) two_sum(h[q], cmp[q], p[q]);
+    }
+  }
+  __shared__ float red[4][32][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) red[warp][lane][q] = h[q] + cmp[q];
+  __syncthreads();
+  if (warp == 0 && lane < LPC) {
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int w = 0; w < 4; ++w)
+      for (int g = 0; g < CPR; ++g)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s[q] += (double)red[w][g * LPC + lane][q];
+    ysn[(size_t)e * NB + 2 * lane] = make_double2(s[0], s[1]);
+    ysn[(size_t)e * NB + 2 * lane + 1] = make_double2(s[2], s[3]);
+  }
+}
+
 // The same product for several right-hand sides (FP32 blocks, mixed form): each block is read
 // once for a group of up to RB right-hand sides (grid dimension y), which divides the HBM
 // traffic of the near field by RB.  Vectors of right-hand side r start at r * vstride.
@@ -837,6 +929,23 @@ efie_status dev_near_apply_batch(Ctx *c, int R, const double2 *xs, double2 *ysn,
 efie_status dev_near_apply(Ctx *c, const double2 *xs, double2 *ysn, cudaStream_t st) {
   const bool f32 = c->opt.precision == EFIE_MIXED_FP32 && c->d_nblkf;
   const int threads = 32 * kApplyWarps;
+  if (f32) {
+    const unsigned grid = (unsigned)c->nE;
+    const float4 *B = reinterpret_cast<const float4 *>(c->d_nblkf);
+    bool done = c->nb == 8 || c->nb == 18 || c->nb == 32;
+    if (done) {
+      if (!c->d_xsf) EFIE_TRY(dalloc(c, &c->d_xsf, (size_t)c->nsup));
+      k_vec_to_f32<<<(c->nsup + 255) / 256, 256, 0, st>>>(c->nsup, xs, c->d_xsf);
+      ++c->launches;
+      const float2 *xf = c->d_xsf;
+      if (c->nb == 8) k_near_apply_v4<8><<<grid, 128, 0, st>>>(c->nE, c->d_near_ptr, c->d_near_src, B, xf, ysn);
+      else if (c->nb == 18) k_near_apply_v4<18><<<grid, 128, 0, st>>>(c->nE, c->d_near_ptr, c->d_near_src, B, xf, ysn);
+      else k_near_apply_v4<32><<<grid, 128, 0, st>>>(c->nE, c->d_near_ptr, c->d_near_src, B, xf, ysn);
+      ++c->launches;
+      EFIE_CUDA(cudaGetLastError());
+      return EFIE_OK;
+    }
+  }
   switch (c->nb) {
 #define EFIE_APPLY_CASE(NBV)                                                                                   \
   case NBV:                                                                                                   \

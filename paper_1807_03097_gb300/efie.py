@@ -27,7 +27,7 @@ ABI_SYMBOLS = (
     "efie_default_options", "efie_create", "efie_set_geometry", "efie_setup", "efie_num_dofs",
     "efie_matvec", "efie_rhs_plane_waves", "efie_solve", "efie_solve_plane_waves", "efie_far_field",
     "efie_block_counts", "efie_export_blocks", "efie_export_near_blocks", "efie_matvec_superspace",
-    "efie_matvec_superspace_batch", "efie_device_bytes", "efie_setup_timings",
+    "efie_matvec_superspace_batch", "efie_device_bytes", "efie_setup_timings", "efie_near_apply",
     "efie_last_timings", "efie_launch_count", "efie_destroy", "efie_status_string", "efie_last_error", "efie_check_device_waits", "efie_exterior_field",
     "efie_rhs_dipole",
     "efie_far_field_noalloc",
@@ -102,6 +102,7 @@ def load(path: str = LIB_PATH):
         "efie_matvec_superspace_batch": (c_int, [P, c_int, P, P, c_int]),
         "efie_device_bytes": (c_int, [P, I64, I64]),
         "efie_setup_timings": (c_int, [P, D, c_int]),
+        "efie_near_apply": (c_int, [P, P, P, c_int]),
         "efie_last_timings": (c_int, [P, D, c_int]),
         "efie_launch_count": (ctypes.c_int64, [P]),
         "efie_far_field_noalloc": (c_int, [P, P, c_int, P, P]),
@@ -229,6 +230,15 @@ class Solver:
                         "efie_matvec_superspace_batch")
         else:
             self._check(self._L.efie_matvec_superspace(self.h, px, py, kx), "efie_matvec_superspace")
+        return out
+
+    def near_apply(self, xs, out=None):
+        """ys = N xs (the near-field blocks alone) on one superspace vector."""
+        if out is None:
+            out = np.empty_like(xs) if isinstance(xs, np.ndarray) else xs.new_empty(xs.shape)
+        px, kx = _ptr(xs)
+        py, _ = _ptr(out)
+        self._check(self._L.efie_near_apply(self.h, px, py, kx), "efie_near_apply")
         return out
 
     def device_bytes(self):

@@ -118,3 +118,42 @@ def test_mixed_precision_matvec(store):
         e = np.linalg.norm(s.matvec(x) - r.fmm_matvec(x)[0]) / np.linalg.norm(r.fmm_matvec(x)[0])
         assert e < TOL32, e
         s.close()
+
+
+def near_product_oracle(r, xs):
+    """ys[a] = sum over the near pairs (a, b) of B_ab xs[b], from the oracle's element blocks."""
+    X = xs.reshape(r.nE, r.nb)
+    Y = np.zeros_like(X)
+    for (a, b), B in zip(r.near_pairs(), r.near_blocks()):
+        Y[a] += B @ X[b]
+    return Y.reshape(-1)
+
+
+def test_near_apply_fp64(pair):
+    name, s, r = pair
+    rng = np.random.default_rng(11)
+    xs = rng.standard_normal(s.nsup) + 1j * rng.standard_normal(s.nsup)
+    assert relmax(s.near_apply(xs), near_product_oracle(r, xs)) < TOL64
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_near_apply_mixed(p):
+    """FP32 blocks (one kernel per block size 2(p+1)^2 = 8, 18, 32, 50), FP32 copy of x*,
+    compensated FP32 sums; against the FP64 oracle blocks, and device pointers against host
+    pointers bit for bit."""
+    torch = pytest.importorskip("torch")
+    from paper_1807_03097_gb300 import Solver
+
+    geo = G.torus()
+    kw = dict(p=p, m=2 if p < 4 else 1, kappa=2.0, q=4, eta=1.6)
+    s = Solver(geo, p=p, level_m=kw["m"], kappa=2.0, q=4, eta=1.6, precision=1)
+    r = O.Problem(geo, **kw)
+    rng = np.random.default_rng(12 + p)
+    xs = rng.standard_normal(s.nsup) + 1j * rng.standard_normal(s.nsup)
+    yh = s.near_apply(xs)
+    assert relmax(yh, near_product_oracle(r, xs)) < TOL32
+    yd = s.near_apply(torch.from_numpy(xs).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(yd.cpu().numpy(), yh)
+    assert s.last_timings()["near"] > 0
+    s.close()
