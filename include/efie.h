@@ -97,8 +97,10 @@ typedef struct {
                         pair (t, s) evaluates its coupling tile; 1 every unordered pair {t, s}
                         evaluates it once and applies it in both directions (K_st = K_ts^T),
                         with npairs x (q+1)^2 x 32 bytes of column sums (used when they fit in a
-                        quarter of the free memory).  A variant of the M2L's cost, same results
-                        within the mixed tolerance. */
+                        quarter of the free memory); 2 autotuned: setup times both kernels on
+                        this problem's blocks (CUDA events, best of 3) and keeps the faster
+                        (efie_setup_timings reports both times and the choice).  A variant of
+                        the M2L's cost, same results within the mixed tolerance. */
 } efie_options;
 
 typedef struct {
@@ -220,7 +222,9 @@ int efie_last_timings(const efie_ctx *ctx, double *out, int n);
  * the context stream), [2] quadrature points it evaluated (Duffy parts x g^4 summed over its
  * pairs), [3] touching pairs it integrated, [4] device time of the separated pairs (tensor
  * Gauss from element tables, ms), [5] separated pairs integrated; pairs (e', e) with e' > e
- * are mirrored, B(e', e) = B(e, e')^T.  Returns the number of values written (<= n). */
+ * are mirrored, B(e', e) = B(e, e')^T; [6] M2L time of the ordered-pair kernel, [7] of the
+ * unordered-pair kernel (ms, when m2l_pairs = 2 timed them, else 0), [8] the M2L kept (0
+ * ordered pairs, 1 unordered pairs).  Returns the number of values written (<= n). */
 int efie_setup_timings(const efie_ctx *ctx, double *out, int n);
 
 /* Far field like efie_far_field, for callers that must not allocate device memory during
@@ -320,6 +324,39 @@ const char *efie_status_string(efie_status s);
  * reason for EFIE_EINVAL / EFIE_ETIMEOUT); "" if none.  Owned by ctx, valid until the next
  * call on ctx. */
 const char *efie_last_error(const efie_ctx *ctx);
+
+/* ---------------------------------------------------------------------------------------
+ * Groups of independent problems (restarted GMRES of Sec. 5 across problems).
+ *
+ * efie_setup_many runs efie_setup of nctx contexts on nthreads host threads (each context's
+ * device work on its own stream, so the setups overlap on the GPU); status[i] (optional,
+ * nctx entries) receives each context's status; the return value is the first error, else
+ * EFIE_OK.
+ *
+ * A group holds nctx contexts that are set up on one device (each with its own geometry,
+ * wavenumber, p, refinement and options).  efie_group_solve solves A_i x_i = b_i for every
+ * context i in lockstep: each step applies the products of all unfinished systems as one
+ * CUDA-graph launch (one branch per context, captured once and again only when a tenth of
+ * its branches belong to finished systems) and runs the Arnoldi (CGS2), Givens and update
+ * work of all systems in one launch per operation, with the arithmetic of efie_solve.  The
+ * GMRES options (tolerance, restart, maximum iterations) are each context's own.
+ *   b[i], x[i]: 2 ndof_i doubles each (ptr_kind memory); x[i] receives the solution.
+ *   iterations, residuals, converged: nctx entries each (optional).
+ * While a group solve runs, its contexts must not be used by other calls.  The contexts
+ * stay owned by the caller and must outlive the group.
+ * Returns EFIE_NOT_CONVERGED if any system did not converge; EFIE_ESTATE if a context is
+ * not set up; EFIE_EINVAL for null pointers, repeated or mixed-device contexts.
+ * efie_group_stats: [steps, product-graph captures, kernels launched (graph nodes counted),
+ * solve wall time ms, kernel nodes of the product graph, vector chunks] of the last solve;
+ * returns the number of values written. */
+typedef struct efie_group efie_group;
+efie_status efie_setup_many(efie_ctx *const *ctxs, int nctx, int nthreads, efie_status *status);
+efie_status efie_group_create(efie_group **g, efie_ctx *const *ctxs, int nctx);
+efie_status efie_group_solve(efie_group *g, const double *const *b, double *const *x, int ptr_kind,
+                             int *iterations, double *residuals, int *converged);
+int efie_group_stats(const efie_group *g, double *out, int n);
+const char *efie_group_last_error(const efie_group *g);
+efie_status efie_group_destroy(efie_group *g);
 
 #ifdef __cplusplus
 }

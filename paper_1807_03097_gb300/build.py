@@ -16,7 +16,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libefie.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["abi.cu", "geom.cu", "nearfield.cu", "fmm.cu", "m2l_tc.cu", "gmres.cu", "rhs_ff.cu", "exterior.cu", "noalloc.cu", "host_setup.cpp", "server.cpp", "devmem.cpp"]
+SOURCES = ["abi.cu", "geom.cu", "nearfield.cu", "fmm.cu", "m2l_tc.cu", "gmres.cu", "rhs_ff.cu", "exterior.cu", "noalloc.cu", "group.cu", "host_setup.cpp", "server.cpp", "devmem.cpp"]
 
 
 def nvcc() -> str:

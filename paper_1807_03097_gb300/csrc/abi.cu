@@ -63,7 +63,7 @@ efie_status check_options(const efie_options *o) {
   if (o->m2l_batch < 0 || o->m2l_batch > 2) return EFIE_EINVAL;
   if (o->m2l_batch == 2 && (o->q + 1) * (o->q + 1) > 128) return EFIE_EINVAL;
   if (o->leaf_dense < 0 || o->leaf_dense > 1) return EFIE_EINVAL;
-  if (o->m2l_pairs < 0 || o->m2l_pairs > 1) return EFIE_EINVAL;
+  if (o->m2l_pairs < 0 || o->m2l_pairs > 2) return EFIE_EINVAL;
   return EFIE_OK;
 }
 
@@ -768,9 +768,10 @@ efie_status efie_rhs_dipole(efie_ctx *ctx, int nrhs, const double *x0, const dou
 int efie_setup_timings(const efie_ctx *ctx, double *out, int n) {
   const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
   if (!c || !out) return 0;
-  const double v[6] = {c->setup_ms, (double)c->near_quad_ms, (double)c->near_quad_points, (double)c->near_quad_pairs,
-                       (double)c->near_sep_ms, (double)c->near_sep_pairs};
-  int k = n < 6 ? n : 6;
+  const double v[9] = {c->setup_ms, (double)c->near_quad_ms, (double)c->near_quad_points, (double)c->near_quad_pairs,
+                       (double)c->near_sep_ms, (double)c->near_sep_pairs, (double)c->m2l_tune_ms[0],
+                       (double)c->m2l_tune_ms[1], c->d_back ? 1.0 : 0.0};
+  int k = n < 9 ? n : 9;
   for (int i = 0; i < k; ++i) out[i] = v[i];
   return k;
 }

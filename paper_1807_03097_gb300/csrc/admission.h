@@ -28,12 +28,14 @@ inline size_t request_footprint(int np, int level_m, int p, int q, int gmres_res
   const size_t n = size_t(1) << level_m, nE = size_t(np) * n * n;
   const size_t p1 = p + 1, nb = 2 * p1 * p1, nI = size_t(q + 1) * (q + 1);
   const size_t ndof = 2 * size_t(np) * (n + p - 1) * (n + p - 1);
-  const size_t near = (leaf_dense ? 160 : 30) * nE * nb * nb * (mixed ? 24 : 16);
+  const size_t near = (leaf_dense ? 160 : 30) * nE * (nb * nb * (mixed ? 24 : 16) + 8);
   const size_t kr = (size_t)std::min(gmres_restart, gmres_maxit) + 1;
   const size_t lockstep = (mixed && nrhs > 1) ? (size_t)std::min(nrhs, 64) : 1;
   const size_t krylov = lockstep * (kr * ndof * 16 + kr * kr * 16);
   const size_t ncl = nE * 4 / 3 + np;
-  const size_t clusters = ncl * nI * (72 + 14 * 16);
+  // per cluster: node geometry and the FMM fields; per admissible pair (at most 130 per
+  // cluster): pair geometry and phase, CSR entries, the unordered-pair lists (48 bytes)
+  const size_t clusters = ncl * nI * (72 + 14 * 16) + 130 * ncl * 48;
   const size_t vecs = nE * nb * 16 * 6 + ndof * 16 * 8;
   const size_t batch = lockstep > 1 ? lockstep * (5 * nE * nb * 16 + 14 * ncl * nI * 8 + 4 * ndof * 16) : 0;
   const size_t farfield = ndir > 0 ? 48 * size_t(ndir) * nE + 48 * size_t(ndir) + 24 * size_t(ndir) : 0;

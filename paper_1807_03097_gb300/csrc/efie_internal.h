@@ -115,6 +115,7 @@ struct Ctx {
   float4 *d_own_pgeo = nullptr;  // per owned pair: c_owner - c_other, r0
   float2 *d_own_pph = nullptr;   // per owned pair: e^{i kappa r0} / (4 pi)
   float4 *d_back = nullptr;      // [npairs][nI][2]: K^T contributions to the non-owner
+  float m2l_tune_ms[2] = {0.f, 0.f};  // autotuned M2L (m2l_pairs = 2): ordered, unordered
   void *d_K = nullptr;        // stored coupling matrices [pair][m'][m] (double2 or float2)
   bool k_stored = false;
   // several right-hand sides (mixed form)
@@ -123,7 +124,7 @@ struct Ctx {
   int h_resB_cap = 0;
   double2 *d_xB = nullptr, *d_yB = nullptr, *d_xsB = nullptr, *d_ysB = nullptr, *d_ysnB = nullptr;
   float2 *d_momB = nullptr, *d_srcB = nullptr, *d_accB = nullptr, *d_locB = nullptr;
-  int *d_tc_err = nullptr;   // set by a tensor-core M2L whose pipeline wait ran out  // FP32 M2L reduces phases explicitly (unless all are within +-100 pi)
+  int *d_tc_err = nullptr;   // set by a tensor-core M2L whose pipeline wait ran out
   int *d_near_ptr = nullptr, *d_near_src = nullptr;  // CSR by target element
   double2 *d_nblk = nullptr;  // [nnear][nb (col)][nb (row)]
   float2 *d_nblkf = nullptr;  // FP32 copy of the blocks (mixed-precision apply)

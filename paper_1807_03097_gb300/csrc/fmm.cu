@@ -1196,6 +1196,50 @@ static efie_status m2l_f32_attrs(int bytes) {
   return e == cudaSuccess ? EFIE_OK : EFIE_ECUDA;
 }
 
+static efie_status launch_m2l_f32(Ctx *c, cudaStream_t st);
+
+// Best of 3 device times (CUDA events on the context stream) of the M2L as it is configured.
+static efie_status time_m2l(Ctx *c, float *best) {
+  EFIE_TRY(launch_m2l_f32(c, c->stream));  // warm-up
+  *best = 1e30f;
+  for (int r = 0; r < 3; ++r) {
+    EFIE_CUDA(cudaEventRecord(c->tm.ev[3], c->stream));
+    EFIE_TRY(launch_m2l_f32(c, c->stream));
+    EFIE_CUDA(cudaEventRecord(c->tm.ev[4], c->stream));
+    EFIE_CUDA(cudaEventSynchronize(c->tm.ev[4]));
+    float ms = 0.f;
+    EFIE_CUDA(cudaEventElapsedTime(&ms, c->tm.ev[3], c->tm.ev[4]));
+    *best = std::min(*best, ms);
+  }
+  return EFIE_OK;
+}
+
+// M2L autotuner (option m2l_pairs = 2): the ordered-pair kernel (one warp per target cluster,
+// its whole far list) and the unordered-pair kernel (one warp per owner, each coupling tile
+// applied both ways) are timed on this problem's blocks and the faster is kept; the other's
+// buffers are returned.  Sources are zero during the timing (the work does not depend on them).
+static efie_status m2l_autotune(Ctx *c) {
+  if (c->n_m2l_targets == 0) return EFIE_OK;
+  EFIE_CUDA(cudaMemsetAsync(c->d_srcf, 0, sizeof(float4) * (size_t)c->ncl * 2 * c->nI, c->stream));
+  float t_sym = 0.f, t_ord = 0.f;
+  EFIE_TRY(time_m2l(c, &t_sym));
+  float4 *back = c->d_back;
+  c->d_back = nullptr;
+  efie_status s = time_m2l(c, &t_ord);
+  c->d_back = back;
+  EFIE_TRY(s);
+  c->m2l_tune_ms[0] = t_ord;
+  c->m2l_tune_ms[1] = t_sym;
+  if (t_ord <= t_sym) {
+    dfree(c, c->d_back);
+    dfree(c, c->d_own_pgeo);
+    dfree(c, c->d_own_pph);
+  }
+  EFIE_CUDA(cudaMemsetAsync(c->d_accf, 0, sizeof(float4) * (size_t)c->ncl * 2 * c->nI, c->stream));
+  EFIE_CUDA(cudaStreamSynchronize(c->stream));
+  return EFIE_OK;
+}
+
 // node offsets (float4) and the per-pair table of the FP32 M2L
 static efie_status m2l_f32_tables(Ctx *c) {
   const size_t n = (size_t)c->ncl * c->nI;
@@ -1222,7 +1266,7 @@ static efie_status m2l_f32_tables(Ctx *c) {
   // unordered-pair form (option m2l_pairs): the column sums of every pair take npairs x nI x 32
   // bytes; used when they fit in a quarter of the free memory, else the one-sided kernel runs
   dfree(c, c->d_back);
-  if (c->opt.m2l_pairs == 1 && c->npairs > 0) {
+  if (c->opt.m2l_pairs >= 1 && c->npairs > 0) {
     size_t freeb = 0, totb = 0;
     EFIE_CUDA(cudaMemGetInfo(&freeb, &totb));
     const size_t bytes = (size_t)c->npairs * c->nI * 2 * sizeof(float4);
@@ -1241,6 +1285,7 @@ static efie_status m2l_f32_tables(Ctx *c) {
     }
   }
   EFIE_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->opt.m2l_pairs == 2 && c->d_back) EFIE_TRY(m2l_autotune(c));
   return EFIE_OK;
 }
 static size_t m2m_smem(int q1, size_t csz) { return sizeof(double) * 2 * kMaxQ1 * kMaxQ1 + csz * 24 * q1 * q1; }

@@ -9,74 +9,22 @@
 #include <vector>
 
 #include "efie_internal.h"
+#include "gmres_ops.cuh"
 
 namespace efie {
-
-constexpr int kDotThreads = 256;
-constexpr int kRowsPerThread = 4;
-constexpr int kChunk = kDotThreads * kRowsPerThread;
-constexpr int kVecPerBlock = 8;
 
 // part[i * nchunk + chunk] = sum_{t in chunk} conj(V_i[t]) w[t], i = i0 .. i0+7
 __global__ void __launch_bounds__(kDotThreads) k_dot_partial(int N, int nvec, const double2 *__restrict__ V, size_t ldv,
                                                              const double2 *__restrict__ w, double2 *__restrict__ part,
                                                              int nchunk) {
-  int chunk = blockIdx.x, i0 = blockIdx.y * kVecPerBlock;
-  double2 acc[kVecPerBlock];
-#pragma unroll
-  for (int v = 0; v < kVecPerBlock; ++v) acc[v] = make_double2(0.0, 0.0);
-  for (int rr = 0; rr < kRowsPerThread; ++rr) {
-    int t = chunk * kChunk + rr * kDotThreads + threadIdx.x;
-    if (t < N) {
-      double2 wt = w[t];
-#pragma unroll
-      for (int v = 0; v < kVecPerBlock; ++v) {
-        int i = i0 + v;
-        if (i < nvec) {
-          double2 a = V[(size_t)i * ldv + t];
-          acc[v].x += a.x * wt.x + a.y * wt.y;
-          acc[v].y += a.x * wt.y - a.y * wt.x;
-        }
-      }
-    }
-  }
-  __shared__ double2 red[kDotThreads / 32][kVecPerBlock];
-  int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-#pragma unroll
-  for (int v = 0; v < kVecPerBlock; ++v) {
-    double x = acc[v].x, y = acc[v].y;
-    for (int o = 16; o > 0; o >>= 1) {
-      x += __shfl_down_sync(0xffffffffu, x, o);
-      y += __shfl_down_sync(0xffffffffu, y, o);
-    }
-    if (lane == 0) red[wp][v] = make_double2(x, y);
-  }
-  __syncthreads();
-  if (threadIdx.x < kVecPerBlock) {
-    int v = threadIdx.x, i = i0 + v;
-    double2 s = make_double2(0.0, 0.0);
-    for (int k = 0; k < kDotThreads / 32; ++k) {
-      s.x += red[k][v].x;
-      s.y += red[k][v].y;
-    }
-    if (i < nvec) part[(size_t)i * nchunk + chunk] = s;
-  }
+  dot_partial_chunk(N, nvec, blockIdx.y * kVecPerBlock, blockIdx.x, V, ldv, w, part, nchunk);
 }
 
 // h[i] = sum over chunks (one warp per vector, fixed order)
 __global__ void k_dot_final(int nvec, int nchunk, const double2 *__restrict__ part, double2 *__restrict__ h) {
-  int i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  int i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   if (i >= nvec) return;
-  double x = 0.0, y = 0.0;
-  for (int k = lane; k < nchunk; k += 32) {
-    x += part[(size_t)i * nchunk + k].x;
-    y += part[(size_t)i * nchunk + k].y;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    x += __shfl_down_sync(0xffffffffu, x, o);
-    y += __shfl_down_sync(0xffffffffu, y, o);
-  }
-  if (lane == 0) h[i] = make_double2(x, y);
+  dot_final_warp(i, nchunk, part, h);
 }
 
 // w[t] += sgn * sum_i h[i] V_i[t]
@@ -87,23 +35,14 @@ __global__ void k_combine(int N, int nvec, const double2 *__restrict__ V, size_t
   __syncthreads();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N) return;
-  double x = 0.0, y = 0.0;
-  for (int i = 0; i < nvec; ++i) {
-    double2 a = V[(size_t)i * ldv + t], c = sh[i];
-    x += c.x * a.x - c.y * a.y;
-    y += c.x * a.y + c.y * a.x;
-  }
-  w[t].x += sgn * x;
-  w[t].y += sgn * y;
+  combine_entry(t, nvec, V, ldv, sh, sgn, w);
 }
 
 __global__ void k_scale_copy(int N, const double2 *__restrict__ w, const double *__restrict__ st, int idx,
                              double2 *__restrict__ out) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N) return;
-  double b = st[idx];
-  double f = b > 0.0 ? 1.0 / b : 0.0;
-  out[t] = make_double2(w[t].x * f, w[t].y * f);
+  out[t] = scaled_entry(w[t], st[idx]);
 }
 
 __global__ void k_residual(int N, const double2 *__restrict__ b, double2 *__restrict__ r) {
@@ -112,87 +51,15 @@ __global__ void k_residual(int N, const double2 *__restrict__ b, double2 *__rest
   r[t] = make_double2(b[t].x - r[t].x, b[t].y - r[t].y);
 }
 
-// Givens state layout in st: [0] beta of the new vector, [1] residual estimate,
-// [2 .. 2+kr) cs, then sn (complex) [kr][2], then g (complex) [kr+1][2].
-__device__ inline double *gs_cs(double *st) { return st + 2; }
+__global__ void k_givens_init(double *st, int kr, const double2 *h) { givens_init_dev(st, kr, h); }
 
-__global__ void k_givens_init(double *st, int kr, const double2 *h) {
-  // g = (||r||, 0, ...); h[0] holds ||r||^2
-  double beta = sqrt(h[0].x);
-  double *g = st + 2 + kr + 2 * kr;
-  for (int i = 0; i <= kr; ++i) {
-    g[2 * i] = 0.0;
-    g[2 * i + 1] = 0.0;
-  }
-  g[0] = beta;
-  st[0] = beta;
-  st[1] = beta;
-}
-
-// Column j of the Hessenberg matrix from the CGS2 coefficients h1 + h2 and the norm of the
-// orthogonalised vector; previous rotations, new rotation, residual estimate |g_{j+1}|.
 __global__ void k_givens_step(int j, int kr, const double2 *h1, const double2 *h2, const double2 *nrm2, double2 *H,
                               double *st) {
-  double *cs = st + 2;
-  double *sn = st + 2 + kr;       // complex [kr]
-  double *g = st + 2 + 3 * kr;    // complex [kr+1]
-  double beta = sqrt(fmax(nrm2[0].x, 0.0));
-  for (int i = 0; i <= j; ++i) H[(size_t)i * kr + j] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
-  for (int i = 0; i < j; ++i) {
-    double2 a = H[(size_t)i * kr + j], b = H[(size_t)(i + 1) * kr + j];
-    double c = cs[i], sr = sn[2 * i], si = sn[2 * i + 1];
-    // [a; b] <- [c a + s b; -conj(s) a + c b]
-    double2 na = make_double2(c * a.x + sr * b.x - si * b.y, c * a.y + sr * b.y + si * b.x);
-    double2 nb = make_double2(-(sr * a.x + si * a.y) + c * b.x, -(sr * a.y - si * a.x) + c * b.y);
-    H[(size_t)i * kr + j] = na;
-    H[(size_t)(i + 1) * kr + j] = nb;
-  }
-  double2 a = H[(size_t)j * kr + j];
-  double aa = hypot(a.x, a.y), tt = hypot(aa, beta);
-  double c, sr, si;
-  if (aa == 0.0) {
-    c = 0.0; sr = 1.0; si = 0.0;
-  } else {
-    c = aa / tt;
-    sr = (a.x / aa) * beta / tt;
-    si = (a.y / aa) * beta / tt;
-  }
-  cs[j] = c;
-  sn[2 * j] = sr;
-  sn[2 * j + 1] = si;
-  H[(size_t)j * kr + j] = make_double2(c * a.x + sr * beta, c * a.y + si * beta);
-  double gr = g[2 * j], gi = g[2 * j + 1];
-  g[2 * (j + 1)] = -(sr * gr + si * gi);
-  g[2 * (j + 1) + 1] = -(sr * gi - si * gr);
-  g[2 * j] = c * gr;
-  g[2 * j + 1] = c * gi;
-  st[0] = beta;
-  st[1] = hypot(g[2 * (j + 1)], g[2 * (j + 1) + 1]);
+  givens_step_dev(j, kr, h1, h2, nrm2, H, st);
 }
 
-// y = H(0:jd, 0:jd)^{-1} g(0:jd), one warp: row sums in parallel, rows in sequence.
 __global__ void k_backsolve(int jd, int kr, const double2 *H, const double *st, double2 *y) {
-  const double *g = st + 2 + 3 * kr;
-  int lane = threadIdx.x;
-  for (int i = jd - 1; i >= 0; --i) {
-    double x = 0.0, z = 0.0;
-    for (int t = i + 1 + lane; t < jd; t += 32) {
-      double2 hh = H[(size_t)i * kr + t], yy = y[t];
-      x += hh.x * yy.x - hh.y * yy.y;
-      z += hh.x * yy.y + hh.y * yy.x;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      x += __shfl_down_sync(0xffffffffu, x, o);
-      z += __shfl_down_sync(0xffffffffu, z, o);
-    }
-    if (lane == 0) {
-      double sr = g[2 * i] - x, si = g[2 * i + 1] - z;
-      double2 d = H[(size_t)i * kr + i];
-      double den = d.x * d.x + d.y * d.y;
-      y[i] = make_double2((sr * d.x + si * d.y) / den, (si * d.x - sr * d.y) / den);
-    }
-    __syncwarp();
-  }
+  backsolve_warp(jd, kr, H, st, y);
 }
 
 static efie_status ensure_part(Ctx *c, int N, int nvec) {

@@ -32,6 +32,8 @@ ABI_SYMBOLS = (
     "efie_rhs_dipole",
     "efie_far_field_noalloc",
     "efie_server_create", "efie_server_submit", "efie_server_poll", "efie_server_destroy",
+    "efie_setup_many", "efie_group_create", "efie_group_solve", "efie_group_stats", "efie_group_last_error",
+    "efie_group_destroy",
 )
 
 
@@ -116,6 +118,12 @@ def load(path: str = LIB_PATH):
         "efie_check_device_waits": (c_int, [P, ctypes.c_longlong]),
         "efie_exterior_field": (c_int, [P, c_int, P, c_int, P, P, c_int]),
         "efie_rhs_dipole": (c_int, [P, c_int, P, P, P, c_int]),
+        "efie_setup_many": (c_int, [ctypes.POINTER(P), c_int, c_int, I]),
+        "efie_group_create": (c_int, [ctypes.POINTER(P), ctypes.POINTER(P), c_int]),
+        "efie_group_solve": (c_int, [P, ctypes.POINTER(P), ctypes.POINTER(P), c_int, I, D, I]),
+        "efie_group_stats": (c_int, [P, D, c_int]),
+        "efie_group_last_error": (ctypes.c_char_p, [P]),
+        "efie_group_destroy": (c_int, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -197,6 +205,9 @@ class Solver:
 
     def setup(self):
         self._check(self._L.efie_setup(self.h), "efie_setup")
+        self._read_counts()
+
+    def _read_counts(self):
         n = ctypes.c_int64()
         self._check(self._L.efie_num_dofs(self.h, ctypes.byref(n)), "efie_num_dofs")
         self.ndof = int(n.value)
@@ -346,16 +357,94 @@ class Solver:
 
     def setup_timings(self):
         """Figures of the last setup: wall ms; touching-pair quadrature kernel ms, its quadrature
-        points and pairs; separated-pair kernel ms and pairs."""
-        out = np.zeros(6)
-        n = self._L.efie_setup_timings(self.h, _d(out), 6)
+        points and pairs; separated-pair kernel ms and pairs; autotuned M2L times (ordered,
+        unordered pairs) and the kernel kept (0 ordered, 1 unordered)."""
+        out = np.zeros(9)
+        n = self._L.efie_setup_timings(self.h, _d(out), 9)
         return dict(zip(["setup_ms", "near_quad_ms", "near_quad_points", "near_quad_pairs", "near_sep_ms",
-                         "near_sep_pairs"], out[:n]))
+                         "near_sep_pairs", "m2l_ordered_ms", "m2l_pairs_ms", "m2l_kept"], out[:n]))
 
     def last_timings(self):
         out = np.zeros(7)
         n = self._L.efie_last_timings(self.h, _d(out), 7)
         return dict(zip(["total", "gather", "near", "moments_m2m", "m2l", "l2l_eval", "scatter"], out[:n]))
+
+
+def setup_many(solvers, nthreads=8):
+    """efie_setup of several solvers (geometry set) on `nthreads` host threads; their device
+    work overlaps on the GPU.  Raises on the first failure."""
+    L = load()
+    n = len(solvers)
+    arr = (ctypes.c_void_p * n)(*[s.h.value for s in solvers])
+    st = np.zeros(n, np.int32)
+    rc = L.efie_setup_many(arr, n, int(nthreads), _i(st))
+    for k, s in enumerate(solvers):
+        if st[k] < 0:
+            raise EfieError(int(st[k]), f"efie_setup_many (problem {k})", L, s.h)
+        s._read_counts()
+    if rc < 0:
+        raise EfieError(rc, "efie_setup_many", L)
+    return solvers
+
+
+class Group:
+    """Independent problems (set-up solvers on one device) solved in lockstep: one CUDA-graph
+    launch of all products per GMRES step, batched Arnoldi/Givens work."""
+
+    STATS = ("steps", "graph_captures", "kernels", "solve_ms", "product_graph_kernels", "chunks")
+
+    def __init__(self, solvers):
+        self._L = load()
+        self.solvers = list(solvers)
+        n = len(self.solvers)
+        arr = (ctypes.c_void_p * n)(*[s.h.value for s in self.solvers])
+        h = ctypes.c_void_p()
+        st = self._L.efie_group_create(ctypes.byref(h), arr, n)
+        if st < 0:
+            raise EfieError(st, "efie_group_create", self._L)
+        self.h = h
+
+    def solve(self, bs, xs=None):
+        """Solve A_i x_i = b_i for every solver i; bs: list of (ndof_i,) numpy arrays or CUDA
+        tensors.  Returns (xs, iterations, residuals, converged, status)."""
+        n = len(self.solvers)
+        if len(bs) != n:
+            raise ValueError("one right-hand side per problem")
+        if xs is None:
+            xs = [np.empty_like(b) if isinstance(b, np.ndarray) else b.new_empty(b.shape) for b in bs]
+        pb = [_ptr(b) for b in bs]
+        px = [_ptr(x) for x in xs]
+        kinds = {k for _, k in pb} | {k for _, k in px}
+        if len(kinds) != 1:
+            raise ValueError("all vectors must be host arrays or all CUDA tensors")
+        for b, s in zip(bs, self.solvers):
+            if b.shape[-1] != s.ndof:
+                raise ValueError("right-hand side size differs from the problem's DOFs")
+        ab = (ctypes.c_void_p * n)(*[p.value for p, _ in pb])
+        ax = (ctypes.c_void_p * n)(*[p.value for p, _ in px])
+        its = np.zeros(n, np.int32)
+        res = np.zeros(n)
+        conv = np.zeros(n, np.int32)
+        st = self._L.efie_group_solve(self.h, ab, ax, kinds.pop(), _i(its), _d(res), _i(conv))
+        if st < 0:
+            raise RuntimeError(f"efie_group_solve: status {st}: {self._L.efie_group_last_error(self.h).decode()}")
+        return xs, its, res, conv, st
+
+    def stats(self):
+        out = np.zeros(len(self.STATS))
+        k = self._L.efie_group_stats(self.h, _d(out), len(out))
+        return dict(zip(self.STATS, out[:k]))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.efie_group_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

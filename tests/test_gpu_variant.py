@@ -89,3 +89,28 @@ def test_unordered_pair_m2l_full_size_rows():
     rows = r.fmm_rows(xs, elems)
     assert np.abs(y[elems] - rows).max() / np.abs(rows).max() < TOL32
     s.close()
+
+
+def test_m2l_autotune_keeps_a_timed_kernel_and_matches_oracle():
+    """Option m2l_pairs = 2: setup times the ordered and the unordered-pair M2L on the problem's
+    own blocks and keeps the faster; the product is then bitwise the product of the kernel kept
+    (the same solver built with m2l_pairs 0 or 1), and within 1e-5 of the oracle."""
+    from paper_1807_03097_gb300 import Solver
+
+    geo = G.sphere()
+    kw = dict(p=1, level_m=3, kappa=3.0, q=5, eta=1.6, precision=1)
+    s = Solver(geo, m2l_pairs=2, **kw)
+    t = s.setup_timings()
+    assert t["m2l_ordered_ms"] > 0 and t["m2l_pairs_ms"] > 0
+    kept = int(t["m2l_kept"])
+    assert kept == (0 if t["m2l_ordered_ms"] <= t["m2l_pairs_ms"] else 1)
+    ref = Solver(geo, m2l_pairs=kept, **kw)
+    r = O.Problem(geo, p=1, m=3, kappa=3.0, q=5, eta=1.6)
+    rng = np.random.default_rng(83)
+    x = rng.standard_normal(s.ndof) + 1j * rng.standard_normal(s.ndof)
+    y = s.matvec(x)
+    assert np.array_equal(y, ref.matvec(x))
+    yr = r.fmm_matvec(x)[0]
+    assert np.linalg.norm(y - yr) / np.linalg.norm(yr) < TOL32
+    s.close()
+    ref.close()
