@@ -927,6 +927,8 @@ def batch_leg(args, n=None):
             "product_graph_captures": int(stats["graph_captures"]),
             "product_graph_kernels_first": int(stats["product_graph_kernels"]),
             "kernels_in_solve": int(stats["kernels"]), "kernels_setup_and_warmup": int(launches_setup),
+            "graph_device_ms": {"pre": stats.get("pre_ms"), "products": stats.get("products_ms"),
+                                "post_gmres": stats.get("post_ms")},
             "gmres_iterations_median": int(np.median(its)), "gmres_iterations_max": int(its.max()),
             "residual_max": float(res.max()),
             "m2l_autotune": {"unordered_pairs_kept": int(sum(kept)), "ordered_kept": int(len(kept) - sum(kept))},

@@ -347,8 +347,9 @@ const char *efie_last_error(const efie_ctx *ctx);
  * Returns EFIE_NOT_CONVERGED if any system did not converge; EFIE_ESTATE if a context is
  * not set up; EFIE_EINVAL for null pointers, repeated or mixed-device contexts.
  * efie_group_stats: [steps, product-graph captures, kernels launched (graph nodes counted),
- * solve wall time ms, kernel nodes of the product graph, vector chunks] of the last solve;
- * returns the number of values written. */
+ * solve wall time ms, kernel nodes of the product graph, vector chunks, device ms of the pre,
+ * product and post graphs summed over the steps (CUDA events on the group's stream)] of the
+ * last solve; returns the number of values written. */
 typedef struct efie_group efie_group;
 efie_status efie_setup_many(efie_ctx *const *ctxs, int nctx, int nthreads, efie_status *status);
 efie_status efie_group_create(efie_group **g, efie_ctx *const *ctxs, int nctx);

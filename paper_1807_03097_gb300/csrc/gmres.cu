@@ -27,15 +27,11 @@ __global__ void k_dot_final(int nvec, int nchunk, const double2 *__restrict__ pa
   dot_final_warp(i, nchunk, part, h);
 }
 
-// w[t] += sgn * sum_i h[i] V_i[t]
-__global__ void k_combine(int N, int nvec, const double2 *__restrict__ V, size_t ldv, const double2 *__restrict__ h,
-                          double sgn, double2 *__restrict__ w) {
-  extern __shared__ double2 sh[];
-  for (int i = threadIdx.x; i < nvec; i += blockDim.x) sh[i] = h[i];
-  __syncthreads();
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= N) return;
-  combine_entry(t, nvec, V, ldv, sh, sgn, w);
+// w[t] += sgn * sum_i h[i] V_i[t], kCombRows entries per block
+__global__ void __launch_bounds__(kCombThreads) k_combine(int N, int nvec, const double2 *__restrict__ V, size_t ldv,
+                                                          const double2 *__restrict__ h, double sgn,
+                                                          double2 *__restrict__ w) {
+  combine_tile(N, blockIdx.x * kCombRows, nvec, V, ldv, h, sgn, w);
 }
 
 __global__ void k_scale_copy(int N, const double2 *__restrict__ w, const double *__restrict__ st, int idx,
@@ -144,9 +140,9 @@ efie_status dev_gmres(Ctx *c, const double2 *b, double2 *x, int *its_out, double
       ++its;
       // CGS2
       EFIE_TRY(dots(c, N, j + 1, V, N, c->d_w, c->d_h));
-      k_combine<<<grid, blk, sizeof(double2) * (j + 1), st>>>(N, j + 1, V, N, c->d_h, -1.0, c->d_w); ++c->launches;
+      k_combine<<<(N + kCombRows - 1) / kCombRows, kCombThreads, 0, st>>>(N, j + 1, V, N, c->d_h, -1.0, c->d_w); ++c->launches;
       EFIE_TRY(dots(c, N, j + 1, V, N, c->d_w, c->d_h2));
-      k_combine<<<grid, blk, sizeof(double2) * (j + 1), st>>>(N, j + 1, V, N, c->d_h2, -1.0, c->d_w); ++c->launches;
+      k_combine<<<(N + kCombRows - 1) / kCombRows, kCombThreads, 0, st>>>(N, j + 1, V, N, c->d_h2, -1.0, c->d_w); ++c->launches;
       EFIE_TRY(dots(c, N, 1, c->d_w, N, c->d_w, c->d_h2 + kr));
       k_givens_step<<<1, 1, 0, st>>>(j, kr, c->d_h, c->d_h2, c->d_h2 + kr, c->d_H, c->d_gs); ++c->launches;
       k_scale_copy<<<grid, blk, 0, st>>>(N, c->d_w, c->d_gs, 0, V + (size_t)(j + 1) * N); ++c->launches;
@@ -159,7 +155,7 @@ efie_status dev_gmres(Ctx *c, const double2 *b, double2 *x, int *its_out, double
     }
     if (jd > 0) {
       k_backsolve<<<1, 32, 0, st>>>(jd, kr, c->d_H, c->d_gs, c->d_sol); ++c->launches;
-      k_combine<<<grid, blk, sizeof(double2) * jd, st>>>(N, jd, V, N, c->d_sol, 1.0, x); ++c->launches;
+      k_combine<<<(N + kCombRows - 1) / kCombRows, kCombThreads, 0, st>>>(N, jd, V, N, c->d_sol, 1.0, x); ++c->launches;
       EFIE_CUDA(cudaGetLastError());
     }
     if (res <= target) {
@@ -309,9 +305,9 @@ efie_status dev_gmres_batch(Ctx *c, int R, const double2 *const *b, double2 *con
       } else if (s.phase == kArnoldi) {
         const int j = s.j;
         EFIE_TRY(dots(c, N, j + 1, s.V, N, s.w, s.h));
-        k_combine<<<grid, blk, sizeof(double2) * (j + 1), st>>>(N, j + 1, s.V, N, s.h, -1.0, s.w); ++c->launches;
+        k_combine<<<(N + kCombRows - 1) / kCombRows, kCombThreads, 0, st>>>(N, j + 1, s.V, N, s.h, -1.0, s.w); ++c->launches;
         EFIE_TRY(dots(c, N, j + 1, s.V, N, s.w, s.h2));
-        k_combine<<<grid, blk, sizeof(double2) * (j + 1), st>>>(N, j + 1, s.V, N, s.h2, -1.0, s.w); ++c->launches;
+        k_combine<<<(N + kCombRows - 1) / kCombRows, kCombThreads, 0, st>>>(N, j + 1, s.V, N, s.h2, -1.0, s.w); ++c->launches;
         EFIE_TRY(dots(c, N, 1, s.w, N, s.w, s.h2 + kr));
         k_givens_step<<<1, 1, 0, st>>>(j, kr, s.h, s.h2, s.h2 + kr, s.H, s.gs); ++c->launches;
         k_scale_copy<<<grid, blk, 0, st>>>(N, s.w, s.gs, 0, s.V + (size_t)(j + 1) * N); ++c->launches;
@@ -344,7 +340,7 @@ efie_status dev_gmres_batch(Ctx *c, int R, const double2 *const *b, double2 *con
         const bool nan = !(s.res == s.res);
         if (s.res <= s.target || nan || jd == kr || s.its >= maxit) {
           k_backsolve<<<1, 32, 0, st>>>(jd, kr, s.H, s.gs, s.sol); ++c->launches;
-          k_combine<<<grid, blk, sizeof(double2) * jd, st>>>(N, jd, s.V, N, s.sol, 1.0, s.x); ++c->launches;
+          k_combine<<<(N + kCombRows - 1) / kCombRows, kCombThreads, 0, st>>>(N, jd, s.V, N, s.sol, 1.0, s.x); ++c->launches;
           if (s.res <= s.target) s.phase = kConfirm;
           else if (nan || s.its >= maxit) s.phase = kDone;
           else s.phase = kStart;

@@ -75,17 +75,35 @@ __device__ __forceinline__ void dot_final_warp(int i, int nchunk, const double2 
   if (lane == 0) h[i] = make_double2(x, y);
 }
 
-// w[t] += sgn * sum_i c_i V_i[t] for one entry t (c in shared memory).
-__device__ __forceinline__ void combine_entry(int t, int nvec, const double2 *__restrict__ V, size_t ldv,
-                                              const double2 *c, double sgn, double2 *__restrict__ w) {
+// w[t] += sgn * sum_i c_i V_i[t] for the kCombRows entries t0 .. t0 + 31 of one block of
+// kCombThreads threads: warp k sums the vectors i = k, k + 8, k + 16, ... for its lane's entry
+// (each load a 512-byte row segment), and the 8 partial sums are added in the order k = 0..7.
+constexpr int kCombRows = 32;
+constexpr int kCombThreads = 256;
+__device__ __forceinline__ void combine_tile(int N, int t0, int nvec, const double2 *__restrict__ V, size_t ldv,
+                                             const double2 *__restrict__ c, double sgn, double2 *__restrict__ w) {
+  __shared__ double2 part[kCombThreads / 32][kCombRows];
+  const int lane = threadIdx.x & 31, k = threadIdx.x >> 5, t = t0 + lane;
   double x = 0.0, y = 0.0;
-  for (int i = 0; i < nvec; ++i) {
-    double2 a = V[(size_t)i * ldv + t], ci = c[i];
-    x += ci.x * a.x - ci.y * a.y;
-    y += ci.x * a.y + ci.y * a.x;
+  if (t < N) {
+    for (int i = k; i < nvec; i += kCombThreads / 32) {
+      double2 a = V[(size_t)i * ldv + t], ci = c[i];
+      x += ci.x * a.x - ci.y * a.y;
+      y += ci.x * a.y + ci.y * a.x;
+    }
   }
-  w[t].x += sgn * x;
-  w[t].y += sgn * y;
+  part[k][lane] = make_double2(x, y);
+  __syncthreads();
+  if (k == 0 && t < N) {
+    double sx = 0.0, sy = 0.0;
+    for (int kk = 0; kk < kCombThreads / 32; ++kk) {
+      sx += part[kk][lane].x;
+      sy += part[kk][lane].y;
+    }
+    w[t].x += sgn * sx;
+    w[t].y += sgn * sy;
+  }
+  __syncthreads();
 }
 
 __device__ __forceinline__ double2 scaled_entry(double2 w, double beta) {
@@ -116,17 +134,18 @@ __device__ __forceinline__ void givens_step_dev(int j, int kr, const double2 *h1
   double *sn = st + 2 + kr;       // complex [kr]
   double *g = st + 2 + 3 * kr;    // complex [kr+1]
   double beta = sqrt(fmax(nrm2[0].x, 0.0));
-  for (int i = 0; i <= j; ++i) H[(size_t)i * kr + j] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
+  // the new column h1 + h2, rotated by the previous rotations; the entry that rotation i passes
+  // on to row i + 1 stays in a register (the column of H is strided in memory)
+  double2 a = make_double2(h1[0].x + h2[0].x, h1[0].y + h2[0].y);
   for (int i = 0; i < j; ++i) {
-    double2 a = H[(size_t)i * kr + j], b = H[(size_t)(i + 1) * kr + j];
-    double c = cs[i], sr = sn[2 * i], si = sn[2 * i + 1];
+    const double2 b = make_double2(h1[i + 1].x + h2[i + 1].x, h1[i + 1].y + h2[i + 1].y);
+    const double c = cs[i], sr = sn[2 * i], si = sn[2 * i + 1];
     // [a; b] <- [c a + s b; -conj(s) a + c b]
-    double2 na = make_double2(c * a.x + sr * b.x - si * b.y, c * a.y + sr * b.y + si * b.x);
-    double2 nb = make_double2(-(sr * a.x + si * a.y) + c * b.x, -(sr * a.y - si * a.x) + c * b.y);
+    const double2 na = make_double2(c * a.x + sr * b.x - si * b.y, c * a.y + sr * b.y + si * b.x);
+    const double2 nb = make_double2(-(sr * a.x + si * a.y) + c * b.x, -(sr * a.y - si * a.x) + c * b.y);
     H[(size_t)i * kr + j] = na;
-    H[(size_t)(i + 1) * kr + j] = nb;
+    a = nb;
   }
-  double2 a = H[(size_t)j * kr + j];
   double aa = hypot(a.x, a.y), tt = hypot(aa, beta);
   double c, sr, si;
   if (aa == 0.0) {

@@ -52,29 +52,21 @@ __global__ void k_g_backsolve(const GSysD *__restrict__ T) {
   backsolve_warp(s.jd, s.kr, s.H, s.gs, s.sol);
 }
 
-__global__ void __launch_bounds__(kDotThreads) k_g_update_pack(const GSysD *__restrict__ T, const int *__restrict__ csys,
-                                                                const int *__restrict__ cidx) {
-  extern __shared__ double2 sh[];
+// grid (chunks, kChunk / kCombRows): the block's kCombRows entries of its chunk
+__global__ void __launch_bounds__(kCombThreads) k_g_update_pack(const GSysD *__restrict__ T, const int *__restrict__ csys,
+                                                                 const int *__restrict__ cidx) {
   const GSysD s = T[csys[blockIdx.x]];
-  const int ch = cidx[blockIdx.x];
-  if (s.mode & G_PRE) {
-    for (int i = threadIdx.x; i < s.jd; i += blockDim.x) sh[i] = s.sol[i];
-    __syncthreads();
-    for (int rr = 0; rr < kRowsPerThread; ++rr) {
-      int t = ch * kChunk + rr * kDotThreads + threadIdx.x;
-      if (t < s.N) combine_entry(t, s.jd, s.V, (size_t)s.N, sh, 1.0, s.x);
-    }
+  const int t0 = cidx[blockIdx.x] * kChunk + blockIdx.y * kCombRows;
+  if (t0 >= s.N) return;
+  if (s.mode & G_PRE) combine_tile(s.N, t0, s.jd, s.V, (size_t)s.N, s.sol, 1.0, s.x);
+  const int t = t0 + (int)threadIdx.x;
+  if (threadIdx.x >= kCombRows || t >= s.N) return;
+  if (s.mode & G_INIT) {
+    s.x[t] = make_double2(0.0, 0.0);
+    s.r[t] = s.b[t];
   }
-  for (int rr = 0; rr < kRowsPerThread; ++rr) {
-    int t = ch * kChunk + rr * kDotThreads + threadIdx.x;
-    if (t >= s.N) continue;
-    if (s.mode & G_INIT) {
-      s.x[t] = make_double2(0.0, 0.0);
-      s.r[t] = s.b[t];
-    }
-    if (s.mode & G_PROD_V) s.px[t] = s.V[(size_t)s.j * s.N + t];
-    else if (s.mode & G_PROD_X) s.px[t] = s.x[t];
-  }
+  if (s.mode & G_PROD_V) s.px[t] = s.V[(size_t)s.j * s.N + t];
+  else if (s.mode & G_PROD_X) s.px[t] = s.x[t];
 }
 
 __global__ void __launch_bounds__(kDotThreads) k_g_unpack(const GSysD *__restrict__ T, const int *__restrict__ csys,
@@ -148,19 +140,13 @@ __global__ void k_g_dot_final(const GSysD *__restrict__ T, int pass) {
   for (int i = threadIdx.x >> 5; i < nvec; i += blockDim.x >> 5) dot_final_warp(i, s.nchunk, s.part, dst);
 }
 
-__global__ void __launch_bounds__(kDotThreads) k_g_combine(const GSysD *__restrict__ T, const int *__restrict__ csys,
-                                                            const int *__restrict__ cidx, int pass) {
-  extern __shared__ double2 sh[];
+__global__ void __launch_bounds__(kCombThreads) k_g_combine(const GSysD *__restrict__ T, const int *__restrict__ csys,
+                                                             const int *__restrict__ cidx, int pass) {
   const GSysD s = T[csys[blockIdx.x]];
   if (!(s.mode & G_ARN)) return;
-  const double2 *c = pass == 0 ? s.h : s.h2;
-  const int nvec = s.j + 1, ch = cidx[blockIdx.x];
-  for (int i = threadIdx.x; i < nvec; i += blockDim.x) sh[i] = c[i];
-  __syncthreads();
-  for (int rr = 0; rr < kRowsPerThread; ++rr) {
-    int t = ch * kChunk + rr * kDotThreads + threadIdx.x;
-    if (t < s.N) combine_entry(t, nvec, s.V, (size_t)s.N, sh, -1.0, s.w);
-  }
+  const int t0 = cidx[blockIdx.x] * kChunk + blockIdx.y * kCombRows;
+  if (t0 >= s.N) return;
+  combine_tile(s.N, t0, s.j + 1, s.V, (size_t)s.N, pass == 0 ? s.h : s.h2, -1.0, s.w);
 }
 
 // one thread per system: Givens step or start, then the values the host reads
@@ -216,6 +202,8 @@ struct Group {
   double *h_out = nullptr, *d_out = nullptr;
   int *d_csys = nullptr, *d_cidx = nullptr;
   cudaEvent_t fork = nullptr;
+  cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};  // around the three graphs of a step
+  double graph_ms[3] = {0.0, 0.0, 0.0};                       // pre, products, post (last solve)
   std::vector<cudaEvent_t> joins;
   cudaGraphExec_t g_pre = nullptr, g_post = nullptr, g_prod = nullptr;
   std::vector<int> members;  // systems with a branch in g_prod
@@ -256,7 +244,7 @@ efie_status body_pre(Group *g) {
   cudaStream_t st = c->stream;
   EFIE_CUDA(cudaMemcpyAsync(g->d_tab, g->h_tab, sizeof(GSysD) * g->nsys, cudaMemcpyHostToDevice, st));
   k_g_backsolve<<<g->nsys, 32, 0, st>>>(g->d_tab);
-  k_g_update_pack<<<g->nchunks, kDotThreads, sizeof(double2) * (g->kr_max + 1), st>>>(g->d_tab, g->d_csys, g->d_cidx);
+  k_g_update_pack<<<dim3(g->nchunks, kChunk / kCombRows), kCombThreads, 0, st>>>(g->d_tab, g->d_csys, g->d_cidx);
   EFIE_CUDA(cudaGetLastError());
   return EFIE_OK;
 }
@@ -264,12 +252,12 @@ efie_status body_pre(Group *g) {
 efie_status body_post(Group *g) {
   Ctx *c = &g->gc;
   cudaStream_t st = c->stream;
-  const size_t shc = sizeof(double2) * (g->kr_max + 1);
   k_g_unpack<<<g->nchunks, kDotThreads, 0, st>>>(g->d_tab, g->d_csys, g->d_cidx);
   for (int pass = 0; pass < 3; ++pass) {
     k_g_dot_partial<<<g->nchunks, kDotThreads, 0, st>>>(g->d_tab, g->d_csys, g->d_cidx, pass);
     k_g_dot_final<<<g->nsys, 256, 0, st>>>(g->d_tab, pass);
-    if (pass < 2) k_g_combine<<<g->nchunks, kDotThreads, shc, st>>>(g->d_tab, g->d_csys, g->d_cidx, pass);
+    if (pass < 2)
+      k_g_combine<<<dim3(g->nchunks, kChunk / kCombRows), kCombThreads, 0, st>>>(g->d_tab, g->d_csys, g->d_cidx, pass);
   }
   k_g_givens<<<(g->nsys + 127) / 128, 128, 0, st>>>(g->d_tab, g->nsys, g->d_out);
   k_g_scale<<<g->nchunks, kDotThreads, 0, st>>>(g->d_tab, g->d_csys, g->d_cidx);
@@ -318,6 +306,8 @@ void release(Group *g) {
   g->h_tab = nullptr;
   g->h_out = nullptr;
   if (g->fork) cudaEventDestroy(g->fork);
+  for (cudaEvent_t &e : g->tev)
+    if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : g->joins) cudaEventDestroy(e);
   g->joins.clear();
   if (c->stream) cudaStreamDestroy(c->stream);
@@ -364,6 +354,8 @@ efie_status efie_group_create(efie_group **out, efie_ctx *const *ctxs, int nctx)
   if (pool_ref(dev) != EFIE_OK) return fail(EFIE_ECUDA);
   c->pool_held = true;
   if (cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming) != cudaSuccess) return fail(EFIE_ECUDA);
+  for (cudaEvent_t &e : g->tev)
+    if (cudaEventCreate(&e) != cudaSuccess) return fail(EFIE_ECUDA);
   g->nsys = nctx;
   for (int i = 0; i < nctx; ++i) {
     Ctx *m = reinterpret_cast<Ctx *>(ctxs[i]);
@@ -417,9 +409,9 @@ const char *efie_group_last_error(const efie_group *grp) {
 int efie_group_stats(const efie_group *grp, double *out, int n) {
   if (!grp || !out || n < 1) return 0;
   const Group *g = reinterpret_cast<const Group *>(grp);
-  const double v[6] = {(double)g->steps, (double)g->captures, (double)g->kernels, g->solve_ms,
-                       (double)g->prod_kernels, (double)g->nchunks};
-  const int k = std::min(n, 6);
+  const double v[9] = {(double)g->steps, (double)g->captures, (double)g->kernels, g->solve_ms,
+                       (double)g->prod_kernels, (double)g->nchunks, g->graph_ms[0], g->graph_ms[1], g->graph_ms[2]};
+  const int k = std::min(n, 9);
   for (int i = 0; i < k; ++i) out[i] = v[i];
   return k;
 }
@@ -474,16 +466,6 @@ efie_status efie_group_solve(efie_group *grp, const double *const *b, double *co
     d.px = m->d_x;
     d.py = m->d_y;
   }
-  // the shared-memory coefficients of the combine steps hold kr_max + 1 complex values
-  const size_t shc = sizeof(double2) * (kr_max + 1);
-  if (shc > 48 * 1024) {
-    EFIE_CUDA(cudaFuncSetAttribute(k_g_update_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shc));
-    EFIE_CUDA(cudaFuncSetAttribute(k_g_combine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shc));
-  }
-  if (shc > 227 * 1024) {
-    c->err = "restart length too large for the group solver";
-    return EFIE_EINVAL;
-  }
   g->kr_max = kr_max;
   // every context finishes what it has queued, then its product runs once outside a graph
   // (buffers created on first use exist before the capture)
@@ -501,11 +483,21 @@ efie_status efie_group_solve(efie_group *grp, const double *const *b, double *co
   g->captures = 1;
   g->kernels = 0;
 
+  g->graph_ms[0] = g->graph_ms[1] = g->graph_ms[2] = 0.0;
   auto run_step = [&](bool any_product) -> efie_status {
+    EFIE_CUDA(cudaEventRecord(g->tev[0], c->stream));
     EFIE_CUDA(cudaGraphLaunch(g->g_pre, c->stream));
+    EFIE_CUDA(cudaEventRecord(g->tev[1], c->stream));
     if (any_product) EFIE_CUDA(cudaGraphLaunch(g->g_prod, c->stream));
+    EFIE_CUDA(cudaEventRecord(g->tev[2], c->stream));
     EFIE_CUDA(cudaGraphLaunch(g->g_post, c->stream));
+    EFIE_CUDA(cudaEventRecord(g->tev[3], c->stream));
     EFIE_CUDA(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 3; ++k) {
+      float ms = 0.f;
+      EFIE_CUDA(cudaEventElapsedTime(&ms, g->tev[k], g->tev[k + 1]));
+      g->graph_ms[k] += ms;
+    }
     ++g->steps;
     g->kernels += kPreKernels + kPostKernels + 1 + (any_product ? g->prod_kernels : 0);
     return EFIE_OK;

@@ -776,6 +776,61 @@ __global__ void __launch_bounds__(128) k_near_apply_v4(int nE, const int *__rest
   }
 }
 
+// One warp per target element (a contiguous range of elements per warp, the same count for
+// every warp): the warp reads the element's source blocks BIF at a time with 16-byte loads as
+// k_near_apply_v4 does, adds each block's FP32 partial sums by two-sum, and combines its column
+// groups with shuffles in a fixed order (FP64 sum).  No shared memory and no block barrier, so a
+// warp goes on to its next element as soon as it has written the last.
+template <int NB, int BIF>
+__global__ void __launch_bounds__(128) k_near_apply_w(int nE, int per, const int *__restrict__ ptr,
+                                                      const int *__restrict__ src, const float4 *__restrict__ blocks,
+                                                      const float2 *__restrict__ xs, double2 *__restrict__ ysn) {
+  constexpr int LPC = NB / 2, CPR = 32 / LPC, ROUNDS = (NB + CPR - 1) / CPR;
+  constexpr int F4 = NB * NB / 2;
+  const int lane = threadIdx.x & 31;
+  const int rp = lane % LPC, cg = lane / LPC;
+  const bool act = cg < CPR;
+  const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int e0 = wid * per, e1 = min(e0 + per, nE);
+  for (int e = e0; e < e1; ++e) {
+    float h[4] = {0.f, 0.f, 0.f, 0.f}, cmp[4] = {0.f, 0.f, 0.f, 0.f};
+    const int k0 = ptr[e], k1 = ptr[e + 1];
+    for (int k = k0; k < k1; k += BIF) {
+      float4 b[BIF][ROUNDS];
+      float2 xv[BIF][ROUNDS];
+#pragma unroll
+      for (int i = 0; i < BIF; ++i) {
+        const bool have = k + i < k1;
+        const int kk = have ? k + i : k;
+        near_v4_block<NB>(blocks + (size_t)kk * F4, xs + (size_t)src[kk] * NB, rp, cg, act && have, b[i], xv[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < BIF; ++i) {
+        float p[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int t = 0; t < ROUNDS; ++t) {
+          p[0] = fmaf(b[i][t].x, xv[i][t].x, fmaf(-b[i][t].y, xv[i][t].y, p[0]));
+          p[1] = fmaf(b[i][t].x, xv[i][t].y, fmaf(b[i][t].y, xv[i][t].x, p[1]));
+          p[2] = fmaf(b[i][t].z, xv[i][t].x, fmaf(-b[i][t].w, xv[i][t].y, p[2]));
+          p[3] = fmaf(b[i][t].z, xv[i][t].y, fmaf(b[i][t].w, xv[i][t].x, p[3]));
+        }
+        if (k + i < k1)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) two_sum(h[q], cmp[q], p[q]);
+      }
+    }
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int g = 0; g < CPR; ++g)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s[q] += (double)__shfl_sync(0xffffffffu, h[q] + cmp[q], g * LPC + rp);
+    if (lane < LPC) {
+      ysn[(size_t)e * NB + 2 * lane] = make_double2(s[0], s[1]);
+      ysn[(size_t)e * NB + 2 * lane + 1] = make_double2(s[2], s[3]);
+    }
+  }
+}
+
 // The same product for several right-hand sides (FP32 blocks, mixed form): each block is read
 // once for a group of up to RB right-hand sides (grid dimension y), which divides the HBM
 // traffic of the near field by RB.  Vectors of right-hand side r start at r * vstride.

@@ -5,6 +5,7 @@
 //  a13: E_inf(d) = (W - d (d.W)) / 4pi with W = int w exp(-i kappa d.y) dsigma, the far field
 //       of the electric single-layer potential (eq. ESLP); on a patch w dsigma = dF w_hat ds.
 // Tensor Gauss rules with quad_regular points per direction; deterministic reductions.
+#include <algorithm>
 #include <cmath>
 
 #include "geom.cuh"
@@ -89,26 +90,26 @@ efie_status dev_rhs(Ctx *c, const double *dir, const double *pol, double2 *g) {
   return EFIE_OK;
 }
 
-// partial W over one element for one direction: part[(dir * nE + e) * 3 + k]
+// Partial W of one element for every direction: part[(dir * nE + e) * 3 + k].  The block first
+// evaluates, at each of the element's g x g Gauss points (one thread each), the point F(x) and
+// the weighted surface current v = w h^2 (d1F w_1 + d2F w_2) from the element's superspace
+// coefficients, once; then thread t sums e^{-i kappa d.F(x)} v over the points, in a fixed
+// order, for the directions t, t + blockDim, ...
 __global__ void k_ff_partial(const PatchDesc *patches, const double *knots, const double4 *cpw, int n, int p, int g,
-                             const double *gx, const double *gw, double kappa, int nE, const double *dirs,
+                             const double *gx, const double *gw, double kappa, int nE, int ndir, const double *dirs,
                              const double2 *__restrict__ xs, double2 *part) {
-  int e = blockIdx.x, dd = blockIdx.y;
-  int P1 = p + 1;
-  __shared__ double2 red[256][3];
+  extern __shared__ double sff[];
+  const int e = blockIdx.x, G2 = g * g, P1 = p + 1;
+  double *sX = sff;           // [G2][3]
+  double2 *sV = reinterpret_cast<double2 *>(sff + 3 * G2);  // [G2][3]
   int j, i1, i2;
   elem_locate(e, n, j, i1, i2);
-  double h = 1.0 / n;
-  int t = threadIdx.x;
-  double2 W[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
-  if (t < g * g) {
-    double u = gx[t % g], v = gx[t / g];
+  const double h = 1.0 / n;
+  for (int t = threadIdx.x; t < G2; t += blockDim.x) {
+    const double u = gx[t % g], v = gx[t / g];
     double X[3], D1[3], D2[3];
     dev_patch_eval(patches[j], knots, cpw, (i1 + u) * h, (i2 + v) * h, X, D1, D2);
-    const double *d = dirs + 3 * dd;
-    double sn, cs;
-    sincos(-kappa * (d[0] * X[0] + d[1] * X[1] + d[2] * X[2]), &sn, &cs);
-    double wt = gw[t % g] * gw[t / g] * h * h;
+    const double wt = gw[t % g] * gw[t / g] * h * h;
     double Bu[kMaxP1], dBu[kMaxP1], Bv[kMaxP1], dBv[kMaxP1];
     dev_bernstein(p, u, Bu, dBu);
     dev_bernstein(p, v, Bv, dBv);
@@ -117,28 +118,33 @@ __global__ void k_ff_partial(const PatchDesc *patches, const double *knots, cons
     for (int al = 0; al < 2; ++al)
       for (int b = 0; b < P1; ++b)
         for (int a = 0; a < P1; ++a) {
-          double f = Bu[a] * Bv[b];
-          double2 cf = xe[(al * P1 + b) * P1 + a];
+          const double f = Bu[a] * Bv[b];
+          const double2 cf = xe[(al * P1 + b) * P1 + a];
           wa[al].x += f * cf.x;
           wa[al].y += f * cf.y;
         }
     for (int k = 0; k < 3; ++k) {
-      double vx = D1[k] * wa[0].x + D2[k] * wa[1].x, vy = D1[k] * wa[0].y + D2[k] * wa[1].y;
-      W[k] = make_double2(wt * (cs * vx - sn * vy), wt * (cs * vy + sn * vx));
+      sX[3 * t + k] = X[k];
+      sV[3 * t + k] = make_double2(wt * (D1[k] * wa[0].x + D2[k] * wa[1].x), wt * (D1[k] * wa[0].y + D2[k] * wa[1].y));
     }
   }
-  for (int k = 0; k < 3; ++k) red[t][k] = W[k];
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (t < s)
+  for (int dd = threadIdx.x; dd < ndir; dd += blockDim.x) {
+    const double d0 = dirs[3 * dd], d1 = dirs[3 * dd + 1], d2 = dirs[3 * dd + 2];
+    double2 W[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+    for (int t = 0; t < G2; ++t) {
+      double sn, cs;
+      sincos(-kappa * (d0 * sX[3 * t] + d1 * sX[3 * t + 1] + d2 * sX[3 * t + 2]), &sn, &cs);
+#pragma unroll
       for (int k = 0; k < 3; ++k) {
-        red[t][k].x += red[t + s][k].x;
-        red[t][k].y += red[t + s][k].y;
+        const double2 v = sV[3 * t + k];
+        W[k].x += cs * v.x - sn * v.y;
+        W[k].y += cs * v.y + sn * v.x;
       }
-    __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) part[((size_t)dd * nE + e) * 3 + k] = W[k];
   }
-  if (t == 0)
-    for (int k = 0; k < 3; ++k) part[((size_t)dd * nE + e) * 3 + k] = red[0][k];
 }
 
 __global__ void k_ff_final(int nE, const double *dirs, const double2 *part, double2 *out) {
@@ -186,9 +192,12 @@ efie_status dev_far_field(Ctx *c, const double2 *w, int ndir, const double *dirs
   EFIE_CUDA(cudaMemcpyAsync(d_rule + c->gr, c->tab.gw.data(), 8 * (size_t)c->gr, cudaMemcpyHostToDevice, c->stream));
   EFIE_CUDA(cudaMemcpyAsync(d_dirs, dirs, 24 * (size_t)ndir, cudaMemcpyHostToDevice, c->stream));
   EFIE_TRY(dev_gather(c, w, c->d_xs));
-  dim3 grid(c->nE, ndir);
-  k_ff_partial<<<grid, 256, 0, c->stream>>>(c->d_patches, c->d_knots, c->d_cpw, c->n, c->p, c->gr, d_rule,
-                                            d_rule + c->gr, c->kappa, c->nE, d_dirs, c->d_xs, d_part); ++c->launches;
+  const int G2 = c->gr * c->gr;
+  const int thr = std::min(256, std::max(64, ((std::max(G2, ndir) + 31) / 32) * 32));
+  k_ff_partial<<<c->nE, thr, sizeof(double) * 9 * G2, c->stream>>>(c->d_patches, c->d_knots, c->d_cpw, c->n, c->p,
+                                                                     c->gr, d_rule, d_rule + c->gr, c->kappa, c->nE,
+                                                                     ndir, d_dirs, c->d_xs, d_part);
+  ++c->launches;
   k_ff_final<<<ndir, 256, 0, c->stream>>>(c->nE, d_dirs, d_part, out); ++c->launches;
   EFIE_CUDA(cudaGetLastError());
   EFIE_CUDA(cudaStreamSynchronize(c->stream));

@@ -391,7 +391,8 @@ class Group:
     """Independent problems (set-up solvers on one device) solved in lockstep: one CUDA-graph
     launch of all products per GMRES step, batched Arnoldi/Givens work."""
 
-    STATS = ("steps", "graph_captures", "kernels", "solve_ms", "product_graph_kernels", "chunks")
+    STATS = ("steps", "graph_captures", "kernels", "solve_ms", "product_graph_kernels", "chunks", "pre_ms",
+             "products_ms", "post_ms")
 
     def __init__(self, solvers):
         self._L = load()

@@ -24,10 +24,12 @@ PROBLEMS = [
 ]
 
 
-def make(i, tol=1e-8, maxit=400, restart=1500):
+def make(i, tol=None, maxit=400, restart=1500):
+    """FP64 problems solve to 1e-8; mixed ones to 1e-6 (their operator carries FP32 rounding)."""
     from paper_1807_03097_gb300 import Solver
 
     mk, p, m, k, prec = PROBLEMS[i]
+    tol = tol if tol is not None else (1e-6 if prec else 1e-8)
     return Solver(mk(), p=p, level_m=m, kappa=k, q=4, eta=1.6, precision=prec, gmres_tol=tol, gmres_maxit=maxit,
                   gmres_restart=restart)
 
@@ -50,7 +52,7 @@ def test_group_equals_each_solve_alone_bitwise():
     xs, its, res, conv, st = g.solve(bs)
     assert st == 0 and conv.all()
     stats = g.stats()
-    assert stats["steps"] >= its.max()
+    assert stats["steps"] >= its.max() and stats["products_ms"] > 0 and stats["post_ms"] > 0
     g.close()
     for i, s in enumerate(solvers):
         x1, info, _ = s.solve(bs[i])
@@ -65,7 +67,7 @@ def test_group_solutions_solve_the_oracle_system():
     from paper_1807_03097_gb300.efie import Group
 
     idx = [0, 1]  # mixed sphere, FP64 cube
-    solvers = [make(i, tol=1e-8) for i in idx]
+    solvers = [make(i) for i in idx]
     data = [rhs(s, i) for s, i in zip(solvers, idx)]
     g = Group(solvers)
     xs, its, res, conv, st = g.solve([d[0] for d in data])
@@ -77,7 +79,7 @@ def test_group_solutions_solve_the_oracle_system():
         b = ref.rhs(data[k][1], data[k][2])
         assert np.abs(b - data[k][0]).max() < 1e-11 * np.abs(b).max()
         r = np.linalg.norm(b - ref.fmm_matvec(xs[k])[0]) / np.linalg.norm(b)
-        # FP64: the GMRES tolerance; mixed: plus the mixed operator's error (1e-5 target)
+        # FP64: the GMRES tolerance; mixed: its tolerance plus the mixed operator's error (1e-5)
         assert r < (2e-8 if prec == 0 else 2e-5), (i, r)
     for s in solvers:
         s.close()
