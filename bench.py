@@ -452,7 +452,7 @@ def run_gpu(args):
             nt.append(s.last_timings()["near"])
     near_alone = statistics.median(nt)
     near_bytes = s.nnear * s.nb * s.nb * (8 if prec else 16) + s.nsup * (8 + 16 + 16 if prec else 32)
-    near_roof = {"kernel": "k_near_apply_v4" if prec else "k_near_apply", "bound": "hbm",
+    near_roof = {"kernel": "k_near_apply_w" if prec else "k_near_apply", "bound": "hbm",
                  "achieved": near_bytes / (near_alone * 1e-3) / 1e9, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
                  "near_ms": near_alone, "near_ms_in_product": mv["near"], "bytes": near_bytes,
                  "work": "blocks (8 B per entry in FP32) + x* read (FP64) and converted (FP32 write + read) + y* write",

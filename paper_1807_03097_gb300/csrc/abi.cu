@@ -124,6 +124,8 @@ efie_status efie_create(efie_ctx **out, const efie_options *opt, void *cuda_stre
   if (!c) return EFIE_ENOMEM;
   c->opt = *opt;
   cudaGetDevice(&c->device);
+  cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
+  if (c->nsm < 1) c->nsm = 1;
   if (cuda_stream) {
     c->stream = (cudaStream_t)cuda_stream;
   } else {

@@ -55,6 +55,7 @@ struct Tables {
 struct Ctx {
   efie_options opt{};
   int device = 0;
+  int nsm = 152;  // streaming multiprocessors of the device
   cudaStream_t stream = nullptr;
   cudaStream_t stream2 = nullptr;  // near-field apply overlaps the far-field chain
   cudaEvent_t fork = nullptr, join = nullptr;

@@ -47,31 +47,45 @@ struct TcLayout {
   static_assert(2 * 128 * (NP + 1) * 4 <= 2 * kStage, "epilogue staging must fit in the stages");
 };
 
-// ut = g + xt (pair offset plus target node), used by the direct form (MODE 0) only
+// Two kernel entries (one target node, source nodes xs0 and xs1) with packed FP32 arithmetic
+// (FFMA2 and friends: two lanes' worth of work per instruction), phase forms as in the CUDA-core
+// kernels; ut = g + xt (pair offset plus target node) is used by the direct form (MODE 0) only.
+// re = (Re G0, Re G1), im = (Im G0, Im G1).
 template <int MODE>
-__device__ __forceinline__ float2 kernel_entry(float4 g, float2 ph, float kappa, float4 xt, float4 ut, float4 xs) {
+__device__ __forceinline__ void kernel_entry2(float4 g, float2 ph, float kappa, float4 xt, float4 ut, float4 xs0,
+                                              float4 xs1, float2 &re, float2 &im) {
   const float inv2pi = 0.15915494309189535f, c1 = 6.28318548202514648f, c2 = -1.7484555e-7f;
-  float rinv, phs;
+  float2 rinv, phs;
   if (MODE == 0) {
-    float vx = ut.x - xs.x, vy = ut.y - xs.y, vz = ut.z - xs.z;
-    float r2 = vx * vx + vy * vy + vz * vz;
-    rinv = rsqrt_ftz(r2);
-    phs = fmaf(kappa, r2 * rinv, -kappa * g.w);
+    const float2 vx = __fadd2_rn(make_float2(ut.x, ut.x), make_float2(-xs0.x, -xs1.x));
+    const float2 vy = __fadd2_rn(make_float2(ut.y, ut.y), make_float2(-xs0.y, -xs1.y));
+    const float2 vz = __fadd2_rn(make_float2(ut.z, ut.z), make_float2(-xs0.z, -xs1.z));
+    const float2 r2 = __ffma2_rn(vz, vz, __ffma2_rn(vy, vy, __fmul2_rn(vx, vx)));
+    rinv = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+    phs = __ffma2_rn(make_float2(kappa, kappa), __fmul2_rn(r2, rinv), make_float2(-kappa * g.w, -kappa * g.w));
   } else {
-    float ex = xt.x - xs.x, ey = xt.y - xs.y, ez = xt.z - xs.z;
-    float num = fmaf(2.f, g.x * ex + g.y * ey + g.z * ez, ex * ex + ey * ey + ez * ez);
-    float r2 = g.w * g.w + num;
-    rinv = rsqrt_ftz(r2);
-    phs = kappa * num * rcp_ftz(r2 * rinv + g.w);
+    const float2 ex = __fadd2_rn(make_float2(xt.x, xt.x), make_float2(-xs0.x, -xs1.x));
+    const float2 ey = __fadd2_rn(make_float2(xt.y, xt.y), make_float2(-xs0.y, -xs1.y));
+    const float2 ez = __fadd2_rn(make_float2(xt.z, xt.z), make_float2(-xs0.z, -xs1.z));
+    const float2 d1 = __ffma2_rn(make_float2(g.z, g.z), ez,
+                                 __ffma2_rn(make_float2(g.y, g.y), ey, __fmul2_rn(make_float2(g.x, g.x), ex)));
+    const float2 d2 = __ffma2_rn(ez, ez, __ffma2_rn(ey, ey, __fmul2_rn(ex, ex)));
+    const float2 num = __ffma2_rn(make_float2(2.f, 2.f), d1, d2);
+    const float2 r2 = __fadd2_rn(make_float2(g.w * g.w, g.w * g.w), num);
+    rinv = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+    const float2 den = __ffma2_rn(r2, rinv, make_float2(g.w, g.w));
+    phs = __fmul2_rn(__fmul2_rn(make_float2(kappa, kappa), num), make_float2(rcp_ftz(den.x), rcp_ftz(den.y)));
     if (MODE == 2) {
-      float q = rintf(phs * inv2pi);
-      phs = fmaf(-q, c1, phs);
-      phs = fmaf(-q, c2, phs);
+      const float2 qq = __fmul2_rn(phs, make_float2(inv2pi, inv2pi));
+      const float2 qn = make_float2(-rintf(qq.x), -rintf(qq.y));
+      phs = __ffma2_rn(qn, make_float2(c1, c1), phs);
+      phs = __ffma2_rn(qn, make_float2(c2, c2), phs);
     }
   }
-  const float sn = sin_ftz(phs), cs = cos_ftz(phs);
-  const float gr = cs * rinv, gi = sn * rinv;
-  return make_float2(ph.x * gr - ph.y * gi, ph.x * gi + ph.y * gr);
+  const float2 sn = make_float2(sin_ftz(phs.x), sin_ftz(phs.y)), cs = make_float2(cos_ftz(phs.x), cos_ftz(phs.y));
+  const float2 gr = __fmul2_rn(cs, rinv), gi = __fmul2_rn(sn, rinv);
+  re = __ffma2_rn(make_float2(ph.x, ph.x), gr, __fmul2_rn(make_float2(-ph.y, -ph.y), gi));
+  im = __ffma2_rn(make_float2(ph.x, ph.x), gi, __fmul2_rn(make_float2(ph.y, ph.y), gr));
 }
 
 __device__ __forceinline__ void st2(uint8_t *base, uint32_t off, float a, float b) {
@@ -253,12 +267,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
       const float4 xt = sXt[n];
       const float4 ut = make_float4(cg.x + xt.x, cg.y + xt.y, cg.z + xt.z, 0.f);
       float rh[2], rl[2], ih[2], il[2];
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const float2 gv = jb + e < nI ? kernel_entry<MODE>(cg, cph, kappa, xt, ut, cx[e]) : make_float2(0.f, 0.f);
-        tc::split_tf32(gv.x, rh[e], rl[e]);
-        tc::split_tf32(gv.y, ih[e], il[e]);
-      }
+      float2 gre, gim;
+      kernel_entry2<MODE>(cg, cph, kappa, xt, ut, cx[0], cx[1], gre, gim);
+      if (jb >= nI) gre.x = gim.x = 0.f;
+      if (jb + 1 >= nI) gre.y = gim.y = 0.f;
+      tc::split_tf32(gre.x, rh[0], rl[0]);
+      tc::split_tf32(gim.x, ih[0], il[0]);
+      tc::split_tf32(gre.y, rh[1], rl[1]);
+      tc::split_tf32(gim.y, ih[1], il[1]);
       st2(sBh, tc::tile_off(n, kcol), rh[0], rh[1]);
       st2(sBl, tc::tile_off(n, kcol), rl[0], rl[1]);
       st2(sBh, tc::tile_off(NP + n, kcol), ih[0], ih[1]);

@@ -698,19 +698,13 @@ __global__ void k_vec_to_f32(int n, const double2 *__restrict__ x, float2 *__res
   if (i < n) y[i] = make_float2((float)x[i].x, (float)x[i].y);
 }
 
-// FP32 blocks, one right-hand side, streamed with 16-byte loads: one block of 4 warps per target
-// element, warp w taking the source blocks w, w + 4, ... kBIF at a time (their loads in flight
-// together).  A block column of NB rows is read by LPC = NB / 2 lanes, each loading two
-// consecutive rows (one float4), so a warp instruction reads CPR = 32 / LPC consecutive columns
-// (contiguous in the column-major block) and a block takes NB / CPR rounds.  Lane l keeps the
-// rows 2 (l % LPC), 2 (l % LPC) + 1 and the columns l / LPC + CPR k; its x* entries (FP32 copy)
-// come through the cache.  Per source block the partial sums enter running sums with two-sum
-// compensation; the lanes and warps that hold the same rows are combined in a fixed order at
-// the end.
-constexpr int kBIF = 2;
-
+// FP32 blocks, one right-hand side, streamed with 16-byte loads.  A block column of NB rows is
+// read by LPC = NB / 2 lanes, each loading two consecutive rows (one float4), so a warp
+// instruction reads CPR = 32 / LPC consecutive columns (contiguous in the column-major block) and
+// a block takes NB / CPR rounds.  Lane l keeps the rows 2 (l % LPC), 2 (l % LPC) + 1 and the
+// columns l / LPC + CPR k; its x* entries (FP32 copy) come through the cache.
 template <int NB>
-__device__ __forceinline__ void near_v4_block(const float4 *__restrict__ B, const float2 *__restrict__ x, int rp,
+__device__ __forceinline__ void near_block16(const float4 *__restrict__ B, const float2 *__restrict__ x, int rp,
                                               int cg, bool act, float4 *b, float2 *xv) {
   constexpr int LPC = NB / 2, CPR = 32 / LPC, ROUNDS = (NB + CPR - 1) / CPR;
 #pragma unroll
@@ -722,64 +716,10 @@ __device__ __forceinline__ void near_v4_block(const float4 *__restrict__ B, cons
   }
 }
 
-template <int NB>
-__global__ void __launch_bounds__(128) k_near_apply_v4(int nE, const int *__restrict__ ptr,
-                                                       const int *__restrict__ src,
-                                                       const float4 *__restrict__ blocks,
-                                                       const float2 *__restrict__ xs,
-                                                       double2 *__restrict__ ysn) {
-  constexpr int LPC = NB / 2, CPR = 32 / LPC, ROUNDS = (NB + CPR - 1) / CPR;
-  constexpr int F4 = NB * NB / 2;  // float4 per block
-  const int e = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (e >= nE) return;
-  const int rp = lane % LPC, cg = lane / LPC;
-  const bool act = cg < CPR;
-  float h[4] = {0.f, 0.f, 0.f, 0.f}, cmp[4] = {0.f, 0.f, 0.f, 0.f};
-  const int k0 = ptr[e], k1 = ptr[e + 1];
-  for (int k = k0 + warp; k < k1; k += 4 * kBIF) {
-    float4 b[kBIF][ROUNDS];
-    float2 xv[kBIF][ROUNDS];
-#pragma unroll
-    for (int i = 0; i < kBIF; ++i) {
-      const int ki = k + 4 * i;
-      const bool have = ki < k1;
-      const int kk = have ? ki : k;
-      near_v4_block<NB>(blocks + (size_t)kk * F4, xs + (size_t)src[kk] * NB, rp, cg, act && have, b[i], xv[i]);
-    }
-#pragma unroll
-    for (int i = 0; i < kBIF; ++i) {
-      float p[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int t = 0; t < ROUNDS; ++t) {
-        p[0] = fmaf(b[i][t].x, xv[i][t].x, fmaf(-b[i][t].y, xv[i][t].y, p[0]));
-        p[1] = fmaf(b[i][t].x, xv[i][t].y, fmaf(b[i][t].y, xv[i][t].x, p[1]));
-        p[2] = fmaf(b[i][t].z, xv[i][t].x, fmaf(-b[i][t].w, xv[i][t].y, p[2]));
-        p[3] = fmaf(b[i][t].z, xv[i][t].y, fmaf(b[i][t].w, xv[i][t].x, p[3]));
-      }
-      if (k + 4 * i < k1)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) two_sum(h[q], cmp[q], p[q]);
-    }
-  }
-  __shared__ float red[4][32][4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) red[warp][lane][q] = h[q] + cmp[q];
-  __syncthreads();
-  if (warp == 0 && lane < LPC) {
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int w = 0; w < 4; ++w)
-      for (int g = 0; g < CPR; ++g)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) s[q] += (double)red[w][g * LPC + lane][q];
-    ysn[(size_t)e * NB + 2 * lane] = make_double2(s[0], s[1]);
-    ysn[(size_t)e * NB + 2 * lane + 1] = make_double2(s[2], s[3]);
-  }
-}
-
 // One warp per target element (a contiguous range of elements per warp, the same count for
-// every warp): the warp reads the element's source blocks BIF at a time with 16-byte loads as
-// k_near_apply_v4 does, adds each block's FP32 partial sums by two-sum, and combines its column
-// groups with shuffles in a fixed order (FP64 sum).  No shared memory and no block barrier, so a
+// every warp): the warp reads the element's source blocks BIF at a time (their loads in flight
+// together), adds each block's FP32 partial sums to running sums by two-sum (compensated), and
+// combines its column groups with shuffles in a fixed order (FP64 sum).  No shared memory and no block barrier, so a
 // warp goes on to its next element as soon as it has written the last.
 template <int NB, int BIF>
 __global__ void __launch_bounds__(128) k_near_apply_w(int nE, int per, const int *__restrict__ ptr,
@@ -802,7 +742,7 @@ __global__ void __launch_bounds__(128) k_near_apply_w(int nE, int per, const int
       for (int i = 0; i < BIF; ++i) {
         const bool have = k + i < k1;
         const int kk = have ? k + i : k;
-        near_v4_block<NB>(blocks + (size_t)kk * F4, xs + (size_t)src[kk] * NB, rp, cg, act && have, b[i], xv[i]);
+        near_block16<NB>(blocks + (size_t)kk * F4, xs + (size_t)src[kk] * NB, rp, cg, act && have, b[i], xv[i]);
       }
 #pragma unroll
       for (int i = 0; i < BIF; ++i) {
@@ -993,9 +933,13 @@ efie_status dev_near_apply(Ctx *c, const double2 *xs, double2 *ysn, cudaStream_t
       k_vec_to_f32<<<(c->nsup + 255) / 256, 256, 0, st>>>(c->nsup, xs, c->d_xsf);
       ++c->launches;
       const float2 *xf = c->d_xsf;
-      if (c->nb == 8) k_near_apply_v4<8><<<grid, 128, 0, st>>>(c->nE, c->d_near_ptr, c->d_near_src, B, xf, ysn);
-      else if (c->nb == 18) k_near_apply_v4<18><<<grid, 128, 0, st>>>(c->nE, c->d_near_ptr, c->d_near_src, B, xf, ysn);
-      else k_near_apply_v4<32><<<grid, 128, 0, st>>>(c->nE, c->d_near_ptr, c->d_near_src, B, xf, ysn);
+      // one warp per element, the same number of elements per warp: about 20 warps per SM
+      const int per = (c->nE + c->nsm * 20 - 1) / (c->nsm * 20);
+      const int nw = (c->nE + per - 1) / per;
+      const unsigned gw = (unsigned)((nw + 3) / 4);
+      if (c->nb == 8) k_near_apply_w<8, 2><<<gw, 128, 0, st>>>(c->nE, per, c->d_near_ptr, c->d_near_src, B, xf, ysn);
+      else if (c->nb == 18) k_near_apply_w<18, 2><<<gw, 128, 0, st>>>(c->nE, per, c->d_near_ptr, c->d_near_src, B, xf, ysn);
+      else k_near_apply_w<32, 2><<<gw, 128, 0, st>>>(c->nE, per, c->d_near_ptr, c->d_near_src, B, xf, ysn);
       ++c->launches;
       EFIE_CUDA(cudaGetLastError());
       return EFIE_OK;

@@ -98,10 +98,10 @@ efie_status dev_rhs(Ctx *c, const double *dir, const double *pol, double2 *g) {
 __global__ void k_ff_partial(const PatchDesc *patches, const double *knots, const double4 *cpw, int n, int p, int g,
                              const double *gx, const double *gw, double kappa, int nE, int ndir, const double *dirs,
                              const double2 *__restrict__ xs, double2 *part) {
-  extern __shared__ double sff[];
+  extern __shared__ double2 sff[];
   const int e = blockIdx.x, G2 = g * g, P1 = p + 1;
-  double *sX = sff;           // [G2][3]
-  double2 *sV = reinterpret_cast<double2 *>(sff + 3 * G2);  // [G2][3]
+  double2 *sV = sff;                                        // [G2][3] (16-byte aligned)
+  double *sX = reinterpret_cast<double *>(sff + 3 * G2);    // [G2][3]
   int j, i1, i2;
   elem_locate(e, n, j, i1, i2);
   const double h = 1.0 / n;
