@@ -8,12 +8,15 @@
 namespace efie {
 
 constexpr int kDotThreads = 256;
-constexpr int kRowsPerThread = 4;
+constexpr int kRowsPerThread = 8;
 constexpr int kChunk = kDotThreads * kRowsPerThread;  // vector entries per partial dot product
 constexpr int kVecPerBlock = 8;
+static_assert(kVecPerBlock == kDotThreads / 32, "one warp reduces one vector of a dot-product block");
 
 // Partial dot products of one chunk: part[i * nchunk + chunk] = sum_{t in chunk} conj(V_i[t]) w[t]
-// for i = i0 .. i0 + 7 (i < nvec).  Called by all kDotThreads threads of a block.
+// for i = i0 .. i0 + 7 (i < nvec).  Each thread sums its kRowsPerThread entries for the 8
+// vectors; warp v then adds the 256 thread sums of vector v (8 per lane, then a shuffle tree), in
+// a fixed order.  Called by all kDotThreads threads of a block.
 __device__ __forceinline__ void dot_partial_chunk(int N, int nvec, int i0, int chunk, const double2 *__restrict__ V,
                                                   size_t ldv, const double2 *__restrict__ w,
                                                   double2 *__restrict__ part, int nchunk) {
@@ -35,26 +38,23 @@ __device__ __forceinline__ void dot_partial_chunk(int N, int nvec, int i0, int c
       }
     }
   }
-  __shared__ double2 red[kDotThreads / 32][kVecPerBlock];
-  int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  __shared__ double2 red[kVecPerBlock][kDotThreads + 1];
 #pragma unroll
-  for (int v = 0; v < kVecPerBlock; ++v) {
-    double x = acc[v].x, y = acc[v].y;
+  for (int v = 0; v < kVecPerBlock; ++v) red[v][threadIdx.x] = acc[v];
+  __syncthreads();
+  {
+    const int v = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double x = 0.0, y = 0.0;
+#pragma unroll
+    for (int k = 0; k < kDotThreads / 32; ++k) {
+      x += red[v][lane + 32 * k].x;
+      y += red[v][lane + 32 * k].y;
+    }
     for (int o = 16; o > 0; o >>= 1) {
       x += __shfl_down_sync(0xffffffffu, x, o);
       y += __shfl_down_sync(0xffffffffu, y, o);
     }
-    if (lane == 0) red[wp][v] = make_double2(x, y);
-  }
-  __syncthreads();
-  if (threadIdx.x < kVecPerBlock) {
-    int v = threadIdx.x, i = i0 + v;
-    double2 s = make_double2(0.0, 0.0);
-    for (int k = 0; k < kDotThreads / 32; ++k) {
-      s.x += red[k][v].x;
-      s.y += red[k][v].y;
-    }
-    if (i < nvec) part[(size_t)i * nchunk + chunk] = s;
+    if (lane == 0 && i0 + v < nvec) part[(size_t)(i0 + v) * nchunk + chunk] = make_double2(x, y);
   }
   __syncthreads();  // red is reused by the next call of the block
 }
