@@ -12,7 +12,8 @@
 namespace efie {
 
 // Device memory of one scattering request, estimated from the discretisation before anything
-// is built: near-field blocks (about 30 neighbours per element, FP64 plus an FP32 copy in the
+// is built: near-field blocks (at most 40 neighbours per element: the sphere workloads have 21 to
+// 30, the tori of the serving mix up to 36; FP64 plus an FP32 copy in the
 // mixed form), the Krylov bases, cluster data and work vectors, and the far-field scratch of
 // ndir directions (3 complex values per element and direction, plus the output).  In the
 // mixed form the directions of a request are solved in lockstep (up to 64 at a time), each
@@ -28,7 +29,7 @@ inline size_t request_footprint(int np, int level_m, int p, int q, int gmres_res
   const size_t n = size_t(1) << level_m, nE = size_t(np) * n * n;
   const size_t p1 = p + 1, nb = 2 * p1 * p1, nI = size_t(q + 1) * (q + 1);
   const size_t ndof = 2 * size_t(np) * (n + p - 1) * (n + p - 1);
-  const size_t near = (leaf_dense ? 160 : 30) * nE * (nb * nb * (mixed ? 24 : 16) + 8);
+  const size_t near = (leaf_dense ? 160 : 40) * nE * (nb * nb * (mixed ? 24 : 16) + 8);
   const size_t kr = (size_t)std::min(gmres_restart, gmres_maxit) + 1;
   const size_t lockstep = (mixed && nrhs > 1) ? (size_t)std::min(nrhs, 64) : 1;
   const size_t krylov = lockstep * (kr * ndof * 16 + kr * kr * 16);

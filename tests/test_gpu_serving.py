@@ -15,6 +15,10 @@ REQUESTS = [
     (G.sphere, dict(p=2, level_m=2, kappa=3.0, q=5, eta=1.6, precision=1)),
     (G.sphere, dict(p=1, level_m=3, kappa=2.0, q=4, eta=1.6, precision=1)),
     (G.torus, dict(p=1, level_m=2, kappa=1.0, q=4, eta=1.6)),
+    # tori at p = 3 have the most near-field blocks per element of the serving mix (the
+    # admission estimate must still bound their device peak)
+    (G.torus, dict(p=3, level_m=2, kappa=11.7, q=6, eta=1.6, precision=1)),
+    (G.torus, dict(p=3, level_m=3, kappa=8.0, q=6, eta=1.6, precision=1)),
 ]
 
 
