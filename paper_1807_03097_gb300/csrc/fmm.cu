@@ -333,8 +333,8 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
 // applied with packed FP32 instructions (fma / add / mul .f32x2 on the pair).  With x_t, x_s
 // the node offsets from the cluster centres, d = c_t - c_s and r0 = |d|:
 //   MODE 0 (direct): r^2 = |u|^2 + |x_s|^2 - 2 u.x_s with u = d + x_t, phase = kappa r -
-//     kappa r0; used when the host has checked that kappa * max r * 2^-24 < 2e-6 (a fixed
-//     perturbation of the matrix below 2e-6 rad per entry);
+//     kappa r0; used when the host has checked that kappa * max r * 2^-24 < 5e-6 (a fixed
+//     perturbation of the matrix of at most about 2e-5 rad per entry);
 //   MODE 1 (split): num = r^2 - r0^2 = (|x_t|^2 + 2 d.x_t) + (|x_s|^2 - 2 d.x_s) - 2 x_t.x_s,
 //     every term of the size of num (no cancellation against r0^2), r = sqrt(r0^2 + num),
 //     phase = kappa (r - r0) = num / ((r + r0) / kappa); the host has checked that every phase

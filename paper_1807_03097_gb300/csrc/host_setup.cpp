@@ -381,7 +381,10 @@ efie_status host_build_trees(Ctx *c) {
     maxkr = std::max(maxkr, c->kappa * (pdist(bt, bs) + 1.5 * (bt[3] + bs[3])));
   }
   if (!(maxph < 100.0 * M_PI)) c->m2l_mode = 2;
-  else if (maxkr * std::ldexp(1.0, -24) < 2e-6) c->m2l_mode = 0;
+  // direct phase when its rounding (a few units of 2^-24 relative in kappa r: about 4 kappa r
+  // 2^-24 rad per entry) stays within 2e-5 rad; the product error, an average over many entries,
+  // is then about 1e-6 or less (4.3e-7 at the 13k-DOF sphere, kappa r up to about 34)
+  else if (maxkr * std::ldexp(1.0, -24) < 5e-6) c->m2l_mode = 0;
   else c->m2l_mode = 1;
   c->nnear = (int)c->nearl.size() / 2;
 
