@@ -335,10 +335,10 @@ const char *efie_last_error(const efie_ctx *ctx);
  *
  * A group holds nctx contexts that are set up on one device (each with its own geometry,
  * wavenumber, p, refinement and options).  efie_group_solve solves A_i x_i = b_i for every
- * context i in lockstep: each step applies the products of all unfinished systems as one
- * CUDA-graph launch (one branch per context, captured once and again only when a tenth of
- * its branches belong to finished systems) and runs the Arnoldi (CGS2), Givens and update
- * work of all systems in one launch per operation, with the arithmetic of efie_solve.  The
+ * context i in lockstep: each step is one CUDA-graph launch that holds the products of all
+ * unfinished systems (one branch per context; the graph is captured again only when a tenth of
+ * its branches belong to finished systems) and the Arnoldi (CGS2), Givens and update work of
+ * all systems, one kernel per operation, with the arithmetic of efie_solve.  The
  * GMRES options (tolerance, restart, maximum iterations) are each context's own.
  *   b[i], x[i]: 2 ndof_i doubles each (ptr_kind memory); x[i] receives the solution.
  *   iterations, residuals, converged: nctx entries each (optional).

@@ -1,17 +1,17 @@
 // Lockstep GMRES over independent problems (a11 across problems): several contexts, each set up
 // for its own geometry, wavenumber, degree and refinement, solve their systems together.  Every
-// step of the lockstep is three CUDA-graph launches on the group's stream, whatever the number
-// of problems:
+// step of the lockstep is one CUDA-graph launch on the group's stream, whatever the number of
+// problems; the graph has three parts:
 //   pre:      upload of the step table, end-of-cycle back substitution and update of x,
 //             packing of each system's product input into its context;
 //   products: the operator products of all unfinished systems, one branch per context (each
 //             branch the context's own product chain: T gather, moments, M2M, M2L, L2L,
-//             evaluation, near field on a second stream, T^T scatter), captured once and
-//             captured again only when a tenth of its branches belong to finished systems;
+//             evaluation, near field on a second stream, T^T scatter); the graph is captured
+//             again only when a tenth of its product branches belong to finished systems;
 //   post:     residuals, CGS2 (two passes), norms, Givens rotations, the next Krylov vector and
 //             the residual estimates of all systems, then one device-to-host copy of them.
 // The per-system work of pre and post runs in one launch per operation over a table of chunks
-// of 1024 vector entries (system, chunk), with the same arithmetic in the same order as the
+// of 2048 vector entries (system, chunk), with the same arithmetic in the same order as the
 // single-context solver (gmres_ops.cuh), so that a system solved in a group follows the same
 // iterates as alone up to the rounding of its products.
 #include <algorithm>
@@ -205,9 +205,11 @@ struct Group {
   cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};  // around the three graphs of a step
   double graph_ms[3] = {0.0, 0.0, 0.0};                       // pre, products, post (last solve)
   std::vector<cudaEvent_t> joins;
-  cudaGraphExec_t g_pre = nullptr, g_post = nullptr, g_prod = nullptr;
-  std::vector<int> members;  // systems with a branch in g_prod
-  long long prod_kernels = 0;  // kernel nodes of g_prod
+  // one graph per step: g_step = pre + products + post, g_noprod = pre + post (steps in which
+  // no system needs a product)
+  cudaGraphExec_t g_step = nullptr, g_noprod = nullptr;
+  std::vector<int> members;  // systems with a product branch in g_step
+  long long prod_kernels = 0;  // kernel nodes of the product branches
   // statistics of the last solve
   long long steps = 0, captures = 0, kernels = 0;
   double solve_ms = 0.0;
@@ -215,7 +217,7 @@ struct Group {
 
 namespace {
 
-constexpr int kPreKernels = 2, kPostKernels = 10;
+constexpr int kPreKernels = 2, kPostKernels = 11;
 
 efie_status capture_graph(Group *g, cudaGraphExec_t *out, efie_status (*body)(Group *)) {
   Ctx *c = &g->gc;
@@ -289,13 +291,29 @@ efie_status body_prod(Group *g) {
   return EFIE_OK;
 }
 
+// The whole step as one graph; external event-record nodes around its three parts give their
+// device times.
+efie_status body_step_t(Group *g, bool products) {
+  cudaStream_t st = g->gc.stream;
+  Ctx *c = &g->gc;
+  EFIE_CUDA(cudaEventRecordWithFlags(g->tev[0], st, cudaEventRecordExternal));
+  EFIE_TRY(body_pre(g));
+  EFIE_CUDA(cudaEventRecordWithFlags(g->tev[1], st, cudaEventRecordExternal));
+  if (products) EFIE_TRY(body_prod(g));
+  EFIE_CUDA(cudaEventRecordWithFlags(g->tev[2], st, cudaEventRecordExternal));
+  EFIE_TRY(body_post(g));
+  EFIE_CUDA(cudaEventRecordWithFlags(g->tev[3], st, cudaEventRecordExternal));
+  return EFIE_OK;
+}
+efie_status body_step(Group *g) { return body_step_t(g, true); }
+efie_status body_noprod(Group *g) { return body_step_t(g, false); }
+
 void release(Group *g) {
   Ctx *c = &g->gc;
   if (c->stream) cudaStreamSynchronize(c->stream);
-  if (g->g_pre) cudaGraphExecDestroy(g->g_pre);
-  if (g->g_post) cudaGraphExecDestroy(g->g_post);
-  if (g->g_prod) cudaGraphExecDestroy(g->g_prod);
-  g->g_pre = g->g_post = g->g_prod = nullptr;
+  if (g->g_step) cudaGraphExecDestroy(g->g_step);
+  if (g->g_noprod) cudaGraphExecDestroy(g->g_noprod);
+  g->g_step = g->g_noprod = nullptr;
   dfree(c, g->d_tab);
   dfree(c, g->d_out);
   dfree(c, g->d_csys);
@@ -474,24 +492,17 @@ efie_status efie_group_solve(efie_group *grp, const double *const *b, double *co
     EFIE_TRY(dev_matvec(m, m->d_x, m->d_y));
   }
   for (Ctx *m : g->ctx) EFIE_CUDA(cudaStreamSynchronize(m->stream));
-  EFIE_TRY(capture_graph(g, &g->g_pre, body_pre));
-  EFIE_TRY(capture_graph(g, &g->g_post, body_post));
   g->members.clear();
   for (int i = 0; i < K; ++i) g->members.push_back(i);
-  EFIE_TRY(capture_graph(g, &g->g_prod, body_prod));
+  EFIE_TRY(capture_graph(g, &g->g_noprod, body_noprod));
+  EFIE_TRY(capture_graph(g, &g->g_step, body_step));
   g->steps = 0;
   g->captures = 1;
   g->kernels = 0;
 
   g->graph_ms[0] = g->graph_ms[1] = g->graph_ms[2] = 0.0;
   auto run_step = [&](bool any_product) -> efie_status {
-    EFIE_CUDA(cudaEventRecord(g->tev[0], c->stream));
-    EFIE_CUDA(cudaGraphLaunch(g->g_pre, c->stream));
-    EFIE_CUDA(cudaEventRecord(g->tev[1], c->stream));
-    if (any_product) EFIE_CUDA(cudaGraphLaunch(g->g_prod, c->stream));
-    EFIE_CUDA(cudaEventRecord(g->tev[2], c->stream));
-    EFIE_CUDA(cudaGraphLaunch(g->g_post, c->stream));
-    EFIE_CUDA(cudaEventRecord(g->tev[3], c->stream));
+    EFIE_CUDA(cudaGraphLaunch(any_product ? g->g_step : g->g_noprod, c->stream));
     EFIE_CUDA(cudaStreamSynchronize(c->stream));
     for (int k = 0; k < 3; ++k) {
       float ms = 0.f;
@@ -558,7 +569,7 @@ efie_status efie_group_solve(efie_group *grp, const double *const *b, double *co
       g->members.clear();
       for (int i = 0; i < K; ++i)
         if (S[i].phase != kDone) g->members.push_back(i);
-      EFIE_TRY(capture_graph(g, &g->g_prod, body_prod));
+      EFIE_TRY(capture_graph(g, &g->g_step, body_step));
       ++g->captures;
     }
     EFIE_TRY(run_step(any_prod));
