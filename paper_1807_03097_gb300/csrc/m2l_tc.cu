@@ -351,269 +351,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
   if (warp == 0) tc::tmem_dealloc(tbase, L::kCols);
 }
 
-// ------------------------------------------------------------------------------------------
-// The same contraction with the fields on the MMA's N dimension, for 128 fields per block
-// (32 right-hand sides): the coupling tile, evaluated once per block pair, then serves twice as
-// many fields as in k_m2l_tc.  In the real form of the complex product
-//   D[n][c] = sum_k A[n][k] B[c][k],   A[n][2 s] = Re G(n, s),  A[n][2 s + 1] = Im G(n, s)
-//   B[2 f][2 s] = Re S(s, f),  B[2 f][2 s + 1] = -Im S(s, f),
-//   B[2 f + 1][2 s] = Im S(s, f),  B[2 f + 1][2 s + 1] = Re S(s, f),
-// column 2 f of D is Re C(n, f) and column 2 f + 1 is Im C(n, f): the target nodes are the 128
-// MMA rows (M = 128), the fields the N = 2 FB columns, and a stage holds 16 source nodes (K = 32).
-// Splits, accumulator groups, running sums in tensor memory, warp roles and bounded waits are
-// those of k_m2l_tc.  Staging map of a stage: lane l of warp w evaluates the kernel for the
-// source pair j = l / 8 + 4 (w % 2) (nodes 2 j, 2 j + 1) and the target rows n = l % 8 +
-// 8 (w / 2) + 64 i (i < 2), each one 16-byte chunk (Re G0, Im G0, Re G1, Im G1) of row n; and it
-// stages the fields f = l % 4 + 4 w + 64 i (i < FB / 64) of the source pair l / 4.
-constexpr int kTcnNodes = 16;  // source nodes per stage
-
-template <int FB>
-struct TcnLayout {
-  static constexpr uint32_t kA = 128 * 128;                 // one [128 x 32] FP32 tile
-  static constexpr uint32_t kB = 2 * FB * 128;              // one [2 FB x 32] FP32 tile
-  static constexpr uint32_t kStage = 2 * kA + 2 * kB;       // A hi, A lo, B hi, B lo
-  static constexpr uint32_t kNodes = 2 * kStage;            // target node positions, float4 [128]
-  static constexpr uint32_t kBars = kNodes + 16 * 128;
-  static constexpr uint32_t kBytes = kBars + 64;
-  static constexpr uint32_t kN = 2 * FB;                    // MMA N
-  static constexpr uint32_t kCols = 2 * kN;                 // D [0, N), S [N, 2 N)
-  static_assert(128 * (kN + 1) * 4 <= 2 * kStage, "epilogue staging must fit in the stages");
-  static_assert(kCols == 256 || kCols == 512, "tensor-memory allocation is a power of two");
-};
-
-template <int FB, int MODE>
-__global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tcn(
-    const int *__restrict__ targets, const int *__restrict__ fptr, const int *__restrict__ fsrc,
-    const float4 *__restrict__ pgeo, const float2 *__restrict__ pph, int nI, float kappa,
-    const float4 *__restrict__ nodeX4, int F, int ld, const float2 *__restrict__ src, float2 *__restrict__ acc,
-    int *__restrict__ err) {
-  using L = TcnLayout<FB>;
-  constexpr int NFI = FB / 64;  // field rows per thread
-  extern __shared__ __align__(1024) uint8_t smem[];
-  float4 *sXt = reinterpret_cast<float4 *>(smem + L::kNodes);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::kBars);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 6);
-  const uint32_t b_full = tc::smem_u32(&bars[0]), b_empty = tc::smem_u32(&bars[2]);
-  const uint32_t b_tfull = tc::smem_u32(&bars[4]), b_tempty = tc::smem_u32(&bars[5]);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ja = (lane >> 3) + 4 * (warp & 1);   // source pair of the kernel evaluations
-  const int na = (lane & 7) + 8 * (warp >> 1);   // target rows na + 64 i
-  const int jb = lane >> 2;                      // source pair of the fields
-  const int fb = (lane & 3) + 4 * warp;          // fields fb + 64 i
-  const int t = targets[blockIdx.x];
-  const int f0 = blockIdx.y * FB;
-  const int k0 = fptr[t], nsrc = fptr[t + 1] - k0;
-  const int nchunk = (nI + kTcnNodes - 1) / kTcnNodes, T = nsrc * nchunk;
-
-  if (tid == 0) {
-    for (int i = 0; i < 2; ++i) {
-      tc::mbar_init(b_full + 8 * i, kTcProducers);
-      tc::mbar_init(b_empty + 8 * i, 1);
-    }
-    tc::mbar_init(b_tfull, 1);
-    tc::mbar_init(b_tempty, kTcProducers);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  for (int i = tid; i < 128; i += kTcThreads) sXt[i] = i < nI ? nodeX4[(size_t)t * nI + i] : make_float4(0, 0, 0, 0);
-  // A rows of target nodes n >= nI (both stages, hi and lo) stay zero
-  for (int i = tid; i < 2 * 2 * (128 - nI) * 8; i += kTcThreads) {
-    const int kg = i & 7, n = nI + (i >> 3) % (128 - nI), tl = (i >> 3) / (128 - nI);  // tl: stage (bit 1), lo (bit 0)
-    *reinterpret_cast<float4 *>(smem + (tl >> 1) * L::kStage + (tl & 1) * L::kA + tc::tile_off(n, 4 * kg)) =
-        make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), L::kCols);
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t tbase = *tslot;
-  const uint32_t idesc = tc::idesc_tf32(128, L::kN);
-  const int q = warp & 3, r4 = warp >> 2;  // lane quadrant and column quarter of the drain
-  const uint32_t tq = tbase + ((uint32_t)(32 * q) << 16);
-
-  if (warp < kTcWarps) {
-    // S += D for group g of block pairs (S = D for the first), then release D to the MMAs; this
-    // thread covers the column blocks b = r4 + 4 i (8 columns each) of D and S
-    auto drain = [&](int g) {
-      constexpr int NBT = L::kN / 32;  // column blocks per thread
-      constexpr int NH = NBT >= 4 ? 4 : NBT;
-      if (!tc::mbar_wait(b_tfull, g & 1, kTcWaitCycles)) atomicOr(err, 1);
-      tc::fence_after_sync();
-#pragma unroll
-      for (int h0 = 0; h0 < NBT; h0 += NH) {
-        uint32_t d[NH][8], sv[NH][8];
-#pragma unroll
-        for (int i = 0; i < NH; ++i) {
-          const uint32_t cd = tq + 8 * (r4 + 4 * (h0 + i));
-          tc::tmem_ld8_async(cd, d[i]);
-          if (g > 0) tc::tmem_ld8_async(cd + L::kN, sv[i]);
-        }
-        tc::tmem_wait_ld();
-#pragma unroll
-        for (int i = 0; i < NH; ++i) {
-          tc::touch8(d[i]);
-          if (g > 0) {
-            tc::touch8(sv[i]);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) d[i][k] = __float_as_uint(__uint_as_float(d[i][k]) + __uint_as_float(sv[i][k]));
-          }
-          tc::tmem_st8_async(tq + 8 * (r4 + 4 * (h0 + i)) + L::kN, d[i]);
-        }
-      }
-      tc::tmem_wait_st();
-      tc::fence_before_sync();
-      tc::mbar_arrive(b_tempty);
-    };
-
-    float4 cx[2], nx[2];
-    float2 cs[NFI][2], ns[NFI][2];
-    float4 cg, ng = make_float4(0, 0, 0, 1);
-    float2 cph, nph = make_float2(0, 0);
-    int s_next = nsrc > 0 ? ldg_pin(fsrc + k0) : 0;
-    int lp = 0, lc = 0;  // (pair, chunk) that load_stage fetches next
-    auto load_stage = [&]() {
-      if (lp >= nsrc) return;
-      const int p2 = lp, c2 = lc;
-      if (++lc == nchunk) {
-        lc = 0;
-        ++lp;
-      }
-      const int s2 = s_next;
-      if (lp < nsrc && lc == 0) s_next = ldg_pin(fsrc + k0 + lp);
-      ng = ldg_pin(pgeo + k0 + p2);
-      nph = ldg_pin(pph + k0 + p2);
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int j = kTcnNodes * c2 + 2 * ja + e;
-        nx[e] = j < nI ? ldg_pin(nodeX4 + (size_t)s2 * nI + j) : make_float4(0, 0, 0, 0);
-        const int jf = kTcnNodes * c2 + 2 * jb + e;
-#pragma unroll
-        for (int i = 0; i < NFI; ++i) {
-          const int f = fb + 64 * i;
-          ns[i][e] = (jf < nI && f0 + f < F) ? ldg_pin(src + ((size_t)s2 * nI + jf) * ld + f0 + f) : make_float2(0.f, 0.f);
-        }
-      }
-    };
-    load_stage();
-    for (int it = 0, p = 0, c = 0; it < T; ++it, c = (c + 1 == nchunk) ? 0 : c + 1, p += (c == 0)) {
-      const int st = it & 1;
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        cx[e] = nx[e];
-#pragma unroll
-        for (int i = 0; i < NFI; ++i) cs[i][e] = ns[i][e];
-      }
-      cg = ng;
-      cph = nph;
-      load_stage();
-      if (it >= 2 && !tc::mbar_wait(b_empty + 8 * st, ((it >> 1) & 1) ^ 1, kTcWaitCycles)) atomicOr(err, 2);
-      uint8_t *sAh = smem + st * L::kStage, *sAl = sAh + L::kA;
-      uint8_t *sBh = sAh + 2 * L::kA, *sBl = sBh + L::kB;
-      // A: kernel entries of target rows na + 64 i for the source pair ja (one 16-byte chunk)
-      const int j0 = kTcnNodes * c + 2 * ja;
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int n = na + 64 * i;
-        if (n >= nI) continue;  // padding rows, zero since the start
-        const float4 xt = sXt[n];
-        const float4 ut = make_float4(cg.x + xt.x, cg.y + xt.y, cg.z + xt.z, 0.f);
-        float2 gre, gim;
-        kernel_entry2<MODE>(cg, cph, kappa, xt, ut, cx[0], cx[1], gre, gim);
-        if (j0 >= nI) gre.x = gim.x = 0.f;
-        if (j0 + 1 >= nI) gre.y = gim.y = 0.f;
-        float4 h, l;
-        tc::split_tf32(gre.x, h.x, l.x);
-        tc::split_tf32(gim.x, h.y, l.y);
-        tc::split_tf32(gre.y, h.z, l.z);
-        tc::split_tf32(gim.y, h.w, l.w);
-        *reinterpret_cast<float4 *>(sAh + tc::tile_off(n, 4 * ja)) = h;
-        *reinterpret_cast<float4 *>(sAl + tc::tile_off(n, 4 * ja)) = l;
-      }
-      // B: the real form of the fields fb + 64 i of the source pair jb
-#pragma unroll
-      for (int i = 0; i < NFI; ++i) {
-        const int f = fb + 64 * i;
-        const float2 a = cs[i][0], b = cs[i][1];
-        float4 h, l;
-        tc::split_tf32(a.x, h.x, l.x);
-        tc::split_tf32(-a.y, h.y, l.y);
-        tc::split_tf32(b.x, h.z, l.z);
-        tc::split_tf32(-b.y, h.w, l.w);
-        *reinterpret_cast<float4 *>(sBh + tc::tile_off(2 * f, 4 * jb)) = h;
-        *reinterpret_cast<float4 *>(sBl + tc::tile_off(2 * f, 4 * jb)) = l;
-        // the row of Im C: (Im S, Re S) = (-(-Im S), Re S), the same split parts rearranged
-        *reinterpret_cast<float4 *>(sBh + tc::tile_off(2 * f + 1, 4 * jb)) = make_float4(-h.y, h.x, -h.w, h.z);
-        *reinterpret_cast<float4 *>(sBl + tc::tile_off(2 * f + 1, 4 * jb)) = make_float4(-l.y, l.x, -l.w, l.z);
-      }
-      tc::fence_proxy_async();
-      tc::mbar_arrive(b_full + 8 * st);
-      // the previous group's MMAs are done by now: fold it into the running sums
-      const bool gstart = c == 0 && p % kTcGroup == 0;
-      if (gstart && p >= 1) drain(p / kTcGroup - 1);
-    }
-    if (nsrc >= 1) drain((nsrc - 1) / kTcGroup);
-  } else if (lane == 0) {
-    // ------------------------------------------------------------------- MMA issue
-    const uint32_t a0 = tc::smem_u32(smem);
-    const uint64_t dah0 = tc::smem_desc(a0), dal0 = tc::smem_desc(a0 + L::kA);
-    const uint64_t dbh0 = tc::smem_desc(a0 + 2 * L::kA), dbl0 = tc::smem_desc(a0 + 2 * L::kA + L::kB);
-    for (int it = 0, p = 0, c = 0; it < T; ++it, c = (c + 1 == nchunk) ? 0 : c + 1, p += (c == 0)) {
-      const int st = it & 1;
-      const bool gstart = c == 0 && p % kTcGroup == 0;
-      if (gstart && p >= 1 && !tc::mbar_wait(b_tempty, (p / kTcGroup - 1) & 1, kTcWaitCycles)) atomicOr(err, 4);
-      if (!tc::mbar_wait(b_full + 8 * st, (it >> 1) & 1, kTcWaitCycles)) atomicOr(err, 8);
-      tc::fence_after_sync();
-      const int ksteps = min(4, (2 * (nI - kTcnNodes * c) + 7) / 8);
-      for (int ks = 0; ks < ksteps; ++ks) {
-        const uint64_t o = (uint64_t)(st * (L::kStage >> 4) + 16 * ks);
-        tc::mma_tf32(tbase, dah0 + o, dbh0 + o, idesc, (gstart && ks == 0) ? 0u : 1u);
-        tc::mma_tf32(tbase, dah0 + o, dbl0 + o, idesc, 1u);
-        tc::mma_tf32(tbase, dal0 + o, dbh0 + o, idesc, 1u);
-      }
-      tc::mma_commit(b_empty + 8 * st);
-      if (c == nchunk - 1 && (p % kTcGroup == kTcGroup - 1 || p == nsrc - 1)) tc::mma_commit(b_tfull);
-    }
-  }
-  __syncwarp();
-  // ------------------------------------------------------------------------- epilogue
-  // every MMA is complete and drained: stage the sums as [128][N + 1] in the stage memory
-  __syncthreads();
-  float *sS = reinterpret_cast<float *>(smem);
-  constexpr int LDS = L::kN + 1;
-  const int m = 32 * q + lane;
-  if (warp >= kTcWarps) {
-    // the MMA-issue warp takes no part in staging the sums
-  } else if (nsrc >= 1) {
-    tc::fence_after_sync();
-#pragma unroll 1
-    for (int b = r4; b < (int)L::kN / 8; b += 4) {
-      float v[8];
-      tc::tmem_ld8(tq + L::kN + 8 * b, v);
-#pragma unroll
-      for (int i = 0; i < 8; ++i) sS[m * LDS + 8 * b + i] = v[i];
-    }
-  } else {
-    for (int b = r4; b < (int)L::kN / 8; b += 4)
-      for (int i = 0; i < 8; ++i) sS[m * LDS + 8 * b + i] = 0.f;
-  }
-  __syncthreads();
-  for (int idx = tid; idx < nI * FB; idx += kTcThreads) {
-    const int f = idx % FB, i = idx / FB;
-    if (f0 + f >= F) continue;
-    acc[((size_t)t * nI + i) * ld + f0 + f] = make_float2(sS[i * LDS + 2 * f], sS[i * LDS + 2 * f + 1]);
-  }
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  if (warp == 0) tc::tmem_dealloc(tbase, L::kCols);
-}
-
-template <int FB, int MODE>
-static efie_status tcn_attr() {
-  cudaError_t e = cudaFuncSetAttribute(k_m2l_tcn<FB, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)TcnLayout<FB>::kBytes);
-  return e == cudaSuccess ? EFIE_OK : EFIE_ECUDA;
-}
-
 template <int NP, int MODE>
 static efie_status tc_attr() {
   cudaError_t e = cudaFuncSetAttribute(k_m2l_tc<NP, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -635,9 +372,6 @@ efie_status m2l_tc_prepare(Ctx *c) {
   EFIE_TRY(tc_attrs<64>());
   EFIE_TRY(tc_attrs<96>());
   EFIE_TRY(tc_attrs<128>());
-  EFIE_TRY((tcn_attr<128, 0>()));
-  EFIE_TRY((tcn_attr<128, 1>()));
-  EFIE_TRY((tcn_attr<128, 2>()));
   if (!c->d_tc_err) {
     EFIE_TRY(dalloc(c, &c->d_tc_err, 1));
     EFIE_CUDA(cudaMemsetAsync(c->d_tc_err, 0, sizeof(int), c->stream));
@@ -658,26 +392,10 @@ static void launch_np(Ctx *c, cudaStream_t st, dim3 grid, int F, int ld, const f
 #undef EFIE_TC
 }
 
-// acc[t][i][f] for the targets of the M2L, f < F = 4 R, row stride ld (float2 entries).  From
-// 128 fields (32 right-hand sides) on, the fields go on the MMA's N dimension, 128 per block.
+// acc[t][i][f] for the targets of the M2L, f < F = 4 R, row stride ld (float2 entries)
 efie_status launch_m2l_tc(Ctx *c, cudaStream_t st, int F, int ld, const float2 *src, float2 *acc) {
   if (c->n_m2l_targets == 0) return EFIE_OK;
   const int nI = c->nI;
-  if (F >= 128 && nI <= 128) {
-    dim3 grid(c->n_m2l_targets, (F + 127) / 128);
-    const float kf = (float)c->kappa;
-#define EFIE_TCN(MV)                                                                                         \
-  k_m2l_tcn<128, MV><<<grid, kTcThreads, TcnLayout<128>::kBytes, st>>>(c->d_m2l_targets, c->d_far_ptr,          \
-                                                                       c->d_far_src, c->d_pgeo, c->d_pph, nI, \
-                                                                       kf, c->d_nodeX4, F, ld, src, acc, c->d_tc_err)
-    if (c->m2l_mode == 0) EFIE_TCN(0);
-    else if (c->m2l_mode == 1) EFIE_TCN(1);
-    else EFIE_TCN(2);
-#undef EFIE_TCN
-    ++c->launches;
-    EFIE_CUDA(cudaGetLastError());
-    return EFIE_OK;
-  }
   dim3 grid(c->n_m2l_targets, (F + kTcFields - 1) / kTcFields);
   if (nI <= 64) launch_np<64>(c, st, grid, F, ld, src, acc);
   else if (nI <= 96) launch_np<96>(c, st, grid, F, ld, src, acc);

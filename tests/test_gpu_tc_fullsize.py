@@ -1,8 +1,8 @@
 """The tensor-core M2L (split TF32, FP32 accumulation) at the far-list lengths of the 139k-DOF
 torus workload: torus R = 2, r = 0.5 (16 patches), p = 3, 32 x 32 elements per patch, kappa =
 20, q = 10 (121 interpolation nodes, the tile of that workload), eta = 1.6, 16 right-hand
-sides in one batched product (and 40 for the kernel that puts the fields on the MMA's N
-dimension).  Sampled superspace rows of every right-hand side are compared
+sides in one batched product (and 40: three blocks of 64 fields, the last one ragged).  Sampled
+superspace rows of every right-hand side are compared
 with the FP64 oracle element by element (max-norm relative, 1e-5): the far part from
 oracle.fmm_rows_far (direct moments, far field of the blocks whose target cluster contains the
 element) and the near part from the oracle's element blocks, which are pinned to equal
@@ -30,11 +30,10 @@ def torus():
     s.close()
 
 
-@pytest.mark.parametrize("R", [16, 40], ids=["fields_on_rows_r16", "fields_on_columns_r40"])
+@pytest.mark.parametrize("R", [16, 40])
 def test_tensor_core_batched_rows_vs_oracle(torus, R):
-    """16 right-hand sides (64 fields) take the kernel with the fields on the MMA rows; 40 (160
-    fields: one full block of 128 and a ragged one of 32) the kernel with the fields on the N
-    dimension."""
+    """16 right-hand sides: one block of 64 fields per target cluster; 40: 160 fields, two full
+    blocks and a ragged one of 32."""
     s, r = torus
     assert s.nfar == len(r.far_pairs()) and s.nsup == r.nsup
     # far lists as long as in the 139k-DOF workload: tens of admissible sources per cluster
@@ -67,8 +66,8 @@ def test_tensor_core_batched_rows_vs_oracle(torus, R):
 @pytest.mark.parametrize("R", [5, 36])
 def test_tensor_core_matches_cuda_core_batched_product(torus, R):
     """The same batched product with the M2L on the CUDA cores (FP32, compensated sums), on all
-    rows: the two mixed forms agree within the mixed tolerance (5 right-hand sides: fields on the
-    MMA rows; 36: fields on the N dimension, a full block of 128 and a ragged one of 16)."""
+    rows: the two mixed forms agree within the mixed tolerance (5 right-hand sides: one ragged
+    block of 20 fields; 36: two full blocks of 64 fields and a ragged one of 16)."""
     s, r = torus
     from paper_1807_03097_gb300 import Solver
 
