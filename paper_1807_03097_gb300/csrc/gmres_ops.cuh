@@ -31,9 +31,12 @@ __device__ __forceinline__ void dot_partial_chunk(int N, int nvec, int i0, int c
       for (int v = 0; v < kVecPerBlock; ++v) {
         int i = i0 + v;
         if (i < nvec) {
+          // conj(a) w as four FMAs into the running sums (FP64 is GB300's scarcest pipe)
           double2 a = V[(size_t)i * ldv + t];
-          acc[v].x += a.x * wt.x + a.y * wt.y;
-          acc[v].y += a.x * wt.y - a.y * wt.x;
+          acc[v].x = fma(a.x, wt.x, acc[v].x);
+          acc[v].x = fma(a.y, wt.y, acc[v].x);
+          acc[v].y = fma(a.x, wt.y, acc[v].y);
+          acc[v].y = fma(-a.y, wt.x, acc[v].y);
         }
       }
     }
@@ -88,8 +91,10 @@ __device__ __forceinline__ void combine_tile(int N, int t0, int nvec, const doub
   if (t < N) {
     for (int i = k; i < nvec; i += kCombThreads / 32) {
       double2 a = V[(size_t)i * ldv + t], ci = c[i];
-      x += ci.x * a.x - ci.y * a.y;
-      y += ci.x * a.y + ci.y * a.x;
+      x = fma(ci.x, a.x, x);
+      x = fma(-ci.y, a.y, x);
+      y = fma(ci.x, a.y, y);
+      y = fma(ci.y, a.x, y);
     }
   }
   part[k][lane] = make_double2(x, y);

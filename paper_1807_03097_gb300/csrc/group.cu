@@ -128,7 +128,8 @@ __global__ void __launch_bounds__(kDotThreads) k_g_dot_partial(const GSysD *__re
   const double2 *V, *w;
   double2 *dst;
   const int nvec = dot_operands(s, pass, V, w, dst);
-  for (int i0 = 0; i0 < nvec; i0 += kVecPerBlock)
+  // grid (chunks, G): block y takes the vector groups y, y + G, ...
+  for (int i0 = kVecPerBlock * blockIdx.y; i0 < nvec; i0 += kVecPerBlock * gridDim.y)
     dot_partial_chunk(s.N, nvec, i0, cidx[blockIdx.x], V, (size_t)s.N, w, s.part, s.nchunk);
 }
 
@@ -256,7 +257,8 @@ efie_status body_post(Group *g) {
   cudaStream_t st = c->stream;
   k_g_unpack<<<g->nchunks, kDotThreads, 0, st>>>(g->d_tab, g->d_csys, g->d_cidx);
   for (int pass = 0; pass < 3; ++pass) {
-    k_g_dot_partial<<<g->nchunks, kDotThreads, 0, st>>>(g->d_tab, g->d_csys, g->d_cidx, pass);
+    const int groups = pass == 2 ? 1 : std::min(32, (g->kr_max + 1 + kVecPerBlock - 1) / kVecPerBlock);
+    k_g_dot_partial<<<dim3(g->nchunks, groups), kDotThreads, 0, st>>>(g->d_tab, g->d_csys, g->d_cidx, pass);
     k_g_dot_final<<<g->nsys, 256, 0, st>>>(g->d_tab, pass);
     if (pass < 2)
       k_g_combine<<<dim3(g->nchunks, kChunk / kCombRows), kCombThreads, 0, st>>>(g->d_tab, g->d_csys, g->d_cidx, pass);
