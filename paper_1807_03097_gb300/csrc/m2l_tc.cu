@@ -34,7 +34,6 @@ constexpr int kTcProducers = 32 * kTcWarps;
 constexpr int kTcThreads = kTcProducers + 32;   // + the MMA-issue warp
 constexpr long long kTcWaitCycles = 1ll << 31;  // about a second
 constexpr int kTcGroup = 4;  // block pairs accumulated in D before it is folded into S
-constexpr int kTcCluster = 2;  // field groups per thread-block cluster (sharing the coupling tile)
 
 template <int NP>
 struct TcLayout {
@@ -118,7 +117,7 @@ __device__ __forceinline__ int ldg_pin(const int *p) {
 // f = r (A rows f and 64 + f, i < 2) and target nodes n = r (B rows, i < NP / 32).  A
 // half-warp then writes 8 rows x 4 K-columns, 32 distinct banks.  Tensor memory: D1 [0, NP), D2 [NP, 2 NP) hold the group of block
 // pairs in flight, S1 [2 NP, 3 NP), S2 [3 NP, 4 NP) the running sums over the far list.
-template <int NP, int MODE, int CL>
+template <int NP, int MODE>
 __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
     const int *__restrict__ targets, const int *__restrict__ fptr, const int *__restrict__ fsrc,
     const float4 *__restrict__ pgeo, const float2 *__restrict__ pph, int nI, float kappa,
@@ -138,16 +137,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
   const int f0 = blockIdx.y * kTcFields;
   const int k0 = fptr[t], nsrc = fptr[t + 1] - k0;
   const int nchunk = (nI + 31) / 32, T = nsrc * nchunk;
-  // With CL > 1 the CL blocks of a cluster are the field groups of one target cluster: block
-  // `crank` evaluates the coupling rows rbase + 32 i with i % CL == crank and writes them into the
-  // B tiles of every block of the cluster; a stage is full when all CL blocks' staging threads
-  // have arrived, and free when all CL blocks' MMAs have consumed it.
-  const uint32_t crank = CL > 1 ? tc::cluster_rank() : 0u;
 
   if (tid == 0) {
     for (int i = 0; i < 2; ++i) {
-      tc::mbar_init(b_full + 8 * i, kTcProducers * CL);
-      tc::mbar_init(b_empty + 8 * i, CL);
+      tc::mbar_init(b_full + 8 * i, kTcProducers);
+      tc::mbar_init(b_empty + 8 * i, 1);
     }
     tc::mbar_init(b_tfull, 1);
     tc::mbar_init(b_tempty, kTcProducers);
@@ -163,8 +157,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), L::kCols);
   tc::fence_before_sync();
-  if (CL > 1) tc::cluster_sync();  // barriers initialised in every block before any remote arrival
-  else __syncthreads();
+  __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
   const uint32_t idesc = tc::idesc_tf32(128, 2 * NP);
@@ -246,11 +239,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
     cg = ng;
     cph = nph;
     load_stage();
-    if (it >= 2) {
-      const bool ok = CL > 1 ? tc::mbar_wait_cluster(b_empty + 8 * st, ((it >> 1) & 1) ^ 1, kTcWaitCycles)
-                             : tc::mbar_wait(b_empty + 8 * st, ((it >> 1) & 1) ^ 1, kTcWaitCycles);
-      if (!ok) atomicOr(err, 2);
-    }
+    if (it >= 2 && !tc::mbar_wait(b_empty + 8 * st, ((it >> 1) & 1) ^ 1, kTcWaitCycles)) atomicOr(err, 2);
     uint8_t *sAh = smem + st * L::kStage, *sAl = sAh + L::kA;
     uint8_t *sBh = sAh + 2 * L::kA, *sBl = sBh + 2 * L::kB;  // rows [0, NP) Re, [NP, 2 NP) Im
     const uint32_t kcol = 4 * jq + 2 * jh;
@@ -274,7 +263,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
 #pragma unroll
     for (int k = 0; k < NP / 32; ++k) {
       const int n = rbase + 32 * k;
-      if (CL > 1 && (k % CL) != (int)crank) continue;  // another block of the cluster evaluates it
       if (n >= nI) continue;  // padding rows, zero since the start
       const float4 xt = sXt[n];
       const float4 ut = make_float4(cg.x + xt.x, cg.y + xt.y, cg.z + xt.z, 0.f);
@@ -287,42 +275,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
       tc::split_tf32(gim.x, ih[0], il[0]);
       tc::split_tf32(gre.y, rh[1], rl[1]);
       tc::split_tf32(gim.y, ih[1], il[1]);
-      if (CL > 1) {
-        const uint32_t bh = tc::smem_u32(sBh), bl = tc::smem_u32(sBl);
-#pragma unroll
-        for (int d = 0; d < CL; ++d) {
-          tc::st_cluster_f2(tc::mapa(bh + tc::tile_off(n, kcol), d), rh[0], rh[1]);
-          tc::st_cluster_f2(tc::mapa(bl + tc::tile_off(n, kcol), d), rl[0], rl[1]);
-          tc::st_cluster_f2(tc::mapa(bh + tc::tile_off(NP + n, kcol), d), ih[0], ih[1]);
-          tc::st_cluster_f2(tc::mapa(bl + tc::tile_off(NP + n, kcol), d), il[0], il[1]);
-        }
-      } else {
-        st2(sBh, tc::tile_off(n, kcol), rh[0], rh[1]);
-        st2(sBl, tc::tile_off(n, kcol), rl[0], rl[1]);
-        st2(sBh, tc::tile_off(NP + n, kcol), ih[0], ih[1]);
-        st2(sBl, tc::tile_off(NP + n, kcol), il[0], il[1]);
-      }
+      st2(sBh, tc::tile_off(n, kcol), rh[0], rh[1]);
+      st2(sBl, tc::tile_off(n, kcol), rl[0], rl[1]);
+      st2(sBh, tc::tile_off(NP + n, kcol), ih[0], ih[1]);
+      st2(sBl, tc::tile_off(NP + n, kcol), il[0], il[1]);
     }
-    if (CL > 1) {
-      tc::fence_proxy_async_cluster();
-#pragma unroll
-      for (int d = 0; d < CL; ++d) tc::mbar_arrive_remote(tc::mapa(b_full + 8 * st, d));
-    } else {
-      tc::fence_proxy_async();
-      tc::mbar_arrive(b_full + 8 * st);
-    }
+    tc::fence_proxy_async();
+    tc::mbar_arrive(b_full + 8 * st);
     // the previous group's MMAs are done by now: fold it into the running sums
     const bool gstart = c == 0 && p % kTcGroup == 0;
     if (gstart && p >= 1) drain(p / kTcGroup - 1);
   }
   if (nsrc >= 1) drain((nsrc - 1) / kTcGroup);
-  if (CL > 1) {
-    // the other blocks' MMAs of the last two stages commit to this block's stage barriers:
-    // wait for them before the block may exit
-    for (int it = T; it < T + 2; ++it)
-      if (it >= 2 && !tc::mbar_wait_cluster(b_empty + 8 * (it & 1), ((it >> 1) & 1) ^ 1, kTcWaitCycles))
-        atomicOr(err, 2);
-  }
   } else if (lane == 0) {
     // ------------------------------------------------------------------- MMA issue
     // One thread, so that its waits on the tensor pipe stall no staging warp.  Descriptors are
@@ -336,9 +300,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
       const bool gstart = c == 0 && p % kTcGroup == 0;
       // [D1 D2] (+)= A [Re B; Im B]^T, three split products per K-step
       if (gstart && p >= 1 && !tc::mbar_wait(b_tempty, (p / kTcGroup - 1) & 1, kTcWaitCycles)) atomicOr(err, 4);
-      const bool full = CL > 1 ? tc::mbar_wait_cluster(b_full + 8 * st, (it >> 1) & 1, kTcWaitCycles)
-                               : tc::mbar_wait(b_full + 8 * st, (it >> 1) & 1, kTcWaitCycles);
-      if (!full) atomicOr(err, 8);
+      if (!tc::mbar_wait(b_full + 8 * st, (it >> 1) & 1, kTcWaitCycles)) atomicOr(err, 8);
       tc::fence_after_sync();
       const int ksteps = min(4, (nI - 32 * c + 7) / 8);
       for (int ks = 0; ks < ksteps; ++ks) {
@@ -347,8 +309,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
         tc::mma_tf32(tbase, dah0 + o, dbl0 + o, idesc, 1u);
         tc::mma_tf32(tbase, dal0 + o, dbh0 + o, idesc, 1u);
       }
-      if (CL > 1) tc::mma_commit_multicast(b_empty + 8 * st, (uint16_t)((1u << CL) - 1u));
-      else tc::mma_commit(b_empty + 8 * st);
+      tc::mma_commit(b_empty + 8 * st);
       if (c == nchunk - 1 && (p % kTcGroup == kTcGroup - 1 || p == nsrc - 1)) tc::mma_commit(b_tfull);
     }
   }
@@ -385,34 +346,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(
     acc[((size_t)t * nI + i) * ld + f0 + f] = make_float2(re, im);
   }
   tc::fence_before_sync();
-  if (CL > 1) tc::cluster_sync();  // no block leaves while another may still address it
-  else __syncthreads();
+  __syncthreads();
   tc::fence_after_sync();
   if (warp == 0) tc::tmem_dealloc(tbase, L::kCols);
 }
 
-template <int NP, int MODE, int CL>
+template <int NP, int MODE>
 static efie_status tc_attr() {
-  cudaError_t e = cudaFuncSetAttribute(k_m2l_tc<NP, MODE, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_m2l_tc<NP, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)TcLayout<NP>::kBytes);
   return e == cudaSuccess ? EFIE_OK : EFIE_ECUDA;
 }
 
-template <int NP, int CL>
+template <int NP>
 static efie_status tc_attrs() {
-  efie_status e = tc_attr<NP, 0, CL>();
-  if (e == EFIE_OK) e = tc_attr<NP, 1, CL>();
-  if (e == EFIE_OK) e = tc_attr<NP, 2, CL>();
+  efie_status e = tc_attr<NP, 0>();
+  if (e == EFIE_OK) e = tc_attr<NP, 1>();
+  if (e == EFIE_OK) e = tc_attr<NP, 2>();
   return e;
 }
 
 bool m2l_tc_supported(const Ctx *c) { return c->nI <= 128; }
 
 efie_status m2l_tc_prepare(Ctx *c) {
-  EFIE_TRY((tc_attrs<64, 1>()));
-  EFIE_TRY((tc_attrs<96, 1>()));
-  EFIE_TRY((tc_attrs<128, 1>()));
-  EFIE_TRY((tc_attrs<128, kTcCluster>()));
+  EFIE_TRY(tc_attrs<64>());
+  EFIE_TRY(tc_attrs<96>());
+  EFIE_TRY(tc_attrs<128>());
   if (!c->d_tc_err) {
     EFIE_TRY(dalloc(c, &c->d_tc_err, 1));
     EFIE_CUDA(cudaMemsetAsync(c->d_tc_err, 0, sizeof(int), c->stream));
@@ -420,58 +379,30 @@ efie_status m2l_tc_prepare(Ctx *c) {
   return EFIE_OK;
 }
 
-template <int NP, int MODE, int CL>
-static cudaError_t launch_cl(Ctx *c, cudaStream_t st, dim3 grid, int F, int ld, const float2 *src, float2 *acc) {
+template <int NP>
+static void launch_np(Ctx *c, cudaStream_t st, dim3 grid, int F, int ld, const float2 *src, float2 *acc) {
   const float kf = (float)c->kappa;
-  if (CL == 1) {
-    k_m2l_tc<NP, MODE, 1><<<grid, kTcThreads, TcLayout<NP>::kBytes, st>>>(
-        c->d_m2l_targets, c->d_far_ptr, c->d_far_src, c->d_pgeo, c->d_pph, c->nI, kf, c->d_nodeX4, F, ld, src, acc,
-        c->d_tc_err);
-    return cudaGetLastError();
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = dim3(kTcThreads, 1, 1);
-  cfg.dynamicSmemBytes = TcLayout<NP>::kBytes;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 1;
-  at[0].val.clusterDim.y = CL;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_m2l_tc<NP, MODE, CL>, (const int *)c->d_m2l_targets, (const int *)c->d_far_ptr,
-                            (const int *)c->d_far_src, (const float4 *)c->d_pgeo, (const float2 *)c->d_pph, c->nI, kf,
-                            (const float4 *)c->d_nodeX4, F, ld, src, acc, c->d_tc_err);
-}
-
-template <int NP, int CL>
-static cudaError_t launch_np(Ctx *c, cudaStream_t st, dim3 grid, int F, int ld, const float2 *src, float2 *acc) {
-  if (c->m2l_mode == 0) return launch_cl<NP, 0, CL>(c, st, grid, F, ld, src, acc);
-  if (c->m2l_mode == 1) return launch_cl<NP, 1, CL>(c, st, grid, F, ld, src, acc);
-  return launch_cl<NP, 2, CL>(c, st, grid, F, ld, src, acc);
+#define EFIE_TC(MV)                                                                                      \
+  k_m2l_tc<NP, MV><<<grid, kTcThreads, TcLayout<NP>::kBytes, st>>>(c->d_m2l_targets, c->d_far_ptr,          \
+                                                                   c->d_far_src, c->d_pgeo, c->d_pph, c->nI, \
+                                                                   kf, c->d_nodeX4, F, ld, src, acc, c->d_tc_err)
+  if (c->m2l_mode == 0) EFIE_TC(0);
+  else if (c->m2l_mode == 1) EFIE_TC(1);
+  else EFIE_TC(2);
+#undef EFIE_TC
 }
 
 // acc[t][i][f] for the targets of the M2L, f < F = 4 R, row stride ld (float2 entries)
 efie_status launch_m2l_tc(Ctx *c, cudaStream_t st, int F, int ld, const float2 *src, float2 *acc) {
   if (c->n_m2l_targets == 0) return EFIE_OK;
   const int nI = c->nI;
-  const int groups = (F + kTcFields - 1) / kTcFields;
-  cudaError_t e;
-  if (nI > 96 && nI <= 128 && groups >= kTcCluster) {
-    // the field groups of a target cluster as one thread-block cluster sharing the coupling tile
-    dim3 grid(c->n_m2l_targets, (groups + kTcCluster - 1) / kTcCluster * kTcCluster);
-    e = launch_np<128, kTcCluster>(c, st, grid, F, ld, src, acc);
-  } else {
-    dim3 grid(c->n_m2l_targets, groups);
-    if (nI <= 64) e = launch_np<64, 1>(c, st, grid, F, ld, src, acc);
-    else if (nI <= 96) e = launch_np<96, 1>(c, st, grid, F, ld, src, acc);
-    else if (nI <= 128) e = launch_np<128, 1>(c, st, grid, F, ld, src, acc);
-    else return EFIE_EINVAL;
-  }
+  dim3 grid(c->n_m2l_targets, (F + kTcFields - 1) / kTcFields);
+  if (nI <= 64) launch_np<64>(c, st, grid, F, ld, src, acc);
+  else if (nI <= 96) launch_np<96>(c, st, grid, F, ld, src, acc);
+  else if (nI <= 128) launch_np<128>(c, st, grid, F, ld, src, acc);
+  else return EFIE_EINVAL;
   ++c->launches;
-  EFIE_CUDA(e);
+  EFIE_CUDA(cudaGetLastError());
   return EFIE_OK;
 }
 
