@@ -864,7 +864,7 @@ BATCH = {
     "m2l": "autotuned per problem at setup (ordered vs unordered-pair kernel, m2l_pairs=2)",
     "execution": "256 contexts set up on 16 host threads (efie_setup_many), then one lockstep group solve "
                  "(efie_group_solve): per GMRES step one CUDA-graph launch holding every unfinished "
-                 "problem's product, batched Arnoldi/Givens launches over all systems",
+                 "problem's product chain as a branch and the Arnoldi/Givens kernels of all systems",
 }
 
 

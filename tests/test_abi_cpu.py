@@ -72,7 +72,25 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     assert lib.efie_server_destroy(None) == 0
     assert lib.efie_launch_count(None) == -1
     assert lib.efie_last_error(None) == b""
-    for bad in (dict(m2l_store=3), dict(m2l_batch=3), dict(m2l_batch=2, q=11)):
+    # near-field product alone, batched superspace product, setup timings, device bytes
+    assert lib.efie_near_apply(None, None, None, 0) == -1
+    assert lib.efie_matvec_superspace_batch(None, 1, None, None, 0) == -1
+    assert lib.efie_setup_timings(None, None, 0) == 0
+    assert lib.efie_device_bytes(None, None, None) == -1
+    # groups of problems
+    g = ctypes.c_void_p()
+    assert lib.efie_group_create(None, None, 1) == -1
+    assert lib.efie_group_create(ctypes.byref(g), None, 1) == -1
+    arr = (ctypes.c_void_p * 1)(None)
+    assert lib.efie_group_create(ctypes.byref(g), arr, 0) == -1
+    assert lib.efie_group_create(ctypes.byref(g), arr, 1) == -1   # a null context
+    assert lib.efie_group_solve(None, None, None, 0, None, None, None) == -1
+    assert lib.efie_group_stats(None, None, 0) == 0
+    assert lib.efie_group_destroy(None) == 0
+    assert lib.efie_group_last_error(None) == b"null group"
+    assert lib.efie_setup_many(None, 1, 1, None) == -1
+    assert lib.efie_setup_many(arr, 1, 0, None) == -1
+    for bad in (dict(m2l_store=3), dict(m2l_batch=3), dict(m2l_batch=2, q=11), dict(m2l_pairs=3), dict(leaf_dense=2)):
         o = efie.options(**bad)
         assert lib.efie_create(ctypes.byref(h), ctypes.byref(o), None) == -1, bad
 
