@@ -528,6 +528,8 @@ def run_gpu(args):
             "gmres_iterations": int(np.median(its)), "converged": all(conv),
             "setup_ms": st_["setup_ms"],
             "matvec_per_s": 1000.0 / mv["total"], "matvec_ms_phases": mv,
+            "matvec_ms_p10_p50_p90": [float(np.percentile([p["total"] for p in ph], q)) for q in (10, 50, 90)],
+            "matvec_count": len(ph),
             "matvec_per_s_fp64": 1000.0 / mv64["total"], "matvec_ms_phases_fp64": mv64,
             "matvec_rel_err_vs_fp64": err_vs_fp64,
             "fp64_solve": fp64,
@@ -977,7 +979,11 @@ def serving_leg(args):
             "footprint_over_device_peak_min": float(min(x[0].footprint_bytes / max(x[0].device_peak_bytes, 1)
                                                         for x in res)),
             "footprint_over_device_peak": [round(x[0].footprint_bytes / max(x[0].device_peak_bytes, 1), 3)
-                                           for x in res]}
+                                           for x in res],
+            "trace": [{"arrival_s": round(r["t"], 4), "ndof": int(x[0].ndof), "directions": len(r["dirs"]),
+                       "p": r["opt"]["p"], "kappa": round(r["opt"]["kappa"], 3), "status": int(x[0].status),
+                       "iterations": int(x[0].iterations), "queue_ms": round(x[0].queue_ms, 1),
+                       "latency_ms": round(x[0].latency_ms, 1)} for r, x in zip(reqs, res)]}
     return line
 
 
