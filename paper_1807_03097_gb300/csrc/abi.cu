@@ -24,6 +24,7 @@ namespace {
 // Returns every device buffer of the context to the pool (in stream order on c->stream;
 // callers make sure that no work on the second stream still reads them).
 void release_device(Ctx *c) {
+  drop_product_graph(c);
   dfree(c, c->d_patches); dfree(c, c->d_knots); dfree(c, c->d_cpw);
   dfree(c, c->d_tg_ptr); dfree(c, c->d_tg_col); dfree(c, c->d_tg_val);
   dfree(c, c->d_ts_ptr); dfree(c, c->d_ts_col); dfree(c, c->d_ts_val);
@@ -250,6 +251,7 @@ efie_status efie_setup(efie_ctx *ctx) {
   if (!c) return EFIE_EINVAL;
   if (!c->have_geometry) return EFIE_ESTATE;
   cudaSetDevice(c->device);
+  drop_product_graph(c);  // the setup rebuilds the buffers it names
   auto t0 = std::chrono::steady_clock::now();
   const efie_options &o = c->opt;
   c->p = o.p;

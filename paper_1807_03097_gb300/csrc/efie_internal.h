@@ -163,6 +163,11 @@ struct Ctx {
   double2 *d_w = nullptr, *d_r = nullptr, *d_b = nullptr, *d_sol = nullptr;
   double *h_res = nullptr;    // pinned host mirror of the residual estimate
   int part_cap = 0;
+  // the product of the single-system solver as one graph: A d_mvin -> d_w (captured once per
+  // setup; dropped whenever the buffers it names are released or rebuilt)
+  cudaGraphExec_t g_mv = nullptr;
+  double2 *d_mvin = nullptr;
+  long long mv_kernels = 0;  // kernels in g_mv
 
   // device memory of this context (stream-ordered pool allocations, devmem.cpp)
   std::mutex mem_mu;
@@ -186,6 +191,9 @@ struct Ctx {
   efie_solve_info info{};
   std::string err;
 };
+
+// drop the captured product graph of the single-system solver (gmres.cu)
+void drop_product_graph(Ctx *c);
 
 // helpers implemented in the .cu / .cpp files
 efie_status host_build_space(Ctx *c, const std::vector<double> &edge_pts, const std::vector<double> &corner_pts);

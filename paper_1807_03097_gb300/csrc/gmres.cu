@@ -79,6 +79,47 @@ static efie_status dots(Ctx *c, int N, int nvec, const double2 *V, size_t ldv, c
   return EFIE_OK;
 }
 
+void drop_product_graph(Ctx *c) {
+  if (c->g_mv) cudaGraphExecDestroy(c->g_mv);
+  c->g_mv = nullptr;
+  dfree(c, c->d_mvin);
+}
+
+// out = A in for the single-system solver as one CUDA-graph launch: the product chain (about
+// 20 small kernels around the M2L, near field on the second stream) is captured once per setup
+// with input d_mvin and output d_w, and replayed, without the launch gaps between its kernels.
+static efie_status gmres_product(Ctx *c, const double2 *in, double2 *out) {
+  cudaStream_t st = c->stream;
+  const size_t bytes = sizeof(double2) * (size_t)c->ndof;
+  if (!c->g_mv) {
+    EFIE_TRY(dalloc(c, &c->d_mvin, (size_t)c->ndof));
+    EFIE_CUDA(cudaMemsetAsync(c->d_mvin, 0, bytes, st));
+    EFIE_TRY(dev_matvec(c, c->d_mvin, c->d_w));  // buffers created on first use exist before the capture
+    EFIE_CUDA(cudaStreamSynchronize(st));
+    const long long l0 = c->launches;
+    EFIE_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const efie_status s = dev_matvec(c, c->d_mvin, c->d_w);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &g);
+    c->mv_kernels = c->launches - l0;
+    c->launches = l0;
+    if (s != EFIE_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    EFIE_CUDA(e);
+    const cudaError_t ei = cudaGraphInstantiate(&c->g_mv, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) c->g_mv = nullptr;
+    EFIE_CUDA(ei);
+  }
+  EFIE_CUDA(cudaMemcpyAsync(c->d_mvin, in, bytes, cudaMemcpyDeviceToDevice, st));
+  EFIE_CUDA(cudaGraphLaunch(c->g_mv, st));
+  if (out != c->d_w) EFIE_CUDA(cudaMemcpyAsync(out, c->d_w, bytes, cudaMemcpyDeviceToDevice, st));
+  c->launches += c->mv_kernels;
+  return EFIE_OK;
+}
+
 efie_status dev_gmres(Ctx *c, const double2 *b, double2 *x, int *its_out, double *res_out, int *conv_out) {
   const int N = c->ndof;
   const int kr = std::max(1, std::min(c->opt.gmres_restart, c->opt.gmres_maxit));
@@ -119,7 +160,7 @@ efie_status dev_gmres(Ctx *c, const double2 *b, double2 *x, int *its_out, double
     if (first) {
       EFIE_CUDA(cudaMemcpyAsync(c->d_r, b, sizeof(double2) * N, cudaMemcpyDeviceToDevice, st));
     } else {
-      EFIE_TRY(dev_matvec(c, x, c->d_r));
+      EFIE_TRY(gmres_product(c, x, c->d_r));
       k_residual<<<grid, blk, 0, st>>>(N, b, c->d_r); ++c->launches;
     }
     first = false;
@@ -136,7 +177,7 @@ efie_status dev_gmres(Ctx *c, const double2 *b, double2 *x, int *its_out, double
     int jd = 0;
     for (int j = 0; j < kr && its < c->opt.gmres_maxit; ++j) {
       double2 *vj = V + (size_t)j * N;
-      EFIE_TRY(dev_matvec(c, vj, c->d_w));
+      EFIE_TRY(gmres_product(c, vj, c->d_w));
       ++its;
       // CGS2
       EFIE_TRY(dots(c, N, j + 1, V, N, c->d_w, c->d_h));
@@ -160,7 +201,7 @@ efie_status dev_gmres(Ctx *c, const double2 *b, double2 *x, int *its_out, double
     }
     if (res <= target) {
       // confirm with the true residual
-      EFIE_TRY(dev_matvec(c, x, c->d_r));
+      EFIE_TRY(gmres_product(c, x, c->d_r));
       k_residual<<<grid, blk, 0, st>>>(N, b, c->d_r); ++c->launches;
       EFIE_TRY(dots(c, N, 1, c->d_r, N, c->d_r, c->d_h));
       EFIE_CUDA(cudaMemcpyAsync(c->h_res, c->d_h, sizeof(double2), cudaMemcpyDeviceToHost, st));
