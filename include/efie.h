@@ -345,7 +345,8 @@ const char *efie_last_error(const efie_ctx *ctx);
  * While a group solve runs, its contexts must not be used by other calls.  The contexts
  * stay owned by the caller and must outlive the group.
  * Returns EFIE_NOT_CONVERGED if any system did not converge; EFIE_ESTATE if a context is
- * not set up; EFIE_EINVAL for null pointers, repeated or mixed-device contexts.
+ * not set up (or, at solve time, was set up again with another number of DOFs since the group
+ * was made); EFIE_EINVAL for null pointers, repeated or mixed-device contexts.
  * efie_group_stats: [steps, product-graph captures, kernels launched (graph nodes counted),
  * solve wall time ms, kernel nodes of the product graph, vector chunks, device ms of the pre,
  * product and post graphs summed over the steps (CUDA events on the group's stream)] of the

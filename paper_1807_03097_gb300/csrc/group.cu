@@ -198,6 +198,7 @@ struct HostSys {
 struct Group {
   Ctx gc;  // device, stream and device memory of the group itself
   std::vector<Ctx *> ctx;
+  std::vector<int> ndof;  // DOFs of each context when the group was made (the chunk table's sizes)
   int nsys = 0, kr_max = 1, nchunks = 0;
   GSysD *h_tab = nullptr, *d_tab = nullptr;
   double *h_out = nullptr, *d_out = nullptr;
@@ -380,6 +381,7 @@ efie_status efie_group_create(efie_group **out, efie_ctx *const *ctxs, int nctx)
   for (int i = 0; i < nctx; ++i) {
     Ctx *m = reinterpret_cast<Ctx *>(ctxs[i]);
     g->ctx.push_back(m);
+    g->ndof.push_back(m->ndof);
     cudaEvent_t e = nullptr;
     if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(EFIE_ECUDA);
     g->joins.push_back(e);
@@ -447,6 +449,11 @@ efie_status efie_group_solve(efie_group *grp, const double *const *b, double *co
   const int K = g->nsys;
   for (int i = 0; i < K; ++i)
     if (!b[i] || !x[i]) return EFIE_EINVAL;
+  for (int i = 0; i < K; ++i)
+    if (!g->ctx[i]->setup_done || g->ctx[i]->ndof != g->ndof[i]) {
+      c->err = "problem " + std::to_string(i) + " was set up again with other sizes since the group was made";
+      return EFIE_ESTATE;
+    }
   const auto t0 = std::chrono::steady_clock::now();
   std::vector<HostSys> S(K);
   DevTemp mem;

@@ -135,3 +135,21 @@ def test_group_recaptures_products_as_systems_finish_and_setup_many():
         assert info.iterations == its[i] and np.array_equal(x1, xs[i])
     for s in solvers:
         s.close()
+
+
+def test_group_refuses_a_problem_set_up_again_with_other_sizes():
+    """A context set up again with another geometry (another number of DOFs) after the group was
+    made is refused at solve time (EFIE_ESTATE) instead of being solved with stale tables."""
+    from paper_1807_03097_gb300.efie import Group
+
+    s = make(0)
+    g = Group([s])
+    b0 = rhs(s, 0)[0]
+    xs, its, res, conv, st = g.solve([b0])
+    assert conv.all()
+    s.set_geometry(G.cube())
+    s.setup()
+    with pytest.raises(RuntimeError, match="set up again"):
+        g.solve([rhs(s, 0)[0]])
+    g.close()
+    s.close()
