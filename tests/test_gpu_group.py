@@ -147,7 +147,7 @@ def test_group_refuses_a_problem_set_up_again_with_other_sizes():
     b0 = rhs(s, 0)[0]
     xs, its, res, conv, st = g.solve([b0])
     assert conv.all()
-    s.set_geometry(G.cube())
+    s.set_geometry(G.torus())  # 16 patches: 512 DOFs instead of the sphere's 192
     s.setup()
     with pytest.raises(RuntimeError, match="set up again"):
         g.solve([rhs(s, 0)[0]])
